@@ -1,0 +1,263 @@
+"""FP64 CPU oracle of e-prop -- TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  The CUDA library never calls it and it
+never calls the CUDA library; the two share no code.  The only thing they
+share is the seeded input generators of the `workloads` package.
+
+Contents
+--------
+* ``Oracle``: ctypes wrapper around the plain C time-driven simulation in
+  ``eprop_oracle.c`` (Methods: neuron models, loss functions, gradients,
+  optimisation; Algorithm 1 "Time-driven gradient computation").
+* ``eligibility_step``: the oracle's per-synapse recursion (Eq. eligibility-
+  vector-substituted, Eq. filtered-eligibility-trace), exported for pins.
+* ``event_driven_gradients``: the event-driven restatement (Algorithm 5,
+  "Optimized event-driven weight update"): each synapse is visited only at
+  the arrivals of its presynaptic spikes and integrates its trace over the
+  left-open interval since the previous arrival; used to check that the
+  event-driven and the time-driven organisations give the same gradient.
+* ``build()``: compiles the C oracle with gcc into ``oracle/_lib``.
+
+Parity status per function: all functions are pinned by the CPU tests in
+``tests/test_oracle_*.py`` (closed forms, autograd BPTT special case, hand
+sums, reductions, event/time-driven invariant).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_SO = os.path.join(_LIBDIR, "libeprop_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (plain -O2, no fast-math) and return the path."""
+    src = os.path.join(_HERE, "eprop_oracle.c")
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-fno-fast-math", "-ffp-contract=off", src,
+                               "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_rec", ctypes.c_int32),
+                ("n_out", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("neuron_model", ctypes.c_int32), ("t_ref", ctypes.c_int32),
+                ("loss", ctypes.c_int32), ("feedback", ctypes.c_int32),
+                ("update_interval", ctypes.c_int32), ("continuous", ctypes.c_int32),
+                ("max_delay", ctypes.c_int32), ("n_drive_thr", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("rho", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("kappa_e", ctypes.c_double),
+                ("beta_a", ctypes.c_double), ("v_th", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("beta_sg", ctypes.c_double),
+                ("lr", ctypes.c_double), ("drive_weight", ctypes.c_double),
+                ("drive_seed", ctypes.c_uint64),
+                ("drive_thr", ctypes.c_void_p)]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int64), ("nnz", ctypes.c_int64)] + [
+        (name, ctypes.c_void_p) for name in (
+            "ptr", "col", "delay", "w", "w_out", "out_mask", "fb", "v", "a",
+            "psi_prev", "ref", "z_prev", "ring", "src_hist", "zbar", "epsa",
+            "ebar", "g", "y", "zk", "g_out", "grad_acc", "grad_out_acc",
+            "counters")]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_simulate.restype = ctypes.c_int
+            lib.oracle_simulate.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_State),
+                                            ctypes.c_int32] + [ctypes.c_void_p] * 12
+            lib.oracle_eligibility_step.restype = ctypes.c_double
+            lib.oracle_eligibility_step.argtypes = [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def eligibility_step(alpha, rho, beta_a, kappa_e, psi_prev, psi, L, arrive,
+                     state: np.ndarray) -> float:
+    """One step of the oracle's synapse recursion; state = [zbar, eps_a, ebar]
+    (float64, updated in place).  Returns g^t = L^t ebar^t."""
+    lib = _load()
+    st = state
+    assert st.dtype == np.float64 and st.shape == (3,)
+    base = st.ctypes.data
+    return lib.oracle_eligibility_step(alpha, rho, beta_a, kappa_e, psi_prev,
+                                       psi, L, arrive, base, base + 8, base + 16)
+
+
+class Oracle:
+    """Time-driven FP64 e-prop on one network (state persists across calls).
+
+    Arguments are the plain arrays produced by the `workloads` generators:
+    a spec (`workloads.configs.Spec`) and the CSR synapse arrays by source.
+    """
+
+    def __init__(self, spec, ptr, col, w, delay, w_out, out_mask, feedback=None):
+        self.spec = spec
+        B, N, K = spec.batch, spec.n_rec, spec.n_out
+        D1 = spec.max_delay + 1
+        self.n_src = spec.n_in + N
+        self.ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.delay = np.ascontiguousarray(delay, dtype=np.uint8)
+        self.w = np.array(w, dtype=np.float64)
+        self.nnz = int(self.ptr[-1])
+        assert self.ptr.shape[0] == self.n_src + 1 and self.col.shape[0] == self.nnz
+        if self.nnz:
+            assert int(self.delay.min()) >= 1 and int(self.delay.max()) <= spec.max_delay
+        self.w_out = np.array(w_out, dtype=np.float64).reshape(N, K)
+        self.out_mask = np.ascontiguousarray(out_mask, dtype=np.uint8)
+        self.fb = None if feedback is None else np.array(feedback, dtype=np.float64).reshape(N, K)
+        if spec.feedback and self.fb is None:
+            raise ValueError("random feedback needs a feedback matrix")
+        self.thr = np.ascontiguousarray(spec.drive_thresholds(), dtype=np.uint32)
+        z = np.zeros
+        self.v, self.a, self.psi_prev = z((B, N)), z((B, N)), z((B, N))
+        self.ref = z((B, N), np.int32)
+        self.z_prev = z((B, N), np.uint8)
+        self.ring = z((B, D1, N))
+        self.src_hist = z((B, D1, self.n_src), np.uint8)
+        self.zbar, self.epsa, self.ebar = z((B, self.nnz)), z((B, self.nnz)), z((B, self.nnz))
+        self.g = z(self.nnz)
+        self.y, self.zk = z((B, K)), z((B, N))
+        self.g_out = z((N, K))
+        self.grad_acc = z(self.nnz)
+        self.grad_out_acc = z((N, K))
+        self.counters = z(2, np.int64)
+
+    def _cfg(self, T):
+        s = self.spec
+        import math
+        kappa = math.exp(-s.dt / s.tau_out)
+        return _Cfg(n_in=s.n_in, n_rec=s.n_rec, n_out=s.n_out, batch=s.batch,
+                    neuron_model=s.neuron_model, t_ref=s.t_ref, loss=s.loss,
+                    feedback=s.feedback, update_interval=s.update_interval,
+                    continuous=s.continuous, max_delay=s.max_delay,
+                    n_drive_thr=int(self.thr.shape[0]),
+                    alpha=math.exp(-s.dt / s.tau_m),
+                    rho=math.exp(-s.dt / s.tau_a),
+                    kappa=kappa,
+                    kappa_e=kappa if s.kappa_e is None else float(s.kappa_e),
+                    beta_a=s.beta_a if s.neuron_model == 1 else 0.0,
+                    v_th=s.v_th, gamma=s.gamma, beta_sg=s.beta_sg, lr=s.lr,
+                    drive_weight=s.drive_weight, drive_seed=s.drive_seed,
+                    drive_thr=_p(self.thr) if self.thr.shape[0] else None)
+
+    def _state(self):
+        st = _State(n_src=self.n_src, nnz=self.nnz)
+        for name in ("ptr", "col", "delay", "w", "w_out", "out_mask", "v", "a",
+                     "psi_prev", "ref", "z_prev", "ring", "src_hist", "zbar",
+                     "epsa", "ebar", "g", "y", "zk", "g_out", "grad_acc",
+                     "grad_out_acc", "counters"):
+            setattr(st, name, _p(getattr(self, name)))
+        st.fb = _p(self.fb)
+        return st
+
+    def simulate(self, T, x_ptr, x_ids, targets, window=None, lengths=None,
+                 forced=None, record=False):
+        """Run T steps; returns a dict with y [B,T,K], loss [B], raster
+        [B,T,N] (uint8), margin [B,T,N] (v - v_th) and, if record, psi and L."""
+        s = self.spec
+        B, N, K = s.batch, s.n_rec, s.n_out
+        if s.update_interval and T % s.update_interval:
+            raise ValueError("T must be a multiple of the update interval")
+        x_ptr = np.ascontiguousarray(x_ptr, dtype=np.int64)
+        x_ids = np.ascontiguousarray(x_ids, dtype=np.int32)
+        assert x_ptr.shape[0] == B * T + 1
+        tg = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(B, T, K))
+        win = None if window is None else np.ascontiguousarray(window, dtype=np.uint8).reshape(B, T)
+        lens = np.full(B, T, np.int32) if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
+        fz = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8).reshape(B, T, N)
+        out = dict(y=np.zeros((B, T, K)), loss=np.zeros(B),
+                   raster=np.zeros((B, T, N), np.uint8), margin=np.zeros((B, T, N)))
+        if record:
+            out["psi"] = np.zeros((B, T, N))
+            out["L"] = np.zeros((B, T, N))
+        cfg = self._cfg(T)
+        st = self._state()
+        rc = _load().oracle_simulate(ctypes.byref(cfg), ctypes.byref(st), T,
+                                     _p(x_ptr), _p(x_ids), _p(tg), _p(win), _p(lens),
+                                     _p(fz), _p(out["y"]), _p(out["loss"]),
+                                     _p(out["raster"]), _p(out["margin"]),
+                                     _p(out.get("psi")), _p(out.get("L")))
+        if rc:
+            raise MemoryError("oracle_simulate failed")
+        return out
+
+    def take_grads(self):
+        """Summed batch-mean gradients applied since the last call (input and
+        recurrent synapses in CSR order, and W_out [N, K]); resets them."""
+        g, go = self.grad_acc.copy(), self.grad_out_acc.copy()
+        self.grad_acc[:] = 0.0
+        self.grad_out_acc[:] = 0.0
+        return g, go
+
+
+def event_driven_gradients(spec, ptr, col, delay, src_raster, psi, L, T_len=None):
+    """Event-driven restatement of the recurrent/input gradient of one sample.
+
+    Follows Algorithm 5 ("Optimized event-driven weight update"): a synapse
+    stores the times of its arriving presynaptic spikes; at each arrival
+    (and once more at the end of the sample) it integrates its eligibility
+    state over the left-open interval (t_prev, t] from the postsynaptic
+    history psi^t, L^t and adds sum L^t F_kappa(e^t) to its gradient.
+
+    src_raster : [T, n_src] source spikes (emission steps 1..T)
+    psi, L     : [T, N] postsynaptic history of the sample
+    returns    : gradient per synapse (CSR order), sum over the sample
+    """
+    import math
+    T = psi.shape[0] if T_len is None else T_len
+    alpha = math.exp(-spec.dt / spec.tau_m)
+    rho = math.exp(-spec.dt / spec.tau_a)
+    kappa = math.exp(-spec.dt / spec.tau_out)
+    kappa_e = kappa if spec.kappa_e is None else spec.kappa_e
+    beta_a = spec.beta_a if spec.neuron_model == 1 else 0.0
+    n_src = ptr.shape[0] - 1
+    grads = np.zeros(int(ptr[-1]))
+    for i in range(n_src):
+        spikes = np.nonzero(src_raster[:T, i])[0] + 1      # emission steps
+        for q in range(int(ptr[i]), int(ptr[i + 1])):
+            j, d = int(col[q]), int(delay[q])
+            arrivals = [int(s) + d for s in spikes if int(s) + d <= T]
+            if not arrivals:
+                continue
+            zbar = epsa = ebar = 0.0
+            g = 0.0
+            t_prev = arrivals[0] - 1        # everything before is zero
+            times = set(arrivals)
+            for t_evt in arrivals[1:] + [T]:
+                # left-open interval (t_prev, t_evt]
+                for t in range(t_prev + 1, t_evt + 1):
+                    pp = psi[t - 2, j] if t >= 2 else 0.0
+                    p = psi[t - 1, j]
+                    epsa_new = pp * zbar + (rho - pp * beta_a) * epsa
+                    zbar = alpha * zbar + (1.0 if t in times else 0.0)
+                    epsa = epsa_new
+                    ebar = kappa_e * ebar + p * (zbar - beta_a * epsa)
+                    g += L[t - 1, j] * ebar
+                t_prev = t_evt
+            grads[q] = g
+    return grads

@@ -1,0 +1,290 @@
+/*
+ * FP64 time-driven e-prop oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * This file is the slow, obviously-correct CPU definition of what the CUDA
+ * library computes.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may build, load or call it; the product path never does.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Each simulated step follows the paper's Methods in order:
+ *   - LIF / ALIF membrane, threshold adaptation and spike   (Eq. lif_update,
+ *     Eq. binary-spike-state-variable, Eq. spike-threshold-adaptation)
+ *   - piecewise-linear surrogate gradient psi               (Eq. piecewise-
+ *     linear-surrogate-gradient)
+ *   - leaky readout y, error signal E (MSE or softmax CE)   (Eq. leaky_
+ *     integrator, Eq. mean-squared-error, Eq. softmax, Eq. cross-entropy-loss)
+ *   - learning signal L_j = sum_k B_jk E_k                  (Eq. final-gradient)
+ *   - eligibility vector, eligibility trace, low-pass filter and per-step
+ *     gradient g^t = L^t F_kappa(e^t)                       (Eq. eligibility-
+ *     vector-substituted, Eq. filtered-eligibility-trace, Eq. gradient-rec,
+ *     Eq. gradient-in, Eq. filter)
+ *   - output-weight gradient E_k^t F_kappa(z_j^t)           (Eq. eprop-output-
+ *     new-subs-rewritten with d = 0)
+ *   - accumulated gradient and gradient-descent update      (Eq. accumulated-
+ *     gradients, Eq. gradient-descent), averaged over the mini-batch.
+ * This is the time-driven gradient computation of Algorithm 1 with the
+ * weight update applied at the end of each update window.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - spike iff v - v_th > 0 (strict);
+ *   - refractory period: after a spike at t, z = 0 and psi = 0 for the next
+ *     t_ref steps, v keeps integrating;
+ *   - input and recurrent spikes act through integer delays d >= 1:
+ *     a source spike emitted at step s reaches its target at step s + d, both
+ *     in the membrane input and in the presynaptic trace F_alpha (d = 1 gives
+ *     the paper's z_i^{t-1} and, for inputs, x_i^{t-1});
+ *   - the weight carried by a spike is the weight in effect at the step the
+ *     spike is emitted (weights change only at update-window ends);
+ *   - an external Poisson drive (non-plastic) adds drive_weight * n_j^t to the
+ *     membrane input, n_j^t drawn by the SplitMix64 counter hash;
+ *   - batch gradient = mean over samples of each sample's sum over steps.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t n_in, n_rec, n_out, batch;
+    int32_t neuron_model;         /* 0 LIF, 1 ALIF */
+    int32_t t_ref, loss, feedback, update_interval, continuous, max_delay;
+    int32_t n_drive_thr;
+    double alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg;
+    double lr, drive_weight;
+    uint64_t drive_seed;
+    const uint32_t *drive_thr;
+} oracle_cfg;
+
+typedef struct {
+    /* network: synapses in CSR by source; sources are the n_in inputs
+       followed by the n_rec recurrent neurons */
+    int64_t n_src, nnz;
+    const int64_t *ptr;
+    const int32_t *col;
+    const uint8_t *delay;
+    double *w;                    /* [nnz], updated in place */
+    double *w_out;                /* [n_rec][n_out], updated in place */
+    const uint8_t *out_mask;      /* [n_rec] 1 = neuron projects to readouts */
+    const double *fb;             /* [n_rec][n_out] or NULL (B = W_out^T) */
+    /* persistent state */
+    double *v, *a, *psi_prev;     /* [B][N] */
+    int32_t *ref;                 /* [B][N] */
+    uint8_t *z_prev;              /* [B][N] */
+    double *ring;                 /* [B][D+1][N] pending membrane input */
+    uint8_t *src_hist;            /* [B][D+1][n_src] source spikes of the last D+1 steps */
+    double *zbar, *epsa, *ebar;   /* [B][nnz] eligibility state */
+    double *g;                    /* [nnz]  sum over samples of sum_t g^t */
+    double *y, *zk;               /* [B][K], [B][N] */
+    double *g_out;                /* [N][K] */
+    double *grad_acc, *grad_out_acc; /* applied batch-mean gradients, summed */
+    int64_t *counters;            /* [0] absolute step, [1] step inside run */
+} oracle_state;
+
+/* SplitMix64 output function (Steele, Lea & Flood 2014). */
+static uint64_t mix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+static int drive_count(const oracle_cfg *c, int64_t b, int64_t t_abs, int64_t j) {
+    uint64_t h = mix64(mix64(mix64(c->drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
+    uint32_t u = (uint32_t)(h >> 32);
+    int n = 0;
+    for (int m = 0; m < c->n_drive_thr; ++m)
+        if (u >= c->drive_thr[m]) n++;
+    return n;
+}
+
+/* One step of the per-synapse eligibility recursion (Eq. eligibility-vector-
+ * substituted and Eq. filtered-eligibility-trace):
+ *   eps_a^t = psi^{t-1} zbar^{t-1} + (rho - psi^{t-1} beta_a) eps_a^{t-1}
+ *   zbar^t  = alpha zbar^{t-1} + s^t          (F_alpha of the arriving spike)
+ *   e^t     = psi^t (zbar^t - beta_a eps_a^t)
+ *   ebar^t  = kappa_e ebar^{t-1} + e^t        (F_kappa)
+ * and returns the per-step gradient g^t = L^t ebar^t. */
+double oracle_eligibility_step(double alpha, double rho, double beta_a,
+                               double kappa_e, double psi_prev, double psi,
+                               double L, double arrive, double *zbar,
+                               double *epsa, double *ebar) {
+    double epsa_new = psi_prev * (*zbar) + (rho - psi_prev * beta_a) * (*epsa);
+    *zbar = alpha * (*zbar) + arrive;
+    *epsa = epsa_new;
+    double e = psi * ((*zbar) - beta_a * (*epsa));
+    *ebar = kappa_e * (*ebar) + e;
+    return L * (*ebar);
+}
+
+static void reset_state(const oracle_cfg *c, oracle_state *s) {
+    int64_t B = c->batch, N = c->n_rec, K = c->n_out, D1 = c->max_delay + 1;
+    memset(s->v, 0, sizeof(double) * B * N);
+    memset(s->a, 0, sizeof(double) * B * N);
+    memset(s->psi_prev, 0, sizeof(double) * B * N);
+    memset(s->ref, 0, sizeof(int32_t) * B * N);
+    memset(s->z_prev, 0, B * N);
+    memset(s->ring, 0, sizeof(double) * B * D1 * N);
+    memset(s->src_hist, 0, B * D1 * s->n_src);
+    memset(s->zbar, 0, sizeof(double) * B * s->nnz);
+    memset(s->epsa, 0, sizeof(double) * B * s->nnz);
+    memset(s->ebar, 0, sizeof(double) * B * s->nnz);
+    memset(s->y, 0, sizeof(double) * B * K);
+    memset(s->zk, 0, sizeof(double) * B * N);
+    s->counters[1] = 0;
+}
+
+/* Runs T steps for every sample; returns 0 on success. */
+int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
+                    const int64_t *x_ptr, const int32_t *x_ids,
+                    const double *targets, const uint8_t *window,
+                    const int32_t *lengths, const uint8_t *forced,
+                    double *y_rec, double *loss, uint8_t *raster,
+                    double *margin, double *psi_rec, double *L_rec) {
+    const int64_t B = c->batch, N = c->n_rec, K = c->n_out, NI = c->n_in;
+    const int64_t D1 = c->max_delay + 1, NS = s->n_src, NNZ = s->nnz;
+    const int64_t U = c->update_interval > 0 ? c->update_interval : T;
+    if (!c->continuous) reset_state(c, s);
+    double *psi = (double *)calloc(N, sizeof(double));
+    double *L = (double *)calloc(N, sizeof(double));
+    double *E = (double *)calloc(K, sizeof(double));
+    double *pi = (double *)calloc(K, sizeof(double));
+    uint8_t *z = (uint8_t *)calloc(N, 1);
+    if (!psi || !L || !E || !pi || !z) return 1;
+    for (int64_t b = 0; b < B; ++b) loss[b] = 0.0;
+
+    for (int32_t t = 1; t <= T; ++t) {
+        const int64_t t_abs = ++s->counters[0];
+        ++s->counters[1];
+        const int64_t slot = t_abs % D1;
+        for (int64_t b = 0; b < B; ++b) {
+            if (t > lengths[b]) continue;
+            double *v = s->v + b * N, *a = s->a + b * N;
+            double *psi_prev = s->psi_prev + b * N;
+            int32_t *ref = s->ref + b * N;
+            uint8_t *z_prev = s->z_prev + b * N;
+            double *ring = s->ring + b * D1 * N;
+            uint8_t *hist = s->src_hist + b * D1 * NS;
+            double *y = s->y + b * K, *zk = s->zk + b * N;
+            const int64_t bt = b * (int64_t)T + (t - 1);
+
+            /* sources that spike at this step: inputs from the raster */
+            memset(hist + slot * NS, 0, NS);
+            for (int64_t q = x_ptr[bt]; q < x_ptr[bt + 1]; ++q)
+                hist[slot * NS + x_ids[q]] = 1;
+
+            /* neurons */
+            for (int64_t j = 0; j < N; ++j) {
+                double I = ring[slot * N + j];
+                ring[slot * N + j] = 0.0;
+                if (c->drive_weight != 0.0)
+                    I += c->drive_weight * drive_count(c, b, t_abs, j);
+                a[j] = c->rho * a[j] + z_prev[j];
+                double vth = c->v_th + c->beta_a * a[j];
+                v[j] = c->alpha * v[j] + I - z_prev[j] * vth;
+                int refractory = ref[j] > 0;
+                double m = v[j] - vth;
+                if (forced)
+                    z[j] = forced[bt * N + j];
+                else
+                    z[j] = (!refractory && m > 0.0) ? 1 : 0;
+                double h = 1.0 - c->beta_sg * fabs(m);
+                psi[j] = refractory ? 0.0 : c->gamma * (h > 0.0 ? h : 0.0);
+                if (refractory) ref[j] -= 1;
+                if (z[j]) ref[j] = c->t_ref;
+                raster[bt * N + j] = z[j];
+                margin[bt * N + j] = m;
+                if (psi_rec) psi_rec[bt * N + j] = psi[j];
+                hist[slot * NS + NI + j] = z[j];
+            }
+
+            /* readout, error signal, loss */
+            const double win = window ? (double)window[bt] : 1.0;
+            const double *tgt = targets + bt * K;
+            for (int64_t k = 0; k < K; ++k) {
+                double acc = 0.0;
+                for (int64_t j = 0; j < N; ++j)
+                    if (z[j]) acc += s->w_out[j * K + k];
+                y[k] = c->kappa * y[k] + acc;
+                y_rec[bt * K + k] = y[k];
+            }
+            if (c->loss == 0) {
+                for (int64_t k = 0; k < K; ++k) {
+                    double diff = y[k] - tgt[k];
+                    E[k] = win * diff;
+                    loss[b] += 0.5 * win * diff * diff;
+                }
+            } else {
+                double mx = y[0];
+                for (int64_t k = 1; k < K; ++k) mx = y[k] > mx ? y[k] : mx;
+                double den = 0.0;
+                for (int64_t k = 0; k < K; ++k) den += exp(y[k] - mx);
+                for (int64_t k = 0; k < K; ++k) {
+                    pi[k] = exp(y[k] - mx) / den;
+                    E[k] = win * (pi[k] - tgt[k]);
+                    loss[b] -= win * tgt[k] * ((y[k] - mx) - log(den));
+                }
+            }
+            /* learning signal */
+            const double *Bm = c->feedback ? s->fb : s->w_out;
+            for (int64_t j = 0; j < N; ++j) {
+                double acc = 0.0;
+                for (int64_t k = 0; k < K; ++k) acc += Bm[j * K + k] * E[k];
+                L[j] = acc;
+                if (L_rec) L_rec[bt * N + j] = acc;
+            }
+
+            /* eligibility traces and gradients, every synapse, every step */
+            for (int64_t i = 0; i < NS; ++i) {
+                for (int64_t q = s->ptr[i]; q < s->ptr[i + 1]; ++q) {
+                    const int64_t j = s->col[q];
+                    const int64_t d = s->delay[q];
+                    double arrive = 0.0;
+                    if (t_abs - d >= 1) arrive = hist[((t_abs - d) % D1) * NS + i];
+                    s->g[q] += oracle_eligibility_step(
+                        c->alpha, c->rho, c->beta_a, c->kappa_e, psi_prev[j],
+                        psi[j], L[j], arrive, s->zbar + b * NNZ + q,
+                        s->epsa + b * NNZ + q, s->ebar + b * NNZ + q);
+                }
+            }
+            for (int64_t j = 0; j < N; ++j) {
+                zk[j] = c->kappa * zk[j] + z[j];
+                if (s->out_mask[j])
+                    for (int64_t k = 0; k < K; ++k) s->g_out[j * K + k] += E[k] * zk[j];
+            }
+            for (int64_t j = 0; j < N; ++j) {
+                psi_prev[j] = psi[j];
+                z_prev[j] = z[j];
+            }
+
+            /* transmission of this step's spikes with the current weights */
+            for (int64_t i = 0; i < NS; ++i) {
+                if (!hist[slot * NS + i]) continue;
+                for (int64_t q = s->ptr[i]; q < s->ptr[i + 1]; ++q) {
+                    const int64_t tgt_slot = (t_abs + s->delay[q]) % D1;
+                    ring[tgt_slot * N + s->col[q]] += s->w[q];
+                }
+            }
+        }
+
+        /* end of an update window: gradient descent with the batch mean */
+        if (s->counters[1] % U == 0) {
+            for (int64_t q = 0; q < NNZ; ++q) {
+                double gm = s->g[q] / (double)B;
+                s->w[q] -= c->lr * gm;
+                s->grad_acc[q] += gm;
+                s->g[q] = 0.0;
+            }
+            for (int64_t j = 0; j < N; ++j) {
+                if (!s->out_mask[j]) continue;
+                for (int64_t k = 0; k < K; ++k) {
+                    double gm = s->g_out[j * K + k] / (double)B;
+                    s->w_out[j * K + k] -= c->lr * gm;
+                    s->grad_out_acc[j * K + k] += gm;
+                    s->g_out[j * K + k] = 0.0;
+                }
+            }
+        }
+    }
+    free(psi); free(L); free(E); free(pi); free(z);
+    return 0;
+}
