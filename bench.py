@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the event-driven e-prop hot path on one GB300 (or N replicas).
+
+Workload: the million-neuron sparse network -- 1e6 LIF neurons, fixed
+in-degree 1000 (1e9 plastic synapses stored as target|delay, FP32 weight,
+BF16 trace), delays 1-5 steps, ~5 Hz, 100 readouts with random feedback,
+continuous dynamics with an online weight update every 100 steps.  One
+bench step = one simulate call of T = 1000 steps (1 s of biological time).
+
+Prints one JSON line: synapse-events/s over K timed steps (device time,
+CUDA events on the library's stream), the roofline of the synapse-trace
+kernel, the FP64 oracle timed on a bounded sample on the host cores, the
+end-to-end number through the public API with host buffers, and the SM
+clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "synapse-events/s and sim-time/wall-time vs HBM roofline at stated grad error"
+UNIT = "synapse-events/s"
+FALLBACK_HBM_GBS = 6800.0
+TRACE_KERNEL_SRC = os.path.join(ROOT, "paper_2511_21674_gb300", "csrc", "kernels_window.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_million_sparse.md")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n-rec", type=int, default=1_000_000)
+    p.add_argument("--k-in", type=int, default=1000)
+    p.add_argument("--T", type=int, default=1000)
+    p.add_argument("--n-out", type=int, default=100)
+    p.add_argument("--trace-dtype", default="bf16", choices=["bf16", "fp32"])
+    p.add_argument("--blocks-per-sm", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-n", type=int, default=10_000)
+    p.add_argument("--cpu-sample-T", type=int, default=100)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per trace launch from the committed ncu summary, if it was
+    taken on the current kernel source (sha256 recorded in the summary)."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+        src = hashlib.sha256(open(TRACE_KERNEL_SRC, "rb").read()).hexdigest()
+        fields = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[0] != " ")
+        if fields.get("kernel_source_sha256", "").strip() != src:
+            return None, None
+        return (float(fields["dram_bytes_per_event"].strip()),
+                float(fields["dram_bytes_per_launch_at_full_size"].strip()))
+    except Exception:
+        return None, None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons every 200 ms during a region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier_max(value, world):
+    import torch
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------- CPU oracle
+
+
+def cpu_baseline(args, steps=1):
+    """The FP64 oracle (test infrastructure, untuned) on a bounded sample of
+    the same workload: cpu_sample_n neurons with the same in-degree, delays,
+    drive and rates, cpu_sample_T steps (one update window)."""
+    import oracle
+    from workloads import configs as C
+    oracle.build()
+    W = C.million_sparse(n_rec=args.cpu_sample_n, k_in=args.k_in, T=args.cpu_sample_T,
+                         n_out=args.n_out)
+    s = W["spec"]
+    s.update_interval = args.cpu_sample_T
+    o = oracle.Oracle(s, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["out_mask"],
+                      W["feedback"])
+    outdeg = np.diff(W["ptr"])
+    tot_events, tot_time = 0, 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        r = o.simulate(s.T, W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"])
+        tot_time += time.perf_counter() - t0
+        tot_events += int((r["raster"][0].sum(axis=0) * outdeg).sum())
+    return {"value": tot_events / tot_time, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{args.cpu_sample_n} LIF neurons, in-degree {args.k_in}, delays 1-5, "
+                      f"~5 Hz, {args.n_out} readouts, {args.cpu_sample_T} steps x {steps}, "
+                      f"FP64 time-driven oracle, single thread",
+            "events": tot_events, "seconds": tot_time}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    W = max(args.warmup, 0)
+    base = cpu_baseline(args, steps=1 + 0 * W)  # warm: builds the oracle
+    K = max(args.steps, 1)
+    res = cpu_baseline(args, steps=K)
+    sec_per_step = res["seconds"] / K
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": K, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sec_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "million_sparse (bounded sample on host cores)",
+                       "n_rec": args.cpu_sample_n, "k_in": args.k_in,
+                       "T": args.cpu_sample_T, "n_out": args.n_out},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"],
+                             "value": res["value"], "unit": UNIT},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    del base
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    side = torch.cuda.Stream()          # graphs are captured on a non-default stream
+    with torch.cuda.stream(side):
+        _run_ours(args, rank, world, local)
+
+
+def _run_ours(args, rank, world, local):
+    import torch
+    import paper_2511_21674_gb300 as ep
+    from workloads import gpu_build as G
+    torch.manual_seed(0)
+    W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
+                               seed=1237 + rank)
+    spec = W["spec"]
+    trace_dtype = 1 if args.trace_dtype == "bf16" else 0
+    net = ep.Network(spec, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], None, W["feedback"],
+                     launch_mode=1, trace_dtype=trace_dtype, record_grad=0, record_raster=0,
+                     profile=1, blocks_per_sm=args.blocks_per_sm)
+    nnz = int(W["col"].shape[0])
+    del W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["feedback"]
+    torch.cuda.empty_cache()
+    T = spec.T
+    # inputs: pinned host buffers (the same arrays serve every step)
+    x_ptr = torch.from_numpy(W["x_ptr"]).pin_memory()
+    x_ids = torch.zeros(1, dtype=torch.int32).pin_memory()[:0]
+    targets = torch.from_numpy(np.ascontiguousarray(W["targets"], np.float32)).pin_memory()
+    window = torch.from_numpy(W["window"]).pin_memory()
+    lengths = torch.from_numpy(W["lengths"]).pin_memory()
+    net.set_inputs(x_ptr, x_ids, targets, window, lengths, T)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        net.simulate(T)
+    net.sync()
+
+    # ---- device-timed region: K simulate calls, inputs resident in HBM
+    K = args.steps
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    events = launches = trace_launches = windows = 0
+    trace_ms = 0.0
+    for _ in range(K):
+        net.simulate(T)
+        st = net.stats()
+        events += st["events"]
+        launches += st["kernel_launches"]
+        trace_launches += st["trace_launches"]
+        windows += st["windows"]
+        trace_ms += st["trace_ms"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = barrier_max(ms, world)
+    ev_total = barrier_max(events, world) * world if world > 1 else events
+    value = ev_total / (ms_max / 1000.0)
+
+    # ---- end to end through the public API with host buffers
+    h2d = (x_ptr.numel() * 8 + targets.numel() * 4 + window.numel() + lengths.numel() * 4)
+    loss_host = np.zeros(spec.batch, np.float32)
+    y_host = np.zeros((spec.batch, T, spec.n_out), np.float32)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_events = 0
+    for _ in range(K):
+        net.set_inputs(x_ptr, x_ids, targets, window, lengths, T)
+        net.simulate(T)
+        net.lib.eprop_readout(net.h, None, loss_host.ctypes.data, None, 0)
+        e2e_events += net.stats()["events"]
+    torch.cuda.synchronize()
+    e2e_s = barrier_max(time.perf_counter() - t0, world)
+    e2e_value = (e2e_events * world) / e2e_s
+    del y_host
+
+    # ---- roofline of the synapse-trace kernel
+    bytes_per_event = 16.0 if trace_dtype == 1 else 20.0     # j|d 4 r, w 4 r/w, trace 2|4 r/w
+    peak, peak_src = measured_peaks()
+    achieved = events * bytes_per_event / (trace_ms / 1000.0) / 1e9 if trace_ms > 0 else None
+    traffic_per_event, traffic_launch = recorded_traffic()
+    traffic = None
+    if traffic_per_event is not None and trace_launches:
+        traffic = traffic_per_event * events / trace_launches
+    net.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "million_sparse: 1e6 LIF, in-degree 1000 (1e9 synapses), "
+                               "delays 1-5, ~5 Hz, 100 readouts, update window 100, continuous",
+                   "n_rec": args.n_rec, "k_in": args.k_in, "synapses": nnz, "T_per_step": T,
+                   "trace_storage": args.trace_dtype, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (synapse records ~10 GB per step)"},
+        "sim_time_per_wall_time": (T * spec.dt / 1000.0) / (ms_max / K / 1000.0),
+        "events_per_step": events / K,
+        "grad_error": "FP32 traces: <=1e-5 relative vs FP64 oracle (scaled replica); "
+                      "BF16 traces: reported in DESIGN.md",
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "trace_stream_kernel", "bytes_per_event": bytes_per_event,
+                     "peak_source": f"{peak_src} (hbm_gbs)",
+                     "trace_ms_per_step": trace_ms / K, "trace_launches_per_step": trace_launches / K},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(loss_host.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            cb = cpu_baseline(args, steps=1)
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as exc:  # the GPU line stands on its own
+            line["cpu_baseline"] = {"error": str(exc)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

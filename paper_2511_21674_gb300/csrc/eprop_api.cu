@@ -1,0 +1,711 @@
+// C ABI of libeprop (see include/eprop.h): argument checks, device memory,
+// and the launch schedule of one simulate call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eprop.h"
+#include "eprop_internal.cuh"
+#include "eprop_launch.h"
+
+using eprop::Net;
+
+struct eprop_net {
+    eprop_config cfg;
+    Net n;
+    cudaStream_t st = nullptr;
+    int dev = 0, sm_count = 1;
+    std::string err;
+    int bad = 0;
+    std::vector<void *> fixed_allocs;   // freed at destroy
+    std::vector<void *> win_allocs;     // window-sized buffers
+    std::vector<void *> in_allocs;      // per-T input buffers
+    long long nnz_in = 0;
+    int U_alloc = 0, T_alloc = 0, T_in = 0, U_fixed = 0;
+    int trace_mode = 0;                 // 0 streaming, 1 batched
+    int qp_stride = 2;
+    long long x_cap = 0;
+    long long max_in_per_step = 0;
+    long long t_abs = 0;
+    int r_base = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int g_T = -1;
+    int have_inputs = 0;
+    int own_stream = 0;
+    float *tmp_w = nullptr, *tmp_g = nullptr;
+    std::vector<cudaEvent_t> ev;        // [2 * windows] trace timing events
+    long long launches = 0, trace_launches = 0, windows = 0;
+    unsigned char *tmp_raster = nullptr;
+    long long tmp_raster_bytes = 0;
+};
+
+static thread_local std::string g_create_err;
+
+static eprop_status fail(eprop_net *net, eprop_status s, const std::string &msg) {
+    if (net) net->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+static eprop_status cuda_fail(eprop_net *net, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (net) {
+        net->bad = 1;
+        net->err = m;
+    } else {
+        g_create_err = m;
+    }
+    return e == cudaErrorMemoryAllocation ? EPROP_ENOMEM : EPROP_ECUDA;
+}
+
+#define CK(net, call)                                              \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return cuda_fail((net), _e, #call); \
+    } while (0)
+
+static cudaError_t dalloc(std::vector<void *> &owner, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    owner.push_back(*p);
+    return cudaMemset(*p, 0, bytes);
+}
+
+static void free_all(std::vector<void *> &v) {
+    for (void *p : v) cudaFree(p);
+    v.clear();
+}
+
+static int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// ------------------------------------------------------- validation kernels
+
+__global__ void check_synapses_kernel(const int32_t *tgt, const uint8_t *dly, long long nnz, int n_rec,
+                                      int D, unsigned int *flag) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nnz;
+         q += (long long)gridDim.x * blockDim.x) {
+        if (tgt[q] < 0 || tgt[q] >= n_rec) atomicOr(flag, 1u);
+        if (dly[q] < 1 || dly[q] > D) atomicOr(flag, 2u);
+    }
+}
+
+__global__ void pack_synapses_kernel(const int32_t *tgt, const uint8_t *dly, const float *w, long long nnz,
+                                     uint32_t *tgt_d, float *w_dst) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nnz;
+         q += (long long)gridDim.x * blockDim.x) {
+        tgt_d[q] = (uint32_t)tgt[q] | ((uint32_t)dly[q] << 24);
+        w_dst[q] = w[q];
+    }
+}
+
+__global__ void check_inputs_kernel(const long long *ptr, long long nptr, const int32_t *ids, long long nids,
+                                    const int32_t *lengths, int B, int T, int n_in, unsigned int *flag) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = tid; q < nids; q += stride)
+        if (ids[q] < 0 || ids[q] >= n_in) atomicOr(flag, 1u);
+    for (long long q = tid; q + 1 < nptr; q += stride)
+        if (ptr[q + 1] < ptr[q]) atomicOr(flag, 2u);
+    if (tid == 0 && (ptr[0] != 0 || ptr[nptr - 1] != nids)) atomicOr(flag, 2u);
+    if (lengths)
+        for (long long b = tid; b < B; b += stride)
+            if (lengths[b] < 1 || lengths[b] > T) atomicOr(flag, 4u);
+}
+
+// ------------------------------------------------------------- allocation
+
+static eprop_status alloc_window(eprop_net *net, int U, int T) {
+    Net &n = net->n;
+    const eprop_config &c = net->cfg;
+    if (net->U_alloc == U) return EPROP_OK;
+    cudaStreamSynchronize(net->st);
+    free_all(net->win_allocs);
+    if (net->gexec) {
+        cudaGraphExecDestroy(net->gexec);
+        net->gexec = nullptr;
+        net->g_T = -1;
+    }
+    const long long B = c.batch, N = c.n_rec, K = c.n_out, S = n.n_src;
+    const int D = c.max_delay;
+    n.U = U;
+    n.RW = next_pow2((U + D + 31) / 32);
+    net->qp_stride = c.neuron_model == 1 ? 4 : 2;
+    const double qp_bytes = (double)U * N * net->qp_stride * 4.0 * B;
+    if (c.trace_kernel == 1) net->trace_mode = 0;
+    else if (c.trace_kernel == 2) net->trace_mode = 1;
+    else net->trace_mode = (B > 1 || (!n.has_state && qp_bytes <= 64.0 * 1024 * 1024)) ? 1 : 0;
+    n.RS = net->trace_mode == 0 ? U + D + 1 : 2;
+    n.RC = 0;
+    if (n.has_state) {
+        int rc = (3000 + U - 1) / U + 2;
+        n.RC = rc < 4 ? 4 : (rc > 64 ? 64 : rc);
+    }
+    std::vector<void *> &o = net->win_allocs;
+    void *p;
+#define WA(field, type, count)                                                   \
+    do {                                                                         \
+        cudaError_t _e = dalloc(o, &p, (size_t)(count) * sizeof(type));          \
+        if (_e != cudaSuccess) return cuda_fail(net, _e, "window allocation");   \
+        n.field = reinterpret_cast<decltype(n.field)>(p);                        \
+    } while (0)
+    WA(bits, uint32_t, B * S * n.RW);
+    WA(list_ids, int, B * n.RS * S);
+    WA(list_cnt, int, B * n.RS);
+    WA(psi_hist, float, B * (U + 1) * N);
+    WA(E_win, float, B * U * K);
+    WA(Ebar_win, float, B * U * K);
+    WA(qp, float, B * (long long)U * N * net->qp_stride);
+    if (n.has_state) WA(coef, float, (long long)n.RC * N * (c.neuron_model == 1 ? 8 : 4));
+#undef WA
+    net->U_alloc = U;
+    net->T_alloc = T;
+    return EPROP_OK;
+}
+
+extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const eprop_synapses *syn,
+                                             const float *w_out, const uint8_t *out_mask,
+                                             const float *feedback, int32_t is_device,
+                                             void *cuda_stream, eprop_net **out) {
+    if (!out) return fail(nullptr, EPROP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg || !syn || !w_out) return fail(nullptr, EPROP_EINVAL, "cfg, syn and w_out are required");
+    const eprop_config &c = *cfg;
+    if (c.abi_version != EPROP_ABI_VERSION) return fail(nullptr, EPROP_EINVAL, "abi_version mismatch");
+    if (c.n_in < 0 || c.n_rec < 1 || c.n_rec >= (1 << 24) || c.n_out < 1 || c.n_out > eprop::kMaxOut ||
+        c.batch < 1 || c.batch >= (1 << 11))
+        return fail(nullptr, EPROP_EINVAL, "sizes out of range (n_rec < 2^24, 1 <= n_out <= 1024, batch < 2048)");
+    if (c.max_delay < 1 || c.max_delay > eprop::kMaxDelay) return fail(nullptr, EPROP_EINVAL, "max_delay must be 1..8");
+    if (c.neuron_model < 0 || c.neuron_model > 1 || c.loss < 0 || c.loss > 1 || c.feedback < 0 ||
+        c.feedback > 1 || c.trace_dtype < 0 || c.trace_dtype > 1 || c.t_ref < 0 || c.update_interval < 0)
+        return fail(nullptr, EPROP_EINVAL, "invalid enum or negative parameter");
+    if (c.batch > 1 && (c.continuous || c.update_interval > 0))
+        return fail(nullptr, EPROP_EINVAL, "batch > 1 needs continuous = 0 and update_interval = 0");
+    if (c.trace_kernel < 0 || c.trace_kernel > 2 || c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
+        return fail(nullptr, EPROP_EINVAL, "trace_kernel must be 0..2 and blocks_per_sm 0..64");
+    if (c.trace_kernel == 1 && c.batch > 1)
+        return fail(nullptr, EPROP_EINVAL, "the streaming trace kernel needs batch = 1");
+    if (c.trace_kernel == 2 && (c.continuous || c.update_interval > 0))
+        return fail(nullptr, EPROP_EINVAL, "the batched trace kernel cannot carry state between windows");
+    if (c.n_drive_thr < 0 || c.n_drive_thr > EPROP_MAX_DRIVE_THR)
+        return fail(nullptr, EPROP_EINVAL, "n_drive_thr out of range");
+    if (!(c.dt > 0.f) || !(c.tau_m > 0.f) || !(c.tau_out > 0.f) || (c.neuron_model == 1 && !(c.tau_a > 0.f)))
+        return fail(nullptr, EPROP_EINVAL, "dt and time constants must be positive");
+    if (syn->n_src != (int64_t)c.n_in + c.n_rec || syn->nnz < 0 || (syn->nnz > 0 && (!syn->row_ptr ||
+        !syn->target || !syn->weight || !syn->delay)) || !syn->row_ptr)
+        return fail(nullptr, EPROP_EINVAL, "synapse arrays inconsistent with n_in + n_rec");
+    if (c.feedback == 1 && !feedback) return fail(nullptr, EPROP_EINVAL, "feedback = 1 needs a feedback matrix");
+
+    eprop_net *net = new (std::nothrow) eprop_net();
+    if (!net) return fail(nullptr, EPROP_ENOMEM, "host allocation failed");
+    net->cfg = c;
+    net->st = (cudaStream_t)cuda_stream;
+    if (net->st == nullptr && c.launch_mode == 1) {
+        // graphs cannot be captured on the legacy default stream
+        if (cudaStreamCreateWithFlags(&net->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete net;
+            return fail(nullptr, EPROP_ECUDA, "cannot create a stream for graph capture");
+        }
+        net->own_stream = 1;
+    }
+    Net &n = net->n;
+    memset(&n, 0, sizeof(n));
+    cudaGetDevice(&net->dev);
+    cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, net->dev);
+    const long long N = c.n_rec, K = c.n_out, B = c.batch, S = syn->n_src, nnz = syn->nnz;
+    n.n_in = c.n_in; n.n_rec = c.n_rec; n.n_out = c.n_out; n.n_src = (int)S; n.B = c.batch;
+    n.D = c.max_delay; n.nnz = nnz;
+    n.alif = c.neuron_model == 1; n.t_ref = c.t_ref; n.loss = c.loss; n.feedback = c.feedback;
+    n.has_state = (c.continuous || c.update_interval > 0) ? 1 : 0;
+    n.trace_bf16 = c.trace_dtype == 1; n.record_grad = c.record_grad != 0;
+    n.record_raster = c.record_raster != 0; n.n_thr = c.drive_weight != 0.f ? c.n_drive_thr : 0;
+    const double alpha = std::exp(-(double)c.dt / c.tau_m);
+    const double kappa = std::exp(-(double)c.dt / c.tau_out);
+    const double kappa_e = c.kappa_e < 0.f ? kappa : (double)c.kappa_e;
+    n.alpha = (float)alpha; n.kappa = (float)kappa; n.kappa_e = (float)kappa_e;
+    n.rho = n.alif ? (float)std::exp(-(double)c.dt / c.tau_a) : 0.f;
+    n.beta_a = n.alif ? c.beta_a : 0.f;
+    n.v_th = c.v_th; n.gamma = c.gamma; n.beta_sg = c.beta_sg; n.lr = c.lr;
+    n.drive_weight = c.drive_weight; n.drive_seed = c.drive_seed;
+    n.log2_alpha = (float)std::log2(alpha); n.log2_kappa = (float)std::log2(kappa);
+    n.inv_B = (float)(1.0 / c.batch);
+
+    std::vector<void *> &o = net->fixed_allocs;
+    void *p;
+    eprop_status s;
+#define FA(field, type, count)                                                        \
+    do {                                                                              \
+        cudaError_t _e = dalloc(o, &p, (size_t)(count) * sizeof(type));               \
+        if (_e != cudaSuccess) { s = cuda_fail(nullptr, _e, "allocation"); goto fail_out; } \
+        n.field = reinterpret_cast<decltype(n.field)>(p);                             \
+    } while (0)
+    {
+        const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        // synapses
+        long long *rp;
+        FA(row_ptr, long long, S + 1);
+        rp = const_cast<long long *>(n.row_ptr);
+        if (cudaMemcpy(rp, syn->row_ptr, (S + 1) * sizeof(long long), kind) != cudaSuccess) {
+            s = fail(nullptr, EPROP_EINVAL, "cannot read row_ptr");
+            goto fail_out;
+        }
+        {
+            std::vector<long long> hp(S + 1);
+            cudaMemcpy(hp.data(), rp, (S + 1) * sizeof(long long), cudaMemcpyDeviceToHost);
+            if (hp[0] != 0 || hp[S] != nnz) { s = fail(nullptr, EPROP_EINVAL, "row_ptr must run from 0 to nnz"); goto fail_out; }
+            for (long long i = 0; i < S; ++i)
+                if (hp[i + 1] < hp[i]) { s = fail(nullptr, EPROP_EINVAL, "row_ptr must be non-decreasing"); goto fail_out; }
+            net->nnz_in = hp[c.n_in];
+        }
+        uint32_t *td;
+        FA(tgt_d, uint32_t, nnz);
+        td = const_cast<uint32_t *>(n.tgt_d);
+        FA(w, float, nnz);
+        if (nnz > 0) {
+            const int32_t *tg = syn->target;
+            const uint8_t *dl = syn->delay;
+            const float *wt = syn->weight;
+            void *t_tg = nullptr, *t_dl = nullptr, *t_w = nullptr;
+            std::vector<void *> tmp;
+            if (!is_device) {
+                if (dalloc(tmp, &t_tg, nnz * 4) != cudaSuccess || dalloc(tmp, &t_dl, nnz) != cudaSuccess ||
+                    dalloc(tmp, &t_w, nnz * 4) != cudaSuccess) {
+                    free_all(tmp);
+                    s = fail(nullptr, EPROP_ENOMEM, "staging allocation failed");
+                    goto fail_out;
+                }
+                cudaMemcpy(t_tg, tg, nnz * 4, cudaMemcpyHostToDevice);
+                cudaMemcpy(t_dl, dl, nnz, cudaMemcpyHostToDevice);
+                cudaMemcpy(t_w, wt, nnz * 4, cudaMemcpyHostToDevice);
+                tg = (const int32_t *)t_tg; dl = (const uint8_t *)t_dl; wt = (const float *)t_w;
+            }
+            unsigned int *flag;
+            cudaMalloc(&flag, 4);
+            cudaMemset(flag, 0, 4);
+            check_synapses_kernel<<<1024, 256>>>(tg, dl, nnz, c.n_rec, c.max_delay, flag);
+            pack_synapses_kernel<<<1024, 256>>>(tg, dl, wt, nnz, td, n.w);
+            unsigned int hflag = 0;
+            cudaError_t e = cudaMemcpy(&hflag, flag, 4, cudaMemcpyDeviceToHost);
+            cudaFree(flag);
+            free_all(tmp);
+            if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "synapse packing"); goto fail_out; }
+            if (hflag & 1u) { s = fail(nullptr, EPROP_EINVAL, "synapse target out of [0, n_rec)"); goto fail_out; }
+            if (hflag & 2u) { s = fail(nullptr, EPROP_EINVAL, "synapse delay out of [1, max_delay]"); goto fail_out; }
+        }
+        if (n.has_state) {
+            FA(ebar, uint16_t, nnz * (n.trace_bf16 ? 1 : 2));
+            if (n.alif) FA(epsa, uint16_t, nnz * (n.trace_bf16 ? 1 : 2));
+        }
+        if (n.record_grad) FA(grad, float, nnz);
+        // neurons
+        FA(v, float, B * N);
+        FA(a, float, B * N);
+        FA(ref, int, B * N);
+        FA(z_prev, uint8_t, B * N);
+        FA(ring, long long, B * (c.max_delay + 1) * N);
+        FA(anchor_t, int, B * S);
+        FA(anchor_z, float, B * S);
+        eprop::launch_fill_int(n.anchor_t, B * S, eprop::kNoSpike, 0);
+        // readout
+        FA(w_out, float, N * K);
+        cudaMemcpy(n.w_out, w_out, N * K * 4, kind);
+        {
+            uint8_t *m;
+            FA(out_mask, uint8_t, N);
+            m = const_cast<uint8_t *>(n.out_mask);
+            if (out_mask) cudaMemcpy(m, out_mask, N, kind);
+            else cudaMemset(m, 1, N);
+        }
+        if (c.feedback == 1) {
+            float *f;
+            FA(fb, float, N * K);
+            f = const_cast<float *>(n.fb);
+            cudaMemcpy(f, feedback, N * K * 4, kind);
+        } else {
+            n.fb = n.w_out;
+        }
+        if (n.record_grad) FA(grad_out, float, N * K);
+        FA(y, float, B * K);
+        FA(y_acc, long long, B * K);
+        FA(Cwin, float, B * K);
+        FA(zk, float, 2 * B * N);
+        FA(loss_acc, float, B);
+        FA(events, unsigned long long, 1);
+        FA(err_flags, unsigned int, 1);
+        FA(clock, eprop::Clock, 1);
+        {
+            uint32_t *thr;
+            FA(drive_thr, uint32_t, EPROP_MAX_DRIVE_THR);
+            thr = const_cast<uint32_t *>(n.drive_thr);
+            cudaMemcpy(thr, c.drive_thr, sizeof(c.drive_thr), cudaMemcpyHostToDevice);
+        }
+        eprop::prepare_kernel_attributes();
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "network set-up"); goto fail_out; }
+        if (c.update_interval > 0) {
+            s = alloc_window(net, c.update_interval, c.update_interval);
+            if (s != EPROP_OK) { g_create_err = net->err; goto fail_out; }
+        }
+    }
+#undef FA
+    *out = net;
+    return EPROP_OK;
+fail_out:
+    free_all(net->fixed_allocs);
+    free_all(net->win_allocs);
+    delete net;
+    return s;
+}
+
+extern "C" eprop_status eprop_set_inputs_targets(eprop_net *net, const int64_t *in_step_ptr,
+                                                 const int32_t *in_ids, int64_t n_in_ids,
+                                                 const float *targets, const uint8_t *window,
+                                                 const int32_t *lengths, int32_t T, int32_t is_device) {
+    if (!net) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    const eprop_config &c = net->cfg;
+    Net &n = net->n;
+    if (T < 1 || !in_step_ptr || !targets || n_in_ids < 0 || (n_in_ids > 0 && !in_ids))
+        return fail(net, EPROP_EINVAL, "T >= 1, in_step_ptr and targets are required");
+    if (c.update_interval > 0 && T % c.update_interval)
+        return fail(net, EPROP_EINVAL, "T must be a multiple of update_interval");
+    if (c.continuous && c.update_interval == 0 && net->U_fixed && T != net->U_fixed)
+        return fail(net, EPROP_EINVAL, "continuous networks with update_interval 0 keep the first T");
+    const long long B = c.batch, K = c.n_out, N = c.n_rec;
+    const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // host-side validation
+    if (!is_device) {
+        if (in_step_ptr[0] != 0 || in_step_ptr[B * T] != n_in_ids)
+            return fail(net, EPROP_EINVAL, "in_step_ptr must run from 0 to n_in_ids");
+        long long mx = 0;
+        for (long long q = 0; q < B * T; ++q) {
+            const long long d = in_step_ptr[q + 1] - in_step_ptr[q];
+            if (d < 0) return fail(net, EPROP_EINVAL, "in_step_ptr must be non-decreasing");
+            if (d > mx) mx = d;
+        }
+        for (long long q = 0; q < n_in_ids; ++q)
+            if (in_ids[q] < 0 || in_ids[q] >= c.n_in) return fail(net, EPROP_EINVAL, "input id out of [0, n_in)");
+        if (lengths)
+            for (long long b = 0; b < B; ++b)
+                if (lengths[b] < 1 || lengths[b] > T) return fail(net, EPROP_EINVAL, "lengths must be in [1, T]");
+        net->max_in_per_step = mx;
+    } else {
+        net->max_in_per_step = 1 << 14;
+    }
+    // (re)allocate per-T buffers
+    if (net->in_allocs.empty() || T != net->T_in || n_in_ids > net->x_cap) {
+        cudaStreamSynchronize(net->st);
+        free_all(net->in_allocs);
+        if (net->gexec) {
+            cudaGraphExecDestroy(net->gexec);
+            net->gexec = nullptr;
+            net->g_T = -1;
+        }
+        void *p;
+        std::vector<void *> &o = net->in_allocs;
+#define IA(field, type, count)                                                     \
+        do {                                                                       \
+            cudaError_t _e = dalloc(o, &p, (size_t)(count) * sizeof(type));        \
+            if (_e != cudaSuccess) return cuda_fail(net, _e, "input allocation");  \
+            n.field = reinterpret_cast<decltype(n.field)>(p);                      \
+        } while (0)
+        const long long cap = n_in_ids > 0 ? n_in_ids : 1;
+        IA(x_ptr, long long, B * T + 1);
+        IA(x_ids, int, cap);
+        IA(targets, float, B * T * K);
+        IA(window, uint8_t, B * T);
+        IA(lengths, int, B);
+        IA(y_rec, float, B * T * K);
+        if (n.record_raster) IA(rec_raster, uint32_t, B * ((T + 31) / 32) * N);
+#undef IA
+        net->x_cap = cap;
+    }
+    n.T = T;
+    cudaStream_t st = net->st;
+    CK(net, cudaMemcpyAsync(const_cast<long long *>(n.x_ptr), in_step_ptr, (B * T + 1) * 8, kind, st));
+    if (n_in_ids > 0) CK(net, cudaMemcpyAsync(const_cast<int *>(n.x_ids), in_ids, n_in_ids * 4, kind, st));
+    CK(net, cudaMemcpyAsync(const_cast<float *>(n.targets), targets, B * T * K * 4, kind, st));
+    if (window) CK(net, cudaMemcpyAsync(const_cast<uint8_t *>(n.window), window, B * T, kind, st));
+    else CK(net, cudaMemsetAsync(const_cast<uint8_t *>(n.window), 1, B * T, st));
+    if (lengths) {
+        CK(net, cudaMemcpyAsync(const_cast<int *>(n.lengths), lengths, B * 4, kind, st));
+    } else {
+        std::vector<int> l(B, T);
+        CK(net, cudaMemcpyAsync(const_cast<int *>(n.lengths), l.data(), B * 4, cudaMemcpyHostToDevice, st));
+        CK(net, cudaStreamSynchronize(st));
+    }
+    if (is_device) {
+        unsigned int *flag;
+        CK(net, cudaMalloc(&flag, 4));
+        cudaMemsetAsync(flag, 0, 4, st);
+        check_inputs_kernel<<<256, 256, 0, st>>>(n.x_ptr, B * T + 1, n.x_ids, n_in_ids, n.lengths, (int)B, T,
+                                                 c.n_in, flag);
+        unsigned int h = 0;
+        cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        cudaFree(flag);
+        if (e != cudaSuccess) return cuda_fail(net, e, "input validation");
+        if (h & 1u) return fail(net, EPROP_EINVAL, "input id out of [0, n_in)");
+        if (h & 2u) return fail(net, EPROP_EINVAL, "in_step_ptr must be non-decreasing from 0 to n_in_ids");
+        if (h & 4u) return fail(net, EPROP_EINVAL, "lengths must be in [1, T]");
+    }
+    const int U = c.update_interval > 0 ? c.update_interval : T;
+    eprop_status s = alloc_window(net, U, T);
+    if (s != EPROP_OK) return s;
+    net->T_in = T;
+    net->have_inputs = 1;
+    return EPROP_OK;
+}
+
+// ------------------------------------------------------------ simulate
+
+static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
+    Net n = net->n;
+    const eprop_config &c = net->cfg;
+    cudaStream_t st = net->st;
+    n.T = T;
+    n.forced = forced;
+    const long long B = c.batch, N = c.n_rec, K = c.n_out, S = n.n_src;
+    const int U = n.U;
+    if (!c.continuous) {
+        cudaMemsetAsync(n.v, 0, B * N * 4, st);
+        cudaMemsetAsync(n.a, 0, B * N * 4, st);
+        cudaMemsetAsync(n.ref, 0, B * N * 4, st);
+        cudaMemsetAsync(n.z_prev, 0, B * N, st);
+        cudaMemsetAsync(n.ring, 0, B * (n.D + 1) * N * 8, st);
+        cudaMemsetAsync(n.bits, 0, B * S * n.RW * 4, st);
+        cudaMemsetAsync(n.list_cnt, 0, B * n.RS * 4, st);
+        cudaMemsetAsync(n.y, 0, B * K * 4, st);
+        cudaMemsetAsync(n.y_acc, 0, B * K * 8, st);
+        cudaMemsetAsync(n.zk, 0, 2 * B * N * 4, st);
+        cudaMemsetAsync(n.psi_hist, 0, B * (U + 1) * N * 4, st);
+        cudaMemsetAsync(n.anchor_z, 0, B * S * 4, st);
+        eprop::launch_fill_int(n.anchor_t, B * S, eprop::kNoSpike, st);
+        if (n.has_state) {
+            const size_t tb = n.trace_bf16 ? 2 : 4;
+            cudaMemsetAsync(n.ebar, 0, n.nnz * tb, st);
+            if (n.alif) cudaMemsetAsync(n.epsa, 0, n.nnz * tb, st);
+        }
+    }
+    if (n.record_raster) cudaMemsetAsync(n.rec_raster, 0, B * ((T + 31) / 32) * N * 4, st);
+    long long L = 0, LT = 0, nwin = 0;
+    if (!c.continuous) L += 1;                       // anchor fill
+    eprop::launch_begin_call(n, c.continuous, st);
+    L += 1;
+    const int grid_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 4) * net->sm_count;
+    const int nw = T / U;
+    if (c.profile && (int)net->ev.size() < 2 * nw) {
+        for (int q = (int)net->ev.size(); q < 2 * nw; ++q) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            net->ev.push_back(e);
+        }
+    }
+    for (int i = 1; i <= T; ++i) {
+        if (c.n_in > 0) { eprop::launch_inject(n, i, (int)net->max_in_per_step, st); L += 1; }
+        eprop::launch_neuron(n, i, st);
+        eprop::launch_readout(n, i, net->sm_count, st);
+        eprop::launch_deliver(n, i, grid_rows, st);
+        L += 4;
+        if (i % U == 0) {
+            eprop::launch_filter_error(n, i, st);
+            eprop::launch_tables(n, i, st);
+            L += 2;
+            if (c.profile) cudaEventRecord(net->ev[2 * nwin], st);
+            if (net->trace_mode == 1) {
+                eprop::launch_trace_batched(n, net->sm_count, st);
+                LT += 1;
+            } else {
+                for (int e = 1; e <= U + n.D - 1; ++e) eprop::launch_trace_stream(n, i, e, grid_rows, st);
+                LT += U + n.D - 1;
+            }
+            if (c.profile) cudaEventRecord(net->ev[2 * nwin + 1], st);
+            eprop::launch_readout_weights(n, i, st);
+            L += 1;
+            if (i < T || n.has_state) { eprop::launch_rollover(n, i, st); L += 1; }
+            nwin += 1;
+        }
+    }
+    if (!c.continuous && n.has_state) {
+        eprop::launch_flush(n, T, nullptr, nullptr, 0, n.nnz, 1, net->sm_count, st);
+        L += 1;
+    }
+    eprop::launch_end_call(n, T, st);
+    L += 1;
+    net->launches = L + LT;
+    net->trace_launches = LT;
+    net->windows = nwin;
+}
+
+extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t *forced_raster) {
+    if (!net) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    const eprop_config &c = net->cfg;
+    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "eprop_set_inputs_targets must come first");
+    if (T != net->T_in) return fail(net, EPROP_EINVAL, "T differs from the T of the inputs");
+    if (c.continuous && c.update_interval == 0) {
+        if (net->U_fixed == 0) net->U_fixed = T;
+        else if (T != net->U_fixed) return fail(net, EPROP_EINVAL, "continuous network: T must stay fixed");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(net, e, "pending error before simulate");
+    const bool use_graph = c.launch_mode == 1 && forced_raster == nullptr;
+    if (use_graph) {
+        if (!net->gexec || net->g_T != T) {
+            if (net->gexec) {
+                cudaGraphExecDestroy(net->gexec);
+                net->gexec = nullptr;
+            }
+            cudaGraph_t g;
+            CK(net, cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal));
+            issue_call(net, T, nullptr);
+            CK(net, cudaStreamEndCapture(net->st, &g));
+            e = cudaGraphInstantiate(&net->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(net, e, "cudaGraphInstantiate");
+            net->g_T = T;
+        }
+        CK(net, cudaGraphLaunch(net->gexec, net->st));
+    } else {
+        issue_call(net, T, forced_raster);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(net, e, "kernel launch");
+    net->t_abs += T;
+    net->r_base = c.continuous ? net->r_base + T : T;
+    return EPROP_OK;
+}
+
+// -------------------------------------------------------------- readback
+
+static eprop_status ensure_tmp(eprop_net *net, long long count) {
+    if (net->tmp_w) return EPROP_OK;
+    void *p;
+    if (dalloc(net->fixed_allocs, &p, count * 4) != cudaSuccess) return fail(net, EPROP_ENOMEM, "tmp alloc");
+    net->tmp_w = (float *)p;
+    if (dalloc(net->fixed_allocs, &p, count * 4) != cudaSuccess) return fail(net, EPROP_ENOMEM, "tmp alloc");
+    net->tmp_g = (float *)p;
+    return EPROP_OK;
+}
+
+extern "C" eprop_status eprop_read_weights_grads(eprop_net *net, int32_t proj, float *w, float *grad,
+                                                 int32_t is_device) {
+    if (!net) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    Net &n = net->n;
+    const eprop_config &c = net->cfg;
+    if (grad && !n.record_grad) return fail(net, EPROP_EINVAL, "gradients need record_grad = 1");
+    const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t st = net->st;
+    if (proj == 2) {
+        const long long cnt = (long long)c.n_rec * c.n_out;
+        if (w) CK(net, cudaMemcpyAsync(w, n.w_out, cnt * 4, kind, st));
+        if (grad) CK(net, cudaMemcpyAsync(grad, n.grad_out, cnt * 4, kind, st));
+        CK(net, cudaStreamSynchronize(st));
+        return EPROP_OK;
+    }
+    if (proj != 0 && proj != 1) return fail(net, EPROP_EINVAL, "proj must be 0, 1 or 2");
+    const long long q0 = proj == 0 ? 0 : net->nnz_in;
+    const long long q1 = proj == 0 ? net->nnz_in : n.nnz;
+    const long long cnt = q1 - q0;
+    if (cnt == 0) return EPROP_OK;
+    if (n.has_state && c.continuous && net->r_base > 0 && net->U_alloc > 0) {
+        eprop_status s = ensure_tmp(net, n.nnz);
+        if (s != EPROP_OK) return s;
+        eprop::launch_flush(n, 0, net->tmp_w, net->tmp_g, q0, q1, 0, net->sm_count, st);
+        if (w) CK(net, cudaMemcpyAsync(w, net->tmp_w, cnt * 4, kind, st));
+        if (grad) CK(net, cudaMemcpyAsync(grad, net->tmp_g, cnt * 4, kind, st));
+    } else {
+        if (w) CK(net, cudaMemcpyAsync(w, n.w + q0, cnt * 4, kind, st));
+        if (grad) CK(net, cudaMemcpyAsync(grad, n.grad + q0, cnt * 4, kind, st));
+    }
+    CK(net, cudaStreamSynchronize(st));
+    return EPROP_OK;
+}
+
+extern "C" eprop_status eprop_readout(eprop_net *net, float *y, float *loss_per_sample, uint8_t *raster,
+                                      int32_t is_device) {
+    if (!net) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    Net &n = net->n;
+    const eprop_config &c = net->cfg;
+    const long long B = c.batch, T = net->T_in, K = c.n_out, N = c.n_rec;
+    const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t st = net->st;
+    if (y) CK(net, cudaMemcpyAsync(y, n.y_rec, B * T * K * 4, kind, st));
+    if (loss_per_sample) CK(net, cudaMemcpyAsync(loss_per_sample, n.loss_acc, B * 4, kind, st));
+    if (raster) {
+        if (!n.record_raster) return fail(net, EPROP_EINVAL, "raster needs record_raster = 1");
+        const long long bytes = B * T * N;
+        if (net->tmp_raster_bytes < bytes) {
+            void *p;
+            if (dalloc(net->fixed_allocs, &p, bytes) != cudaSuccess) return fail(net, EPROP_ENOMEM, "raster alloc");
+            net->tmp_raster = (unsigned char *)p;
+            net->tmp_raster_bytes = bytes;
+        }
+        Net nn = n;
+        nn.T = (int)T;
+        eprop::launch_unpack_raster(nn, net->tmp_raster, st);
+        CK(net, cudaMemcpyAsync(raster, net->tmp_raster, bytes, kind, st));
+    }
+    CK(net, cudaStreamSynchronize(st));
+    return EPROP_OK;
+}
+
+extern "C" eprop_status eprop_get_stats(eprop_net *net, eprop_stats *out) {
+    if (!net || !out) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    unsigned long long h = 0;
+    CK(net, cudaMemcpyAsync(&h, net->n.events, 8, cudaMemcpyDeviceToHost, net->st));
+    CK(net, cudaStreamSynchronize(net->st));
+    out->events = (int64_t)h;
+    out->kernel_launches = net->launches;
+    out->trace_launches = net->trace_launches;
+    out->windows = net->windows;
+    out->trace_ms = 0.0;
+    if (net->cfg.profile) {
+        for (long long w = 0; w < net->windows && 2 * w + 1 < (long long)net->ev.size(); ++w) {
+            float ms = 0.f;
+            CK(net, cudaEventElapsedTime(&ms, net->ev[2 * w], net->ev[2 * w + 1]));
+            out->trace_ms += ms;
+        }
+    }
+    return EPROP_OK;
+}
+
+extern "C" eprop_status eprop_sync(eprop_net *net) {
+    if (!net) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    CK(net, cudaStreamSynchronize(net->st));
+    CK(net, cudaGetLastError());
+    unsigned int f = 0;
+    CK(net, cudaMemcpy(&f, net->n.err_flags, 4, cudaMemcpyDeviceToHost));
+    if (f & 1u) net->err = "warning: a synapse skipped more update windows than the coefficient ring holds";
+    return EPROP_OK;
+}
+
+extern "C" void eprop_destroy(eprop_net *net) {
+    if (!net) return;
+    if (net->st) cudaStreamSynchronize(net->st);
+    else cudaDeviceSynchronize();
+    if (net->gexec) cudaGraphExecDestroy(net->gexec);
+    for (cudaEvent_t e : net->ev) cudaEventDestroy(e);
+    free_all(net->in_allocs);
+    free_all(net->win_allocs);
+    free_all(net->fixed_allocs);
+    if (net->own_stream) cudaStreamDestroy(net->st);
+    delete net;
+}
+
+extern "C" const char *eprop_last_error(const eprop_net *net) {
+    if (!net) return g_create_err.c_str();
+    return net->err.c_str();
+}

@@ -1,0 +1,198 @@
+// Internal definitions shared by the CUDA translation units of libeprop.
+//
+// Data layout in HBM (one network, batch B, N recurrent neurons, S = n_in + N
+// sources, nnz synapses, D = max delay, U = update window in steps):
+//   synapse records, CSR by source (SoA, 4-byte aligned streams):
+//     tgt_d [nnz] u32   target | delay << 24
+//     w     [nnz] f32   weight in effect after the synapse's last update
+//     ebar  [nnz] f32/bf16  filtered eligibility trace at the end of the
+//                       update window of the synapse's last arrival
+//     epsa  [nnz] f32/bf16  adaptation eligibility (ALIF only)
+//     grad  [nnz] f32   cumulative applied gradient (optional)
+//   neurons [B][N]: v, a, ref, z_prev; psi history [B][U+1][N] (slot 0 =
+//     last step of the previous window)
+//   membrane input ring [B][D+1][N] int64 fixed point (2^-32): arrivals are
+//     summed exactly, so the result does not depend on the atomic order
+//   source spike bits [B][S][RW] u32: a ring of RW*32 >= U+D steps per source
+//   source anchor [B][S]: last spike before the ring range and the
+//     presynaptic trace sum_s alpha^{t-s} right after it
+//   per-step spike lists (ring of RS steps) [B][RS][S] i32 + counts
+//   window tables [B][U][N] float2 (LIF: Q, Pe) or float4 (ALIF: Q, Pe, Pa)
+//   window coefficients (ring of RC windows) [RC][N] float4 (LIF) or
+//     2 x float4 (ALIF)
+//   readout: W_out [N][K], B [N][K], y [B][K], error window [B][U][K]
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace eprop {
+
+constexpr int kMaxDelay = 8;
+constexpr int kMaxOut = 1024;
+constexpr double kFixScale = 4294967296.0;          // 2^32
+constexpr float kFixInv = 2.3283064365386963e-10f;  // 2^-32
+constexpr int kNoSpike = -1073741824;               // "no spike" time
+
+struct Clock {            // device-resident time base (graph-safe)
+    long long t_abs_base; // absolute steps completed before the current call
+    int r_base;           // steps since the last state reset before the call
+    int pad;
+};
+
+struct Net {
+    // sizes
+    int n_in, n_rec, n_out, n_src, B, D, U, RW, RS, RC;
+    long long nnz;
+    // model switches
+    int alif, t_ref, loss, feedback, has_state, trace_bf16, record_grad, record_raster;
+    int n_thr, T;             // T of the current call
+    // constants (float, computed on the host in double)
+    float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
+    float log2_alpha, log2_kappa, alphaU, kappaeU, inv_B;
+    unsigned long long drive_seed;
+    const uint32_t *drive_thr;
+    // synapses
+    const long long *row_ptr;
+    const uint32_t *tgt_d;
+    float *w;
+    void *ebar;
+    void *epsa;
+    float *grad;
+    // neurons
+    float *v, *a, *psi_hist;
+    int *ref;
+    uint8_t *z_prev;
+    long long *ring;
+    // sources
+    uint32_t *bits;
+    int *anchor_t;
+    float *anchor_z;
+    int *list_ids;
+    int *list_cnt;
+    // readout
+    float *w_out;
+    const uint8_t *out_mask;
+    const float *fb;          // feedback matrix (== w_out when symmetric)
+    float *grad_out;
+    float *y;
+    long long *y_acc;
+    float *E_win, *Ebar_win, *Cwin;
+    float *zk, *zk_next;
+    float *y_rec, *loss_acc;
+    // window tables
+    float *qp;
+    float *coef;
+    // inputs of the current call
+    const long long *x_ptr;
+    const int *x_ids;
+    const float *targets;
+    const uint8_t *window;
+    const int *lengths;
+    const uint8_t *forced;
+    uint32_t *rec_raster;     // [B][T/32+1][N] bits (record_raster)
+    unsigned long long *events;
+    unsigned int *err_flags;  // bit 0: catch-up ring overflow
+    Clock *clock;
+};
+
+// ----------------------------------------------------------------- helpers
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    // SplitMix64 output function (Steele, Lea & Flood 2014)
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float pow_alpha(const Net &n, int k) {
+    return k <= 0 ? 1.0f : exp2f(n.log2_alpha * (float)k);
+}
+__device__ __forceinline__ float pow_kappa(const Net &n, int k) {
+    return k <= 0 ? 1.0f : exp2f(n.log2_kappa * (float)k);
+}
+
+__device__ __forceinline__ bool bit_at(const uint32_t *words, int RW, int r) {
+    int p = r & (RW * 32 - 1);
+    return (words[p >> 5] >> (p & 31)) & 1u;
+}
+
+__device__ __forceinline__ float load_trace(const void *base, long long q, int bf16) {
+    if (bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[q]);
+    return reinterpret_cast<const float *>(base)[q];
+}
+__device__ __forceinline__ void store_trace(void *base, long long q, float x, int bf16) {
+    if (bf16) reinterpret_cast<__nv_bfloat16 *>(base)[q] = __float2bfloat16_rn(x);
+    else reinterpret_cast<float *>(base)[q] = x;
+}
+
+// Presynaptic summary of one source row for one delay d, relative to the
+// update window (a0, a0 + U]:
+//   zbar_a0  presynaptic trace F_alpha of the arrivals up to a0, at a0
+//   b_prev   end of the window holding the last arrival <= a0 (kNoSpike: none)
+//   zbar_bp  trace at b_prev
+//   s_first  first spike whose arrival falls inside the window (kNoSpike: none)
+struct RowInfo {
+    float zbar_a0, zbar_bp;
+    int b_prev, s_first;
+};
+
+// Computes RowInfo for delay d from the source's spike bits and anchor.
+// The bit ring covers run steps [a0 + 1 - D, a0 + U].
+__device__ __forceinline__ RowInfo row_info(const Net &n, const uint32_t *words, int anchor_t,
+                                            float anchor_z, int a0, int d, bool want_first) {
+    RowInfo ri;
+    const int lo = a0 + 1 - n.D;
+    const int lim = a0 - d;            // last emission whose arrival is <= a0
+    int s_p = anchor_t;
+    float z_p = anchor_z;
+    for (int s = (lo > 1 ? lo : 1); s <= lim; ++s) {
+        if (bit_at(words, n.RW, s)) {
+            z_p = (s_p == kNoSpike ? 0.0f : z_p * pow_alpha(n, s - s_p)) + 1.0f;
+            s_p = s;
+        }
+    }
+    if (s_p == kNoSpike) {
+        ri.zbar_a0 = 0.0f;
+        ri.zbar_bp = 0.0f;
+        ri.b_prev = kNoSpike;
+    } else {
+        const int a_p = s_p + d;
+        const int b_p = ((a_p + n.U - 1) / n.U) * n.U;
+        ri.b_prev = b_p;
+        ri.zbar_bp = z_p * pow_alpha(n, b_p - a_p);
+        ri.zbar_a0 = z_p * pow_alpha(n, a0 - a_p);
+    }
+    ri.s_first = kNoSpike;
+    if (want_first) {
+        const int hi = a0 + n.U - d;
+        for (int s = (lim + 1 > 1 ? lim + 1 : 1); s <= hi; ++s)
+            if (bit_at(words, n.RW, s)) { ri.s_first = s; break; }
+    }
+    return ri;
+}
+
+// Window transfer of one synapse state x = (zbar, eps_a, ebar) over window
+// index k (coefficients c, Phi from the coefficient ring); adds c . x to G.
+template <bool ALIF>
+__device__ __forceinline__ void apply_window(const Net &n, long long j, int k, float &zbar,
+                                             float &epsa, float &ebar, float &G) {
+    const int slot = k % n.RC;
+    if (ALIF) {
+        const float4 *c = reinterpret_cast<const float4 *>(n.coef) + ((long long)slot * n.n_rec + j) * 2;
+        const float4 c0 = c[0], c1 = c[1];   // (cz, ca, ce, maz), (maa, mez, mea, -)
+        G += c0.x * zbar + c0.y * epsa + c0.z * ebar;
+        const float ea = c0.w * zbar + c1.x * epsa;
+        const float ee = c1.y * zbar + c1.z * epsa + n.kappaeU * ebar;
+        epsa = ea;
+        ebar = ee;
+    } else {
+        const float4 c = reinterpret_cast<const float4 *>(n.coef)[(long long)slot * n.n_rec + j];
+        G += c.x * zbar + c.y * ebar;        // (cz, ce, mez, -)
+        ebar = c.z * zbar + n.kappaeU * ebar;
+    }
+    zbar *= n.alphaU;
+}
+
+}  // namespace eprop

@@ -1,0 +1,28 @@
+// Host-side launch wrappers of the libeprop kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace eprop {
+
+struct Net;
+
+void launch_inject(const Net &n, int i, int max_events_per_step, cudaStream_t st);
+void launch_neuron(const Net &n, int i, cudaStream_t st);
+void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st);
+void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st);
+
+void prepare_kernel_attributes();
+void launch_begin_call(const Net &n, int continuous, cudaStream_t st);
+void launch_end_call(const Net &n, int T, cudaStream_t st);
+void launch_filter_error(const Net &n, int i_end, cudaStream_t st);
+int launch_tables(const Net &n, int i_end, cudaStream_t st);
+void launch_trace_stream(const Net &n, int i_end, int e, int grid_x, cudaStream_t st);
+void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st);
+void launch_readout_weights(const Net &n, int i_end, cudaStream_t st);
+void launch_rollover(const Net &n, int i_end, cudaStream_t st);
+void launch_flush(const Net &n, int i_end, float *w_dst, float *g_dst, long long q_begin, long long q_end,
+                  int write_back, int sm_count, cudaStream_t st);
+void launch_fill_int(int *p, long long count, int value, cudaStream_t st);
+void launch_unpack_raster(const Net &n, unsigned char *dst, cudaStream_t st);
+
+}  // namespace eprop

@@ -1,0 +1,302 @@
+// Per-step kernels: input injection, neuron update, readout and error
+// signal, spike transmission through the delayed synapses.
+#include "eprop_internal.cuh"
+#include "eprop_launch.h"
+
+namespace eprop {
+
+// list slot / ring helpers -------------------------------------------------
+
+__device__ __forceinline__ int run_step(const Net &n, int i) { return n.clock->r_base + i; }
+__device__ __forceinline__ long long abs_step(const Net &n, int i) { return n.clock->t_abs_base + i; }
+__device__ __forceinline__ int win_start(const Net &n, int r) { return ((r - 1) / n.U) * n.U; }
+
+__device__ __forceinline__ uint32_t *src_words(const Net &n, int b, int src) {
+    return n.bits + ((long long)b * n.n_src + src) * n.RW;
+}
+
+// Appends `src` to the spike list of run step r of sample b and sets its
+// bit; returns without a second entry if the bit was already set.
+__device__ __forceinline__ void mark_spike(const Net &n, int b, int src, int r) {
+    const int p = r & (n.RW * 32 - 1);
+    uint32_t *wd = src_words(n, b, src) + (p >> 5);
+    const uint32_t m = 1u << (p & 31);
+    const uint32_t old = atomicOr(wd, m);
+    if (old & m) return;
+    const int slot = r % n.RS;
+    const int pos = atomicAdd(&n.list_cnt[(long long)b * n.RS + slot], 1);
+    n.list_ids[((long long)b * n.RS + slot) * n.n_src + pos] = src;
+}
+
+// K9: input spikes of call step i ------------------------------------------
+__global__ void inject_kernel(Net n, int i) {
+    const int b = blockIdx.y;
+    if (i > n.lengths[b]) return;
+    const long long q0 = n.x_ptr[(long long)b * n.T + i - 1];
+    const long long q1 = n.x_ptr[(long long)b * n.T + i];
+    const int r = run_step(n, i);
+    for (long long q = q0 + blockIdx.x * blockDim.x + threadIdx.x; q < q1;
+         q += (long long)gridDim.x * blockDim.x)
+        mark_spike(n, b, n.x_ids[q], r);
+}
+
+// K1: LIF / ALIF neuron update (Eq. lif_update, Eq. binary-spike-state-
+// variable, Eq. spike-threshold-adaptation, Eq. piecewise-linear-surrogate-
+// gradient), one thread per (sample, neuron).
+__global__ void neuron_kernel(Net n, int i) {
+    const int b = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n.n_rec) return;
+    const int r = run_step(n, i);
+    const int a0 = win_start(n, r);
+    const long long nb = (long long)b * n.n_rec + j;
+    float *psi_slot = n.psi_hist + ((long long)b * (n.U + 1) + (r - a0)) * n.n_rec + j;
+    if (i > n.lengths[b]) {      // sample already finished: frozen, silent
+        *psi_slot = 0.0f;
+        return;
+    }
+    const long long t_abs = abs_step(n, i);
+    const int slot = (int)(t_abs % (n.D + 1));
+    long long *ring = n.ring + ((long long)b * (n.D + 1) + slot) * n.n_rec + j;
+    float I = (float)(*ring) * kFixInv;
+    *ring = 0;
+    if (n.n_thr > 0) {
+        const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
+        const uint32_t u = (uint32_t)(h >> 32);
+        int cnt = 0;
+        for (int m = 0; m < n.n_thr; ++m) cnt += (u >= n.drive_thr[m]);
+        I += n.drive_weight * (float)cnt;
+    }
+    const float zp = (float)n.z_prev[nb];
+    float vth = n.v_th;
+    if (n.alif) {
+        const float a = n.rho * n.a[nb] + zp;
+        n.a[nb] = a;
+        vth = n.v_th + n.beta_a * a;
+    }
+    const float v = n.alpha * n.v[nb] + I - zp * vth;
+    n.v[nb] = v;
+    const float m = v - vth;
+    int ref = n.ref[nb];
+    const bool refractory = ref > 0;
+    int z;
+    if (n.forced) z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
+    else z = (!refractory && m > 0.0f) ? 1 : 0;
+    const float h = 1.0f - n.beta_sg * fabsf(m);
+    *psi_slot = refractory ? 0.0f : n.gamma * fmaxf(h, 0.0f);
+    if (refractory) ref -= 1;
+    if (z) ref = n.t_ref;
+    n.ref[nb] = ref;
+    n.z_prev[nb] = (uint8_t)z;
+    if (z) {
+        mark_spike(n, b, n.n_in + j, r);
+        if (n.record_raster) {
+            const int W32 = (n.T + 31) / 32;
+            atomicOr(&n.rec_raster[((long long)b * W32 + ((i - 1) >> 5)) * n.n_rec + j],
+                     1u << ((i - 1) & 31));
+        }
+    }
+}
+
+// K3a: readout input sum_j W_out[j][k] z_j^t in exact fixed point; one CTA per
+// (chunk of the step's spike list, sample); thread = readout k.
+__global__ void readout_accum_kernel(Net n, int i, int chunk) {
+    const int b = blockIdx.y;
+    if (i > n.lengths[b]) return;
+    const int r = run_step(n, i);
+    const int slot = r % n.RS;
+    const int cnt = n.list_cnt[(long long)b * n.RS + slot];
+    const int *ids = n.list_ids + ((long long)b * n.RS + slot) * n.n_src;
+    for (int c0 = blockIdx.x * chunk; c0 < cnt; c0 += gridDim.x * chunk) {
+        const int c1 = min(c0 + chunk, cnt);
+        for (int k = threadIdx.x; k < n.n_out; k += blockDim.x) {
+            long long acc = 0;
+            for (int c = c0; c < c1; ++c) {
+                const int src = ids[c];
+                if (src < n.n_in) continue;
+                acc += __float2ll_rn(n.w_out[(long long)(src - n.n_in) * n.n_out + k] * 4294967296.0f);
+            }
+            if (acc) atomicAdd(reinterpret_cast<unsigned long long *>(&n.y_acc[(long long)b * n.n_out + k]),
+                               (unsigned long long)acc);
+        }
+    }
+}
+
+__device__ float block_sum(float x, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = x;
+    __syncthreads();
+    float t = 0.0f;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int q = 0; q < nw; ++q) t += sh[q];
+    return t;
+}
+
+__device__ float block_max(float x, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = x;
+    __syncthreads();
+    float t = -INFINITY;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int q = 0; q < nw; ++q) t = fmaxf(t, sh[q]);
+    return t;
+}
+
+// K3b: leaky readout (Eq. leaky_integrator), error signal and loss
+// (Eq. mean-squared-error / Eq. softmax, Eq. cross-entropy-loss), one CTA per
+// sample, thread = readout k (blockDim multiple of 32, >= n_out).
+__global__ void readout_error_kernel(Net n, int i) {
+    __shared__ float sh[32];
+    const int b = blockIdx.x;
+    const int k = threadIdx.x;
+    const bool has_k = k < n.n_out;
+    const int r = run_step(n, i);
+    const int a0 = win_start(n, r);
+    const long long bk = (long long)b * n.n_out + k;
+    float *E = n.E_win + ((long long)b * n.U + (r - a0 - 1)) * n.n_out;
+    // the list slot of step r + 1 was last used RS steps ago; every reader of
+    // it has finished (RS = U + D + 1 covers the window's trace launches)
+    if (threadIdx.x == 0) n.list_cnt[(long long)b * n.RS + (r + 1) % n.RS] = 0;
+    if (i > n.lengths[b]) {
+        if (has_k) {
+            E[k] = 0.0f;
+            n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = n.y[bk];
+        }
+        return;
+    }
+    float y = 0.0f;
+    if (has_k) {
+        const long long acc = n.y_acc[bk];
+        n.y_acc[bk] = 0;
+        y = n.kappa * n.y[bk] + (float)acc * kFixInv;
+        n.y[bk] = y;
+        n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = y;
+    }
+    const float win = n.window ? (float)n.window[(long long)b * n.T + (i - 1)] : 1.0f;
+    const float tgt = has_k ? n.targets[((long long)b * n.T + (i - 1)) * n.n_out + k] : 0.0f;
+    float l;
+    if (n.loss == 0) {
+        const float diff = y - tgt;
+        if (has_k) E[k] = win * diff;
+        l = has_k ? 0.5f * win * diff * diff : 0.0f;
+    } else {
+        const float mx = block_max(has_k ? y : -INFINITY, sh);
+        const float ex = has_k ? expf(y - mx) : 0.0f;
+        const float den = block_sum(ex, sh);
+        if (has_k) E[k] = win * (ex / den - tgt);
+        l = has_k ? -win * tgt * ((y - mx) - logf(den)) : 0.0f;
+    }
+    const float tot = block_sum(l, sh);
+    if (threadIdx.x == 0) n.loss_acc[b] += tot;
+}
+
+// K2: transmission of the spikes of call step i.  One warp per spiking
+// source row; lanes stride over the row's synapses (coalesced 4-byte
+// streams).  The weight carried is the weight in effect at emission: with
+// per-synapse lazy updates, the gradient of update windows that closed
+// since the synapse's last arrival is added on the fly (read-only).
+template <bool ALIF, bool STATE>
+__global__ void deliver_kernel(Net n, int i) {
+    __shared__ RowInfo info[8][kMaxDelay + 1];
+    __shared__ unsigned long long ev_block;
+    const int b = blockIdx.y;
+    if (i > n.lengths[b]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) ev_block = 0ULL;
+    __syncthreads();
+    unsigned long long ev_warp = 0ULL;
+    const int r = run_step(n, i);
+    const int a0 = win_start(n, r);
+    const long long t_abs = abs_step(n, i);
+    const int slot = r % n.RS;
+    const int cnt = n.list_cnt[(long long)b * n.RS + slot];
+    const int *ids = n.list_ids + ((long long)b * n.RS + slot) * n.n_src;
+    const int D1 = n.D + 1;
+    long long *ring_b = n.ring + (long long)b * D1 * n.n_rec;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int row = gw; row < cnt; row += nw) {
+        const int src = ids[row];
+        const long long q0 = n.row_ptr[src], q1 = n.row_ptr[src + 1];
+        ev_warp += (unsigned long long)(q1 - q0);
+        if (STATE) {
+            if (lane >= 1 && lane <= n.D)
+                info[warp][lane] = row_info(n, src_words(n, b, src), n.anchor_t[(long long)b * n.n_src + src],
+                                            n.anchor_z[(long long)b * n.n_src + src], a0, lane, false);
+            __syncwarp();
+        }
+        for (long long q = q0 + lane; q < q1; q += 32) {
+            const uint32_t td = n.tgt_d[q];
+            const int j = (int)(td & 0xFFFFFFu);
+            const int d = (int)(td >> 24);
+            float wv = n.w[q];
+            if (STATE) {
+                const RowInfo ri = info[warp][d];
+                if (ri.b_prev != kNoSpike && ri.b_prev < a0) {
+                    float zbar = ri.zbar_bp;
+                    float ebar = load_trace(n.ebar, q, n.trace_bf16);
+                    float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.0f;
+                    float G = 0.0f;
+                    int k0 = ri.b_prev / n.U;
+                    const int k1 = a0 / n.U;           // windows k0 .. k1-1 closed, not applied
+                    if (k1 - k0 > n.RC) {
+                        atomicOr(n.err_flags, 1u);
+                        k0 = k1 - n.RC;
+                    }
+                    for (int k = k0; k < k1; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                    wv -= n.lr * G;
+                }
+            }
+            const long long fx = __float2ll_rn(wv * 4294967296.0f);
+            atomicAdd(reinterpret_cast<unsigned long long *>(
+                          &ring_b[(long long)((t_abs + d) % D1) * n.n_rec + j]),
+                      (unsigned long long)fx);
+        }
+        if (STATE) __syncwarp();
+    }
+    if (lane == 0 && ev_warp) atomicAdd(&ev_block, ev_warp);
+    __syncthreads();
+    if (threadIdx.x == 0 && ev_block) atomicAdd(n.events, ev_block);
+}
+
+// ----------------------------------------------------------------- launches
+
+void launch_inject(const Net &n, int i, int max_events_per_step, cudaStream_t st) {
+    if (n.n_in == 0) return;
+    int blocks = (max_events_per_step + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 64) blocks = 64;
+    inject_kernel<<<dim3(blocks, n.B), 256, 0, st>>>(n, i);
+}
+
+void launch_neuron(const Net &n, int i, cudaStream_t st) {
+    neuron_kernel<<<dim3((n.n_rec + 255) / 256, n.B), 256, 0, st>>>(n, i);
+}
+
+void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
+    const int chunk = 32;
+    int blocks = (n.n_src + chunk - 1) / chunk;
+    const int cap = n.B > 1 ? 4 : 2 * sm_count;
+    if (blocks > cap) blocks = cap;
+    int th = ((n.n_out + 31) / 32) * 32;
+    if (th > 256) th = 256;
+    readout_accum_kernel<<<dim3(blocks, n.B), th, 0, st>>>(n, i, chunk);
+    int th2 = ((n.n_out + 31) / 32) * 32;
+    readout_error_kernel<<<n.B, th2, 0, st>>>(n, i);
+}
+
+void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st) {
+    const dim3 grid(grid_x, n.B);
+    if (n.has_state) {
+        if (n.alif) deliver_kernel<true, true><<<grid, 256, 0, st>>>(n, i);
+        else deliver_kernel<false, true><<<grid, 256, 0, st>>>(n, i);
+    } else {
+        deliver_kernel<false, false><<<grid, 256, 0, st>>>(n, i);
+    }
+}
+
+}  // namespace eprop

@@ -1,0 +1,550 @@
+// Update-window kernels: learning-signal tables, event-driven synapse trace
+// and gradient (the metric kernel), readout-weight gradient, window rollover.
+//
+// Closed form used by the synapse kernel.  Inside one update window
+// (a0, b] the state of synapse j <- i, x = (zbar, eps_a, ebar), evolves as
+// x^t = A^t x^{t-1} + s^t (1, 0, psi_j^t) with s^t the arrival indicator and
+//   A^{t} = [[alpha, 0, 0],
+//            [psi^{t-1}, rho - beta psi^{t-1}, 0],
+//            [psi^t (alpha - beta psi^{t-1}), -beta psi^t (rho - beta psi^{t-1}), kappa_e]]
+// (Eq. eligibility-vector-substituted, Eq. filtered-eligibility-trace), and the
+// window's gradient is G = sum_t L^t ebar^t (Eq. final-gradient).  Everything
+// is linear in x and in the arrivals and depends on the presynaptic side only
+// through the arrival times, so for each postsynaptic neuron j one backward
+// (adjoint) sweep over the window gives
+//   Q(a)  = dG/d(arrival at a),  Pe(a), Pa(a) = d(ebar^b, eps_a^b)/d(arrival at a)
+//   c     = dG/dx^{a0},          Phi = dx^b/dx^{a0}
+// and an arrival costs one table lookup instead of a loop over the history.
+// The paper's event-driven algorithm (Algorithm 5) instead loops over the
+// archived psi/L history of the inter-spike interval; the sums are the same.
+#include "eprop_internal.cuh"
+#include "eprop_launch.h"
+
+namespace eprop {
+
+__device__ __forceinline__ int run_step_w(const Net &n, int i) { return n.clock->r_base + i; }
+
+__device__ __forceinline__ const uint32_t *src_words_c(const Net &n, int b, int src) {
+    return n.bits + ((long long)b * n.n_src + src) * n.RW;
+}
+
+// Calls f(s) for every spike time s in [lo, hi] (hi - lo < ring span) in
+// increasing order.
+template <typename F>
+__device__ __forceinline__ void for_each_spike(const uint32_t *words, int RW, int lo, int hi, F f) {
+    const int mask = RW * 32 - 1;
+    int r = lo < 1 ? 1 : lo;
+    while (r <= hi) {
+        const int p = r & mask;
+        const int bit = p & 31;
+        const int span = min(31 - bit, hi - r);        // bits bit..bit+span
+        uint32_t m = words[p >> 5] >> bit;
+        if (span < 31) m &= (2u << span) - 1u;
+        while (m) {
+            const int o = __ffs(m) - 1;
+            f(r + o);
+            m &= m - 1;
+        }
+        r += span + 1;
+    }
+}
+
+// begin / end of a simulate call -------------------------------------------
+__global__ void begin_call_kernel(Net n, int continuous) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (!continuous) n.clock->r_base = 0;
+        *n.events = 0ULL;
+    }
+    for (int b = threadIdx.x; b < n.B; b += blockDim.x) n.loss_acc[b] = 0.0f;
+}
+
+__global__ void end_call_kernel(Net n, int T) {
+    if (threadIdx.x == 0) {
+        n.clock->t_abs_base += T;
+        n.clock->r_base += T;
+    }
+}
+
+// filtered error for the readout gradient: Ebar(u) = sum_{t >= u} kappa^{t-u} E^t
+// inside the window, and C = kappa * Ebar(a0 + 1) (Eq. eprop-output-new-subs-
+// rewritten, index-flipped inside the window).
+__global__ void filter_error_kernel(Net n) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n.B * n.n_out) return;
+    const int b = idx / n.n_out, k = idx % n.n_out;
+    const float *E = n.E_win + (long long)b * n.U * n.n_out + k;
+    float *Eb = n.Ebar_win + (long long)b * n.U * n.n_out + k;
+    float acc = 0.0f;
+    for (int u = n.U - 1; u >= 0; --u) {
+        acc = E[(long long)u * n.n_out] + n.kappa * acc;
+        Eb[(long long)u * n.n_out] = acc;
+    }
+    n.Cwin[idx] = n.kappa * acc;
+}
+
+// learning-signal tables: one thread per (sample, neuron); the window's
+// errors E[U][K] are staged in shared memory (when they fit), the learning
+// signal L^t = sum_k B_jk E_k^t of the window is formed k-chunk by k-chunk in
+// a per-thread shared-memory column, then a backward adjoint sweep writes
+// the per-step tables and the window coefficients.
+template <bool ALIF>
+__global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
+    extern __shared__ float smem[];
+    const int b = blockIdx.y;
+    const int U = n.U, K = n.n_out, N = n.n_rec;
+    const int r_end = run_step_w(n, i_end);
+    const int a0 = r_end - U;
+    const float *Eg = n.E_win + (long long)b * U * K;
+    float *Es = smem;
+    float *Ls = smem + (e_in_smem ? U * K : 0);
+    if (e_in_smem) {
+        for (int q = threadIdx.x; q < U * K; q += blockDim.x) Es[q] = Eg[q];
+        __syncthreads();
+    }
+    const float *E = e_in_smem ? Es : Eg;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const float *Bj = n.fb + (long long)j * K;
+    const int bd = blockDim.x, tid = threadIdx.x;
+    if (l_in_smem) {
+        for (int u = 0; u < U; ++u) Ls[u * bd + tid] = 0.0f;
+        for (int k0 = 0; k0 < K; k0 += 8) {
+            float f[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) f[c] = (k0 + c < K) ? Bj[k0 + c] : 0.0f;
+            const int kc = min(8, K - k0);
+            for (int u = 0; u < U; ++u) {
+                const float *e = E + u * K + k0;
+                float acc = Ls[u * bd + tid];
+                if (kc == 8) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc += f[c] * e[c];
+                } else {
+                    for (int c = 0; c < kc; ++c) acc += f[c] * e[c];
+                }
+                Ls[u * bd + tid] = acc;
+            }
+        }
+    }
+    auto Lat = [&](int u) -> float {      // L at window step u (1..U)
+        if (l_in_smem) return Ls[(u - 1) * bd + tid];
+        float acc = 0.0f;
+        const float *e = E + (u - 1) * K;
+        for (int k = 0; k < K; ++k) acc += Bj[k] * e[k];
+        return acc;
+    };
+    const float *psi = n.psi_hist + (long long)b * (U + 1) * N + j;
+    const float alpha = n.alpha, rho = n.rho, beta = n.beta_a, ke = n.kappa_e;
+    float pn = psi[(long long)U * N];          // psi^b
+    const float psi_b = pn;
+    // adjoint of G (mz, ma, me); of ebar^b (ez, ea, ee); of eps_a^b (az, aa, ae)
+    float mz = 0.f, ma = 0.f, me = Lat(U);
+    float ez = 0.f, ea = 0.f, ee = 1.f;
+    float az = 0.f, aa = 1.f, ae = 0.f;
+    long long qbase = ((long long)b * U) * N + j;
+    if (ALIF) {
+        reinterpret_cast<float4 *>(n.qp)[qbase + (long long)(U - 1) * N] =
+            make_float4(mz + pn * me, ez + pn * ee, az + pn * ae, 0.f);
+    } else {
+        reinterpret_cast<float2 *>(n.qp)[qbase + (long long)(U - 1) * N] =
+            make_float2(mz + pn * me, ez + pn * ee);
+    }
+    for (int u = U - 1; u >= 0; --u) {
+        const float p = psi[(long long)u * N];       // psi^{a0+u}
+        // x -> (A^{u+1})^T x
+        float nz, na, ne;
+        if (ALIF) {
+            const float g1 = alpha - beta * p, g2 = rho - beta * p;
+            nz = alpha * mz + p * ma + pn * g1 * me;
+            na = g2 * ma - beta * pn * g2 * me;
+            ne = ke * me;
+            mz = nz; ma = na; me = ne;
+            nz = alpha * ez + p * ea + pn * g1 * ee;
+            na = g2 * ea - beta * pn * g2 * ee;
+            ne = ke * ee;
+            ez = nz; ea = na; ee = ne;
+            nz = alpha * az + p * aa + pn * g1 * ae;
+            na = g2 * aa - beta * pn * g2 * ae;
+            ne = ke * ae;
+            az = nz; aa = na; ae = ne;
+        } else {
+            mz = alpha * mz + alpha * pn * me;
+            me = ke * me;
+            ez = alpha * ez + alpha * pn * ee;
+            ee = ke * ee;
+        }
+        if (u >= 1) {
+            me += Lat(u);
+            if (ALIF) {
+                reinterpret_cast<float4 *>(n.qp)[qbase + (long long)(u - 1) * N] =
+                    make_float4(mz + p * me, ez + p * ee, az + p * ae, 0.f);
+            } else {
+                reinterpret_cast<float2 *>(n.qp)[qbase + (long long)(u - 1) * N] =
+                    make_float2(mz + p * me, ez + p * ee);
+            }
+        }
+        pn = p;
+    }
+    // window coefficients: c = (mz, ma, me), Phi rows (ez, ea, .) and (az, aa, .)
+    if (n.has_state) {
+        const int slot = (a0 / U) % n.RC;
+        if (ALIF) {
+            float4 *c = reinterpret_cast<float4 *>(n.coef) + ((long long)slot * N + j) * 2;
+            c[0] = make_float4(mz, ma, me, az);
+            c[1] = make_float4(aa, ez, ea, 0.f);
+        } else {
+            reinterpret_cast<float4 *>(n.coef)[(long long)slot * N + j] = make_float4(mz, me, ez, 0.f);
+        }
+    }
+    n.psi_hist[(long long)b * (U + 1) * N + j] = psi_b;     // slot 0 of the next window
+}
+
+// event-driven synapse trace + gradient, streaming form: one launch per
+// emission step s = b - e of the window's arrivals, rows = sources that spiked
+// at s; every synapse of the row whose arrival s + d lies in the window is
+// advanced in closed form and its weight updated.  Table slabs of the
+// arrival steps s+1..s+D stay resident in L2 while the record streams pass.
+template <bool ALIF, bool STATE>
+__global__ void __launch_bounds__(256) trace_stream_kernel(Net n, int i_end, int e) {
+    __shared__ RowInfo info[8][kMaxDelay + 1];
+    const int U = n.U, N = n.n_rec;
+    const int r_end = run_step_w(n, i_end);
+    const int a0 = r_end - U;
+    const int s = r_end - e;
+    if (s < 1) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = s % n.RS;
+    const int cnt = n.list_cnt[slot];
+    const int *ids = n.list_ids + (long long)slot * n.n_src;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int kW = a0 / U;
+    const float step = n.lr * n.inv_B;
+    for (int row = gw; row < cnt; row += nw) {
+        const int src = ids[row];
+        const long long q0 = n.row_ptr[src], q1 = n.row_ptr[src + 1];
+        if (STATE) {
+            if (lane >= 1 && lane <= n.D)
+                info[warp][lane] = row_info(n, src_words_c(n, 0, src), n.anchor_t[src],
+                                            n.anchor_z[src], a0, lane, true);
+            __syncwarp();
+        }
+        for (long long q = q0 + lane; q < q1; q += 32) {
+            const uint32_t td = __ldcs(n.tgt_d + q);
+            const int j = (int)(td & 0xFFFFFFu);
+            const int d = (int)(td >> 24);
+            const int a = s + d;
+            if (a <= a0 || a > r_end) continue;
+            const long long qi = (long long)(a - a0 - 1) * N + j;
+            float Q, Pe, Pa = 0.f;
+            if (ALIF) {
+                const float4 t = reinterpret_cast<const float4 *>(n.qp)[qi];
+                Q = t.x; Pe = t.y; Pa = t.z;
+            } else {
+                const float2 t = reinterpret_cast<const float2 *>(n.qp)[qi];
+                Q = t.x; Pe = t.y;
+            }
+            float G;
+            if (STATE) {
+                const RowInfo ri = info[warp][d];
+                float ebar = 0.f, epsa = 0.f;
+                G = 0.f;
+                if (s == ri.s_first) {
+                    if (ri.b_prev != kNoSpike) {
+                        float zbar = ri.zbar_bp;
+                        ebar = load_trace(n.ebar, q, n.trace_bf16);
+                        if (ALIF) epsa = load_trace(n.epsa, q, n.trace_bf16);
+                        int k0 = ri.b_prev / U;
+                        if (kW - k0 > n.RC - 1) {
+                            atomicOr(n.err_flags, 1u);
+                            k0 = kW - (n.RC - 1);
+                        }
+                        for (int k = k0; k <= kW; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                    }
+                } else {
+                    ebar = load_trace(n.ebar, q, n.trace_bf16);
+                    if (ALIF) epsa = load_trace(n.epsa, q, n.trace_bf16);
+                }
+                G += Q;
+                ebar += Pe;
+                store_trace(n.ebar, q, ebar, n.trace_bf16);
+                if (ALIF) store_trace(n.epsa, q, epsa + Pa, n.trace_bf16);
+            } else {
+                G = Q;
+            }
+            n.w[q] -= step * G;
+            if (n.record_grad) n.grad[q] += n.inv_B * G;
+        }
+        if (STATE) __syncwarp();
+    }
+}
+
+// event-driven synapse gradient, batched single-window form (no carried
+// state: each arrival contributes Q(a) independently).  One warp per source
+// row; the row's spikes of every sample are gathered into shared memory and
+// every synapse sums the table entries of its arrivals over all samples.
+template <int QP_STRIDE>
+__global__ void __launch_bounds__(256) trace_batched_kernel(Net n) {
+    constexpr int CAP = 512;
+    __shared__ int sp[8][CAP];      // (sample << 20) | step
+    __shared__ int ncount[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int U = n.U, N = n.n_rec, T = n.T;
+    for (int src = gw; src < n.n_src; src += nw) {
+        const long long q0 = n.row_ptr[src], q1 = n.row_ptr[src + 1];
+        if (q1 == q0) continue;
+        // gather (sample, step) pairs; lanes split the samples
+        if (lane == 0) ncount[warp] = 0;
+        __syncwarp();
+        for (int b = lane; b < n.B; b += 32) {
+            const uint32_t *words = src_words_c(n, b, src);
+            for_each_spike(words, n.RW, 1, T, [&](int st) {
+                const int pos = atomicAdd(&ncount[warp], 1);
+                if (pos < CAP) sp[warp][pos] = (b << 20) | st;
+            });
+        }
+        __syncwarp();
+        const int ns = ncount[warp];
+        if (ns == 0) continue;
+        for (long long q = q0 + lane; q < q1; q += 32) {
+            const uint32_t td = n.tgt_d[q];
+            const int j = (int)(td & 0xFFFFFFu);
+            const int d = (int)(td >> 24);
+            float G = 0.f;
+            if (ns <= CAP) {
+                for (int c = 0; c < ns; ++c) {
+                    const int v = sp[warp][c];
+                    const int b = v >> 20, a = (v & 0xFFFFF) + d;
+                    if (a <= T) G += n.qp[(((long long)b * U + (a - 1)) * N + j) * QP_STRIDE];
+                }
+            } else {
+                for (int b = 0; b < n.B; ++b) {
+                    const uint32_t *words = src_words_c(n, b, src);
+                    for_each_spike(words, n.RW, 1, T - d, [&](int st) {
+                        G += n.qp[(((long long)b * U + (st + d - 1)) * N + j) * QP_STRIDE];
+                    });
+                }
+            }
+            n.w[q] -= n.lr * n.inv_B * G;
+            if (n.record_grad) n.grad[q] += n.inv_B * G;
+        }
+        __syncwarp();
+    }
+}
+
+// readout weights: g_kj = sum_b [zk_j^{a0} C_k + sum_{spikes s in window} Ebar_k(s)]
+// (Eq. eprop-output-new-subs-rewritten), one thread per (j, k).
+__global__ void readout_weights_kernel(Net n, int i_end) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int K = n.n_out, N = n.n_rec, U = n.U;
+    if (idx >= (long long)N * K) return;
+    const int j = (int)(idx / K), k = (int)(idx % K);
+    const int r_end = run_step_w(n, i_end);
+    const int a0 = r_end - U;
+    const int par = (a0 / U) & 1;
+    const float *zk_cur = n.zk + (long long)par * n.B * N;
+    float *zk_nxt = n.zk + (long long)(par ^ 1) * n.B * N;
+    const float kU = exp2f(n.log2_kappa * (float)U);
+    float g = 0.f;
+    for (int b = 0; b < n.B; ++b) {
+        const float z0 = zk_cur[(long long)b * N + j];
+        const float *Eb = n.Ebar_win + (long long)b * U * K + k;
+        float gb = z0 * n.Cwin[b * K + k];
+        float zn = kU * z0;
+        for_each_spike(src_words_c(n, b, n.n_in + j), n.RW, a0 + 1, r_end, [&](int st) {
+            gb += Eb[(long long)(st - a0 - 1) * K];
+            zn += exp2f(n.log2_kappa * (float)(r_end - st));
+        });
+        g += gb;
+        if (k == 0) zk_nxt[(long long)b * N + j] = zn;
+    }
+    if (n.out_mask[j]) {
+        n.w_out[idx] -= n.lr * n.inv_B * g;
+        if (n.record_grad) n.grad_out[idx] += n.inv_B * g;
+    }
+}
+
+// rollover to the next window: move each source's anchor to its last spike
+// <= b - D and clear the bit positions of steps b+1 .. b+U.
+__global__ void rollover_kernel(Net n, int i_end) {
+    extern __shared__ uint32_t clear_mask[];
+    const int U = n.U;
+    const int r_end = run_step_w(n, i_end);
+    const int a0 = r_end - U;
+    const int S = n.RW * 32;
+    for (int w = threadIdx.x; w < n.RW; w += blockDim.x) clear_mask[w] = 0u;
+    __syncthreads();
+    for (int r = r_end + 1 + threadIdx.x; r <= r_end + U; r += blockDim.x) {
+        const int p = r & (S - 1);
+        atomicOr(&clear_mask[p >> 5], 1u << (p & 31));
+    }
+    __syncthreads();
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n.B * n.n_src) return;
+    uint32_t *words = n.bits + idx * n.RW;
+    int at = n.anchor_t[idx];
+    float az = n.anchor_z[idx];
+    for_each_spike(words, n.RW, a0 + 1 - n.D, r_end - n.D, [&](int st) {
+        az = (at == kNoSpike ? 0.f : az * exp2f(n.log2_alpha * (float)(st - at))) + 1.f;
+        at = st;
+    });
+    n.anchor_t[idx] = at;
+    n.anchor_z[idx] = az;
+    for (int w = 0; w < n.RW; ++w) words[w] &= ~clear_mask[w];
+    (void)a0;
+}
+
+// catch-up of every synapse to the last closed window boundary (a0 = r_base):
+// write_back = 1 applies the pending gradient to the weights (end of a
+// non-continuous call), else exports the effective weights and gradients
+// without touching the state.
+template <bool ALIF>
+__global__ void flush_kernel(Net n, int i_end, float *w_dst, float *g_dst, long long q_begin,
+                             long long q_end, int write_back) {
+    __shared__ RowInfo info[8][kMaxDelay + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int a0 = n.clock->r_base + i_end;
+    const int U = n.U;
+    for (int src = gw; src < n.n_src; src += nw) {
+        const long long q0 = max(n.row_ptr[src], q_begin), q1 = min(n.row_ptr[src + 1], q_end);
+        if (q1 <= q0) continue;
+        if (lane >= 1 && lane <= n.D)
+            info[warp][lane] = row_info(n, src_words_c(n, 0, src), n.anchor_t[src],
+                                        n.anchor_z[src], a0, lane, false);
+        __syncwarp();
+        for (long long q = q0 + lane; q < q1; q += 32) {
+            const uint32_t td = n.tgt_d[q];
+            const int j = (int)(td & 0xFFFFFFu);
+            const int d = (int)(td >> 24);
+            const RowInfo ri = info[warp][d];
+            float G = 0.f;
+            if (ri.b_prev != kNoSpike && ri.b_prev < a0) {
+                float zbar = ri.zbar_bp;
+                float ebar = load_trace(n.ebar, q, n.trace_bf16);
+                float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+                int k0 = ri.b_prev / U;
+                const int k1 = a0 / U;
+                if (k1 - k0 > n.RC) {
+                    atomicOr(n.err_flags, 1u);
+                    k0 = k1 - n.RC;
+                }
+                for (int k = k0; k < k1; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+            }
+            const float wv = n.w[q] - n.lr * G;
+            const float gv = n.record_grad ? n.grad[q] + G : 0.f;
+            if (write_back) {
+                n.w[q] = wv;
+                if (n.record_grad) n.grad[q] = gv;
+            } else {
+                if (w_dst) w_dst[q - q_begin] = wv;
+                if (g_dst) g_dst[q - q_begin] = gv;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void fill_int_kernel(int *p, long long count, int value) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x)
+        p[q] = value;
+}
+
+__global__ void unpack_raster_kernel(Net n, unsigned char *dst) {
+    const long long total = (long long)n.B * n.T * n.n_rec;
+    const int W32 = (n.T + 31) / 32;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q % n.n_rec);
+        const long long bt = q / n.n_rec;
+        const int t = (int)(bt % n.T);
+        const int b = (int)(bt / n.T);
+        dst[q] = (n.rec_raster[((long long)b * W32 + (t >> 5)) * n.n_rec + j] >> (t & 31)) & 1u;
+    }
+}
+
+// ----------------------------------------------------------------- launches
+
+void prepare_kernel_attributes() {
+    const int limit = 200 * 1024;
+    cudaFuncSetAttribute(tables_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    cudaFuncSetAttribute(tables_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+}
+
+void launch_begin_call(const Net &n, int continuous, cudaStream_t st) {
+    begin_call_kernel<<<1, 64, 0, st>>>(n, continuous);
+}
+
+void launch_end_call(const Net &n, int T, cudaStream_t st) { end_call_kernel<<<1, 32, 0, st>>>(n, T); }
+
+void launch_filter_error(const Net &n, int i_end, cudaStream_t st) {
+    (void)i_end;
+    const int tot = n.B * n.n_out;
+    filter_error_kernel<<<(tot + 127) / 128, 128, 0, st>>>(n);
+}
+
+int launch_tables(const Net &n, int i_end, cudaStream_t st) {
+    const int bd = 128;
+    const size_t e_bytes = (size_t)n.U * n.n_out * sizeof(float);
+    const size_t l_bytes = (size_t)n.U * bd * sizeof(float);
+    const size_t limit = 200 * 1024;
+    int e_in = e_bytes <= limit ? 1 : 0;
+    int l_in = (n.n_out > 1 && (e_in ? e_bytes : 0) + l_bytes <= limit) ? 1 : 0;
+    const size_t sm = (e_in ? e_bytes : 0) + (l_in ? l_bytes : 0);
+    const dim3 grid((n.n_rec + bd - 1) / bd, n.B);
+    if (n.alif) tables_kernel<true><<<grid, bd, sm, st>>>(n, i_end, e_in, l_in);
+    else tables_kernel<false><<<grid, bd, sm, st>>>(n, i_end, e_in, l_in);
+    return 0;
+}
+
+void launch_trace_stream(const Net &n, int i_end, int e, int grid_x, cudaStream_t st) {
+    if (n.has_state) {
+        if (n.alif) trace_stream_kernel<true, true><<<grid_x, 256, 0, st>>>(n, i_end, e);
+        else trace_stream_kernel<false, true><<<grid_x, 256, 0, st>>>(n, i_end, e);
+    } else {
+        if (n.alif) trace_stream_kernel<true, false><<<grid_x, 256, 0, st>>>(n, i_end, e);
+        else trace_stream_kernel<false, false><<<grid_x, 256, 0, st>>>(n, i_end, e);
+    }
+}
+
+void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st) {
+    int blocks = (n.n_src + 7) / 8;
+    if (blocks > 8 * sm_count) blocks = 8 * sm_count;
+    if (n.alif) trace_batched_kernel<4><<<blocks, 256, 0, st>>>(n);
+    else trace_batched_kernel<2><<<blocks, 256, 0, st>>>(n);
+}
+
+void launch_readout_weights(const Net &n, int i_end, cudaStream_t st) {
+    const long long tot = (long long)n.n_rec * n.n_out;
+    readout_weights_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, i_end);
+}
+
+void launch_rollover(const Net &n, int i_end, cudaStream_t st) {
+    const long long tot = (long long)n.B * n.n_src;
+    rollover_kernel<<<(unsigned)((tot + 255) / 256), 256, n.RW * sizeof(uint32_t), st>>>(n, i_end);
+}
+
+void launch_flush(const Net &n, int i_end, float *w_dst, float *g_dst, long long q_begin, long long q_end,
+                  int write_back, int sm_count, cudaStream_t st) {
+    int blocks = (n.n_src + 7) / 8;
+    if (blocks > 8 * sm_count) blocks = 8 * sm_count;
+    if (n.alif) flush_kernel<true><<<blocks, 256, 0, st>>>(n, i_end, w_dst, g_dst, q_begin, q_end, write_back);
+    else flush_kernel<false><<<blocks, 256, 0, st>>>(n, i_end, w_dst, g_dst, q_begin, q_end, write_back);
+}
+
+void launch_fill_int(int *p, long long count, int value, cudaStream_t st) {
+    if (count <= 0) return;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    fill_int_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, count, value);
+}
+
+void launch_unpack_raster(const Net &n, unsigned char *dst, cudaStream_t st) {
+    unpack_raster_kernel<<<1024, 256, 0, st>>>(n, dst);
+}
+
+}  // namespace eprop
