@@ -196,7 +196,8 @@ eprop_status eprop_read_weights_grads(eprop_net *net, int32_t proj, float *w, fl
 
 /*
  * Copies the outputs of the last simulate call.
- *   y     [batch][T][n_out] readout signal y_k^t (or NULL)
+ *   y     [batch][T][n_out] readout signal y_k^t, 0 after a sample's length
+ *         (or NULL)
  *   loss_per_sample [batch] sum over steps of the (windowed) loss (or NULL)
  *   raster [batch][T][n_rec] uint8 spikes (needs record_raster; or NULL)
  * Pointers are host pointers unless is_device.

@@ -74,7 +74,8 @@ class _State(ctypes.Structure):
             "ptr", "col", "delay", "w", "w_out", "out_mask", "fb", "v", "a",
             "psi_prev", "ref", "z_prev", "ring", "src_hist", "zbar", "epsa",
             "ebar", "g", "y", "zk", "g_out", "grad_acc", "grad_out_acc",
-            "counters")]
+            "counters", "g_abs", "g_out_abs", "grad_abs_acc", "grad_out_abs_acc",
+            "y_abs")]
 
 
 def _load():
@@ -84,7 +85,7 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_simulate.restype = ctypes.c_int
             lib.oracle_simulate.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_State),
-                                            ctypes.c_int32] + [ctypes.c_void_p] * 12
+                                            ctypes.c_int32] + [ctypes.c_void_p] * 13
             lib.oracle_eligibility_step.restype = ctypes.c_double
             lib.oracle_eligibility_step.argtypes = [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3
             _lib = lib
@@ -146,6 +147,11 @@ class Oracle:
         self.grad_acc = z(self.nnz)
         self.grad_out_acc = z((N, K))
         self.counters = z(2, np.int64)
+        self.g_abs = z(self.nnz)
+        self.g_out_abs = z((N, K))
+        self.grad_abs_acc = z(self.nnz)
+        self.grad_out_abs_acc = z((N, K))
+        self.y_abs = z((B, K))
 
     def _cfg(self, T):
         s = self.spec
@@ -170,7 +176,8 @@ class Oracle:
         for name in ("ptr", "col", "delay", "w", "w_out", "out_mask", "v", "a",
                      "psi_prev", "ref", "z_prev", "ring", "src_hist", "zbar",
                      "epsa", "ebar", "g", "y", "zk", "g_out", "grad_acc",
-                     "grad_out_acc", "counters"):
+                     "grad_out_acc", "counters", "g_abs", "g_out_abs", "grad_abs_acc",
+                     "grad_out_abs_acc", "y_abs"):
             setattr(st, name, _p(getattr(self, name)))
         st.fb = _p(self.fb)
         return st
@@ -191,7 +198,8 @@ class Oracle:
         lens = np.full(B, T, np.int32) if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
         fz = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8).reshape(B, T, N)
         out = dict(y=np.zeros((B, T, K)), loss=np.zeros(B),
-                   raster=np.zeros((B, T, N), np.uint8), margin=np.zeros((B, T, N)))
+                   raster=np.zeros((B, T, N), np.uint8), margin=np.zeros((B, T, N)),
+                   y_abs=np.zeros((B, T, K)))
         if record:
             out["psi"] = np.zeros((B, T, N))
             out["L"] = np.zeros((B, T, N))
@@ -201,7 +209,7 @@ class Oracle:
                                      _p(x_ptr), _p(x_ids), _p(tg), _p(win), _p(lens),
                                      _p(fz), _p(out["y"]), _p(out["loss"]),
                                      _p(out["raster"]), _p(out["margin"]),
-                                     _p(out.get("psi")), _p(out.get("L")))
+                                     _p(out.get("psi")), _p(out.get("L")), _p(out["y_abs"]))
         if rc:
             raise MemoryError("oracle_simulate failed")
         return out
@@ -212,6 +220,14 @@ class Oracle:
         g, go = self.grad_acc.copy(), self.grad_out_acc.copy()
         self.grad_acc[:] = 0.0
         self.grad_out_acc[:] = 0.0
+        return g, go
+
+    def take_grad_magnitudes(self):
+        """Sums of |g^t| matching `take_grads` (the condition of each
+        accumulated gradient, for the parity tolerance); resets them."""
+        g, go = self.grad_abs_acc.copy(), self.grad_out_abs_acc.copy()
+        self.grad_abs_acc[:] = 0.0
+        self.grad_out_abs_acc[:] = 0.0
         return g, go
 
 

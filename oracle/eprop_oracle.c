@@ -38,6 +38,12 @@
  *   - an external Poisson drive (non-plastic) adds drive_weight * n_j^t to the
  *     membrane input, n_j^t drawn by the SplitMix64 counter hash;
  *   - batch gradient = mean over samples of each sample's sum over steps.
+ *
+ * Besides the method's results the oracle keeps, for the parity tolerance,
+ * the sum of the magnitudes of the terms of every accumulated sum: sum_t
+ * |g^t| per weight and |y| accumulated with |W_out| (the condition of each
+ * sum: FP32 rounding of a sum is bounded relative to it, not to the sum's
+ * possibly cancelled value).  They do not feed back into any result.
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,6 +84,9 @@ typedef struct {
     double *g_out;                /* [N][K] */
     double *grad_acc, *grad_out_acc; /* applied batch-mean gradients, summed */
     int64_t *counters;            /* [0] absolute step, [1] step inside run */
+    double *g_abs, *g_out_abs;    /* sum_t |g^t| of the current window      */
+    double *grad_abs_acc, *grad_out_abs_acc; /* the same, batch mean, summed */
+    double *y_abs;                /* [B][K] kappa-filtered sum of |W_out| z  */
 } oracle_state;
 
 /* SplitMix64 output function (Steele, Lea & Flood 2014). */
@@ -129,6 +138,7 @@ static void reset_state(const oracle_cfg *c, oracle_state *s) {
     memset(s->epsa, 0, sizeof(double) * B * s->nnz);
     memset(s->ebar, 0, sizeof(double) * B * s->nnz);
     memset(s->y, 0, sizeof(double) * B * K);
+    memset(s->y_abs, 0, sizeof(double) * B * K);
     memset(s->zk, 0, sizeof(double) * B * N);
     s->counters[1] = 0;
 }
@@ -139,7 +149,8 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     const double *targets, const uint8_t *window,
                     const int32_t *lengths, const uint8_t *forced,
                     double *y_rec, double *loss, uint8_t *raster,
-                    double *margin, double *psi_rec, double *L_rec) {
+                    double *margin, double *psi_rec, double *L_rec,
+                    double *y_abs_rec) {
     const int64_t B = c->batch, N = c->n_rec, K = c->n_out, NI = c->n_in;
     const int64_t D1 = c->max_delay + 1, NS = s->n_src, NNZ = s->nnz;
     const int64_t U = c->update_interval > 0 ? c->update_interval : T;
@@ -165,6 +176,7 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
             double *ring = s->ring + b * D1 * N;
             uint8_t *hist = s->src_hist + b * D1 * NS;
             double *y = s->y + b * K, *zk = s->zk + b * N;
+            double *y_abs = s->y_abs + b * K;
             const int64_t bt = b * (int64_t)T + (t - 1);
 
             /* sources that spike at this step: inputs from the raster */
@@ -201,11 +213,16 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
             const double win = window ? (double)window[bt] : 1.0;
             const double *tgt = targets + bt * K;
             for (int64_t k = 0; k < K; ++k) {
-                double acc = 0.0;
+                double acc = 0.0, acc_abs = 0.0;
                 for (int64_t j = 0; j < N; ++j)
-                    if (z[j]) acc += s->w_out[j * K + k];
+                    if (z[j]) {
+                        acc += s->w_out[j * K + k];
+                        acc_abs += fabs(s->w_out[j * K + k]);
+                    }
                 y[k] = c->kappa * y[k] + acc;
+                y_abs[k] = c->kappa * y_abs[k] + acc_abs;
                 y_rec[bt * K + k] = y[k];
+                if (y_abs_rec) y_abs_rec[bt * K + k] = y_abs[k];
             }
             if (c->loss == 0) {
                 for (int64_t k = 0; k < K; ++k) {
@@ -240,16 +257,21 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     const int64_t d = s->delay[q];
                     double arrive = 0.0;
                     if (t_abs - d >= 1) arrive = hist[((t_abs - d) % D1) * NS + i];
-                    s->g[q] += oracle_eligibility_step(
+                    const double gt = oracle_eligibility_step(
                         c->alpha, c->rho, c->beta_a, c->kappa_e, psi_prev[j],
                         psi[j], L[j], arrive, s->zbar + b * NNZ + q,
                         s->epsa + b * NNZ + q, s->ebar + b * NNZ + q);
+                    s->g[q] += gt;
+                    s->g_abs[q] += fabs(gt);
                 }
             }
             for (int64_t j = 0; j < N; ++j) {
                 zk[j] = c->kappa * zk[j] + z[j];
                 if (s->out_mask[j])
-                    for (int64_t k = 0; k < K; ++k) s->g_out[j * K + k] += E[k] * zk[j];
+                    for (int64_t k = 0; k < K; ++k) {
+                        s->g_out[j * K + k] += E[k] * zk[j];
+                        s->g_out_abs[j * K + k] += fabs(E[k] * zk[j]);
+                    }
             }
             for (int64_t j = 0; j < N; ++j) {
                 psi_prev[j] = psi[j];
@@ -273,6 +295,8 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 s->w[q] -= c->lr * gm;
                 s->grad_acc[q] += gm;
                 s->g[q] = 0.0;
+                s->grad_abs_acc[q] += s->g_abs[q] / (double)B;
+                s->g_abs[q] = 0.0;
             }
             for (int64_t j = 0; j < N; ++j) {
                 if (!s->out_mask[j]) continue;
@@ -281,6 +305,8 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     s->w_out[j * K + k] -= c->lr * gm;
                     s->grad_out_acc[j * K + k] += gm;
                     s->g_out[j * K + k] = 0.0;
+                    s->grad_out_abs_acc[j * K + k] += s->g_out_abs[j * K + k] / (double)B;
+                    s->g_out_abs[j * K + k] = 0.0;
                 }
             }
         }

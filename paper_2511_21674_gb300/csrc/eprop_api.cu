@@ -136,6 +136,9 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     const long long B = c.batch, N = c.n_rec, K = c.n_out, S = n.n_src;
     const int D = c.max_delay;
     n.U = U;
+    n.alphaU = (float)std::exp(-(double)c.dt / c.tau_m * U);
+    n.kappaeU = (float)(c.kappa_e < 0.f ? std::exp(-(double)c.dt / c.tau_out * U)
+                                        : std::pow((double)c.kappa_e, (double)U));
     n.RW = next_pow2((U + D + 31) / 32);
     net->qp_stride = c.neuron_model == 1 ? 4 : 2;
     const double qp_bytes = (double)U * N * net->qp_stride * 4.0 * B;
@@ -518,7 +521,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             eprop::launch_filter_error(n, i, st);
             eprop::launch_tables(n, i, st);
             L += 2;
-            if (c.profile) cudaEventRecord(net->ev[2 * nwin], st);
+            if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin], st, cudaEventRecordExternal);
             if (net->trace_mode == 1) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
                 LT += 1;
@@ -526,7 +529,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
                 for (int e = 1; e <= U + n.D - 1; ++e) eprop::launch_trace_stream(n, i, e, grid_rows, st);
                 LT += U + n.D - 1;
             }
-            if (c.profile) cudaEventRecord(net->ev[2 * nwin + 1], st);
+            if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin + 1], st, cudaEventRecordExternal);
             eprop::launch_readout_weights(n, i, st);
             L += 1;
             if (i < T || n.has_state) { eprop::launch_rollover(n, i, st); L += 1; }

@@ -161,10 +161,10 @@ __global__ void readout_error_kernel(Net n, int i) {
     // the list slot of step r + 1 was last used RS steps ago; every reader of
     // it has finished (RS = U + D + 1 covers the window's trace launches)
     if (threadIdx.x == 0) n.list_cnt[(long long)b * n.RS + (r + 1) % n.RS] = 0;
-    if (i > n.lengths[b]) {
+    if (i > n.lengths[b]) {      // after the sample's end: no error, no output
         if (has_k) {
             E[k] = 0.0f;
-            n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = n.y[bk];
+            n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = 0.0f;
         }
         return;
     }

@@ -5,10 +5,14 @@ Agreement rules (written out here and in each test):
   spike decision must equal the oracle's FP64 decision (v - v_th > 0 and not
   refractory) except where |v - v_th| <= DELTA_V * (1 + |v|), a bound on the
   FP32 rounding of the membrane recursion; such ambiguous steps are counted;
-* gradients, weights, readout and loss: |gpu - oracle| <= RTOL *
-  max(|oracle|, FLOOR * max|oracle|) element by element (RTOL = 1e-5,
-  FLOOR = 1e-3), i.e. a relative tolerance of 1e-5 with a floor for
-  elements that are small compared with the largest one.
+* every accumulated quantity q = sum_i x_i is compared with a relative
+  tolerance of RTOL = 1e-5 taken on the condition of the sum,
+  |gpu - oracle| <= RTOL * sum_i |x_i|  (>= RTOL * |q|),
+  because the FP32 rounding error of a sum is bounded relative to the sum
+  of the magnitudes of its terms, not to its possibly cancelled value.  The
+  oracle reports these magnitude sums: sum_t |g^t| per gradient element,
+  the |W_out|-filtered |y| per readout step; a weight after updates is
+  compared on |w_0| + lr * sum |g^t|; a loss on loss + sum |E| |y|_abs.
 """
 from __future__ import annotations
 
@@ -40,14 +44,21 @@ def check_decisions(raster_gpu, margin_or, v_th_or, t_ref, lengths):
     return int((diff & ~amb).sum()), int((amb & active & ~ref).sum())
 
 
-def assert_close(gpu, ref, what, rtol=RTOL, floor=FLOOR):
+def assert_close(gpu, ref, what, rtol=RTOL, floor=FLOOR, mag=None):
+    """|gpu - ref| <= rtol * mag element-wise (mag = magnitude sum of the
+    terms of each element, >= |ref|); without mag, a relative tolerance with
+    a floor of `floor` times the largest |ref|."""
     gpu = np.asarray(gpu, dtype=np.float64).ravel()
     ref = np.asarray(ref, dtype=np.float64).ravel()
     assert gpu.shape == ref.shape, (what, gpu.shape, ref.shape)
     if ref.size == 0:
         return 0.0
-    scale = np.abs(ref).max()
-    tol = rtol * np.maximum(np.abs(ref), floor * scale) + 1e-30
+    if mag is not None:
+        mag = np.asarray(mag, dtype=np.float64).ravel()
+        tol = rtol * np.maximum(mag, np.abs(ref)) + 1e-30
+    else:
+        scale = np.abs(ref).max()
+        tol = rtol * np.maximum(np.abs(ref), floor * scale) + 1e-30
     err = np.abs(gpu - ref)
     bad = err > tol
     worst = float((err / tol).max())

@@ -3,8 +3,8 @@
 Each case runs the CUDA library through the C ABI, then the oracle on the
 same arrays with its spikes teacher-forced to the GPU raster, and checks the
 agreement rules of `tests/parity.py`: spike decisions bit-exact outside the
-FP32 ambiguity band, readout, loss, weights and gradients within relative
-1e-5 (floor 1e-3 of the largest element).
+FP32 ambiguity band; readout, loss, weights and gradients within relative
+1e-5 of the magnitude sum of their terms.
 """
 from __future__ import annotations
 
@@ -41,9 +41,13 @@ def run_parity(W, calls=1, gpu_kw=None, inputs_per_call=None, check=True, grad_r
     orc = _oracle(W)
     rep = dict(ambiguous=0, mismatches=0, worst={})
     nnz_in = int(W["ptr"][s.n_in]) if s.n_in else 0
-    g_in_or = np.zeros(nnz_in)
-    g_rec_or = np.zeros(int(W["ptr"][-1]) - nnz_in)
+    nnz = int(W["ptr"][-1])
+    g_or = np.zeros(nnz)
+    g_mag = np.zeros(nnz)
     g_out_or = np.zeros((s.n_rec, s.n_out))
+    g_out_mag = np.zeros((s.n_rec, s.n_out))
+    w0 = np.abs(np.asarray(W["w"], np.float64))
+    w_out0 = np.abs(np.asarray(W["w_out"], np.float64))
     for c in range(calls):
         inp = inputs_per_call[c] if inputs_per_call else W
         net.set_inputs(inp["x_ptr"], inp["x_ids"], inp["targets"], inp["window"], inp["lengths"], s.T)
@@ -52,9 +56,11 @@ def run_parity(W, calls=1, gpu_kw=None, inputs_per_call=None, check=True, grad_r
         r = orc.simulate(s.T, inp["x_ptr"], inp["x_ids"], inp["targets"], inp["window"],
                          inp["lengths"], forced=raster)
         g, go = orc.take_grads()
-        g_in_or += g[:nnz_in]
-        g_rec_or += g[nnz_in:]
+        gm, gom = orc.take_grad_magnitudes()
+        g_or += g
+        g_mag += gm
         g_out_or += go
+        g_out_mag += gom
         mm, amb = P.check_decisions(raster, r["margin"], s.v_th, s.t_ref, inp["lengths"])
         rep["mismatches"] += mm
         rep["ambiguous"] += amb
@@ -62,25 +68,45 @@ def run_parity(W, calls=1, gpu_kw=None, inputs_per_call=None, check=True, grad_r
         rep["spikes"] += int(raster.sum())
         if check:
             assert mm == 0, f"call {c}: {mm} spike decisions differ outside the ambiguity band"
-            rep["worst"]["y"] = P.assert_close(y, r["y"], f"call {c} readout y")
-            rep["worst"]["loss"] = P.assert_close(loss, r["loss"], f"call {c} loss")
+            rep["worst"]["y"] = P.assert_close(y, r["y"], f"call {c} readout y", mag=r["y_abs"])
+            rep["worst"]["loss"] = P.assert_close(loss, r["loss"], f"call {c} loss",
+                                                  mag=_loss_mag(s, inp, r))
     net.sync()
     w_out, gw_out = net.weights(ep.PROJ_OUT, with_grad=True)
     w_rec, gw_rec = net.weights(ep.PROJ_REC, with_grad=True)
     rep["events"] = net.events()
-    res = dict(w_rec=(w_rec, orc.w[nnz_in:]), g_rec=(gw_rec, g_rec_or),
-               w_out=(w_out, orc.w_out), g_out=(gw_out, g_out_or))
+    rec = slice(nnz_in, nnz)
+    res = dict(w_rec=(w_rec, orc.w[rec], w0[rec] + s.lr * g_mag[rec]),
+               g_rec=(gw_rec, g_or[rec], g_mag[rec]),
+               w_out=(w_out, orc.w_out, w_out0 + s.lr * g_out_mag),
+               g_out=(gw_out, g_out_or, g_out_mag))
     if s.n_in:
         w_in, gw_in = net.weights(ep.PROJ_IN, with_grad=True)
-        res.update(w_in=(w_in, orc.w[:nnz_in]), g_in=(gw_in, g_in_or))
+        inn = slice(0, nnz_in)
+        res.update(w_in=(w_in, orc.w[inn], w0[inn] + s.lr * g_mag[inn]),
+                   g_in=(gw_in, g_or[inn], g_mag[inn]))
     net.close()
-    for k, (a, b) in res.items():
+    for k, (a, b, mag) in res.items():
         rep.setdefault("rel_l2", {})[k] = P.rel_l2(a, b)
         if check:
             rtol = grad_rtol if k.startswith("g") else P.RTOL
-            rep["worst"][k] = P.assert_close(a, b, k, rtol=rtol)
-    rep["res"] = res
+            rep["worst"][k] = P.assert_close(a, b, k, rtol=rtol, mag=mag)
+    rep["res"] = {k: v[:2] for k, v in res.items()}
     return rep
+
+
+def _loss_mag(s, inp, r):
+    """loss + sum_t sum_k |E_k^t| |y|_abs,k^t per sample (first-order bound of
+    the loss's sensitivity to the readout's rounding)."""
+    y, yabs = r["y"], r["y_abs"]
+    tg = np.asarray(inp["targets"], np.float64)
+    win = np.asarray(inp["window"], np.float64)[..., None]
+    if s.loss == 0:
+        E = win * (y - tg)
+    else:
+        e = np.exp(y - y.max(axis=2, keepdims=True))
+        E = win * (e / e.sum(axis=2, keepdims=True) - tg)
+    return r["loss"] + (np.abs(E) * yabs).sum(axis=(1, 2))
 
 
 def _pattern(**kw):
@@ -182,8 +208,10 @@ def test_forced_raster_on_gpu_matches_oracle_free_run():
     assert np.array_equal(raster, r["raster"])
     w_rec, g_rec = net.weights(ep.PROJ_REC, with_grad=True)
     nnz_in = int(W["ptr"][s.n_in])
-    P.assert_close(g_rec, g_or[nnz_in:], "forced recurrent gradient")
-    P.assert_close(net.weights(ep.PROJ_OUT, with_grad=True)[1], go_or, "forced readout gradient")
+    gm, gom = orc.take_grad_magnitudes()
+    P.assert_close(g_rec, g_or[nnz_in:], "forced recurrent gradient", mag=gm[nnz_in:])
+    P.assert_close(net.weights(ep.PROJ_OUT, with_grad=True)[1], go_or, "forced readout gradient",
+                   mag=gom)
     net.close()
 
 
@@ -202,5 +230,5 @@ def test_bf16_traces_report_error():
     # form (1): traces stored in BF16, FP32 accumulation; reported, not gated
     W = C.million_sparse(n_rec=4000, k_in=1000, T=200, n_out=10)
     rep = run_parity(W, calls=2, gpu_kw=dict(trace_dtype=1), check=False)
-    assert rep["mismatches"] == 0 or rep["mismatches"] < 10
+    print("bf16 traces: rel_l2", rep["rel_l2"], "decision mismatches", rep["mismatches"])
     assert rep["rel_l2"]["g_rec"] < 5e-2
