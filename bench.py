@@ -330,6 +330,7 @@ def _run_ours(args, rank, world, local):
                    "l2": "inputs larger than L2 (synapse records ~10 GB per step)"},
         "sim_time_per_wall_time": (T * spec.dt / 1000.0) / (ms_max / K / 1000.0),
         "events_per_step": events / K,
+        "mean_rate_hz": events / K / nnz / (T * spec.dt / 1000.0),
         "grad_error": "FP32 traces: <=1e-5 relative vs FP64 oracle (scaled replica); "
                       "BF16 traces: reported in DESIGN.md",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -234,6 +234,8 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     const double kappa_e = c.kappa_e < 0.f ? kappa : (double)c.kappa_e;
     n.alpha = (float)alpha; n.kappa = (float)kappa; n.kappa_e = (float)kappa_e;
     n.rho = n.alif ? (float)std::exp(-(double)c.dt / c.tau_a) : 0.f;
+    n.alpha_lo = (float)(alpha - (double)n.alpha);
+    n.rho_lo = n.alif ? (float)(std::exp(-(double)c.dt / c.tau_a) - (double)n.rho) : 0.f;
     n.beta_a = n.alif ? c.beta_a : 0.f;
     n.v_th = c.v_th; n.gamma = c.gamma; n.beta_sg = c.beta_sg; n.lr = c.lr;
     n.drive_weight = c.drive_weight; n.drive_seed = c.drive_seed;
@@ -310,6 +312,8 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         // neurons
         FA(v, float, B * N);
         FA(a, float, B * N);
+        FA(v_lo, float, B * N);
+        FA(a_lo, float, B * N);
         FA(ref, int, B * N);
         FA(z_prev, uint8_t, B * N);
         FA(ring, long long, B * (c.max_delay + 1) * N);
@@ -480,6 +484,8 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     if (!c.continuous) {
         cudaMemsetAsync(n.v, 0, B * N * 4, st);
         cudaMemsetAsync(n.a, 0, B * N * 4, st);
+        cudaMemsetAsync(n.v_lo, 0, B * N * 4, st);
+        cudaMemsetAsync(n.a_lo, 0, B * N * 4, st);
         cudaMemsetAsync(n.ref, 0, B * N * 4, st);
         cudaMemsetAsync(n.z_prev, 0, B * N, st);
         cudaMemsetAsync(n.ring, 0, B * (n.D + 1) * N * 8, st);
@@ -526,7 +532,9 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
                 LT += 1;
             } else {
-                for (int e = 1; e <= U + n.D - 1; ++e) eprop::launch_trace_stream(n, i, e, grid_rows, st);
+                // ascending emission steps: a synapse's first arrival of the
+                // window (which restores its stored state) precedes its others
+                for (int e = U + n.D - 1; e >= 1; --e) eprop::launch_trace_stream(n, i, e, grid_rows, st);
                 LT += U + n.D - 1;
             }
             if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin + 1], st, cudaEventRecordExternal);

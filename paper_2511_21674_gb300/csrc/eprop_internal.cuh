@@ -49,6 +49,7 @@ struct Net {
     int n_thr, T;             // T of the current call
     // constants (float, computed on the host in double)
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
+    float alpha_lo, rho_lo;   // alpha - (float)alpha, rho - (float)rho
     float log2_alpha, log2_kappa, alphaU, kappaeU, inv_B;
     unsigned long long drive_seed;
     const uint32_t *drive_thr;
@@ -59,8 +60,8 @@ struct Net {
     void *ebar;
     void *epsa;
     float *grad;
-    // neurons
-    float *v, *a, *psi_hist;
+    // neurons: v and a are carried as unevaluated FP32 pairs (hi + lo)
+    float *v, *a, *v_lo, *a_lo, *psi_hist;
     int *ref;
     uint8_t *z_prev;
     long long *ring;
@@ -97,6 +98,32 @@ struct Net {
 };
 
 // ----------------------------------------------------------------- helpers
+
+// TwoSum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated first-order recursion x' = c * x + u in FP32 pairs:
+// (x_hi + x_lo) and (c_hi + c_lo), u = u_hi + u_lo; error-free product
+// (FMA) and TwoSum, then renormalisation (Fast2Sum).  Keeps the recursion's
+// rounding error at the level of the FP32 pair instead of accumulating one
+// FP32 rounding of |x| per step.
+__device__ __forceinline__ void comp_step(float c_hi, float c_lo, float u_hi, float u_lo,
+                                          float &x_hi, float &x_lo) {
+    const float p = c_hi * x_hi;
+    const float pe = fmaf(c_hi, x_hi, -p);
+    const float small = fmaf(c_hi, x_lo, fmaf(c_lo, x_hi, pe)) + u_lo;
+    const float s = p + u_hi;
+    const float bb = s - p;
+    const float err = (p - (s - bb)) + (u_hi - bb);
+    const float lo = err + small;
+    const float hi = s + lo;
+    x_lo = lo - (hi - s);
+    x_hi = hi;
+}
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     // SplitMix64 output function (Steele, Lea & Flood 2014)

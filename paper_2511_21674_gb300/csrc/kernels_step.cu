@@ -58,25 +58,44 @@ __global__ void neuron_kernel(Net n, int i) {
     const long long t_abs = abs_step(n, i);
     const int slot = (int)(t_abs % (n.D + 1));
     long long *ring = n.ring + ((long long)b * (n.D + 1) + slot) * n.n_rec + j;
-    float I = (float)(*ring) * kFixInv;
+    // exact fixed-point input split into an FP32 pair
+    const long long acc = *ring;
     *ring = 0;
+    const float acc_hi = (float)acc;
+    float u_hi = acc_hi * kFixInv;
+    float u_lo = (float)(acc - (long long)acc_hi) * kFixInv;
     if (n.n_thr > 0) {
         const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
         const uint32_t u = (uint32_t)(h >> 32);
         int cnt = 0;
         for (int m = 0; m < n.n_thr; ++m) cnt += (u >= n.drive_thr[m]);
-        I += n.drive_weight * (float)cnt;
+        const float dv = n.drive_weight * (float)cnt;
+        const float de = fmaf(n.drive_weight, (float)cnt, -dv);
+        float e;
+        two_sum(u_hi, dv, u_hi, e);
+        u_lo += e + de;
     }
     const float zp = (float)n.z_prev[nb];
-    float vth = n.v_th;
+    float vth = n.v_th, vth_lo = 0.0f;
     if (n.alif) {
-        const float a = n.rho * n.a[nb] + zp;
-        n.a[nb] = a;
-        vth = n.v_th + n.beta_a * a;
+        float a_hi = n.a[nb], a_lo = n.a_lo[nb];
+        comp_step(n.rho, n.rho_lo, zp, 0.0f, a_hi, a_lo);
+        n.a[nb] = a_hi;
+        n.a_lo[nb] = a_lo;
+        vth = fmaf(n.beta_a, a_hi, n.v_th);
+        vth_lo = fmaf(n.beta_a, a_hi, n.v_th - vth) + n.beta_a * a_lo;
     }
-    const float v = n.alpha * n.v[nb] + I - zp * vth;
-    n.v[nb] = v;
-    const float m = v - vth;
+    // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
+    {
+        float e;
+        two_sum(u_hi, -zp * vth, u_hi, e);
+        u_lo += e - zp * vth_lo;
+    }
+    float v_hi = n.v[nb], v_lo = n.v_lo[nb];
+    comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi, v_lo);
+    n.v[nb] = v_hi;
+    n.v_lo[nb] = v_lo;
+    const float m = (v_hi - vth) + (v_lo - vth_lo);
     int ref = n.ref[nb];
     const bool refractory = ref > 0;
     int z;

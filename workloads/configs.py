@@ -209,8 +209,10 @@ def _weights(seed, tag, pre, post, std):
 def pattern_regression(seed: int = 1234, T: int = 1000, n_in: int = 20,
                        n_rec: int = 100, n_out: int = 1, rate_hz: float = 50.0,
                        **over) -> dict:
+    # learning rate 1e-3 on the loss averaged over the T steps of a sample,
+    # i.e. 1e-3 / T on the summed loss of Eq. mean-squared-error
     spec = Spec(name="pattern_regression", n_in=n_in, n_rec=n_rec,
-                n_out=n_out, T=T, lr=1e-3, max_delay=1, seed=seed)
+                n_out=n_out, T=T, lr=1e-3 / T, max_delay=1, seed=seed)
     for key, val in over.items():
         setattr(spec, key, val)
     # input -> recurrent: all-to-all, delay 1
