@@ -99,6 +99,7 @@ typedef struct eprop_config {
     int32_t trace_dtype;      /* storage of per-synapse traces: 0 FP32, 1 BF16 */
     int32_t record_grad;      /* 1: keep per-synapse gradient sums             */
     int32_t record_raster;    /* 1: keep the spike raster of the last call     */
+    int32_t record_psi;       /* 1: keep the surrogate values of the last call */
     int32_t n_drive_thr;      /* entries used in drive_thr (0: no drive)       */
     int32_t launch_mode;      /* 0: launch every kernel of a simulate call;
                                  1: capture a call once in a CUDA graph and
@@ -204,6 +205,13 @@ eprop_status eprop_read_weights_grads(eprop_net *net, int32_t proj, float *w, fl
  */
 eprop_status eprop_readout(eprop_net *net, float *y, float *loss_per_sample,
                            uint8_t *raster, int32_t is_device);
+
+/*
+ * Copies the surrogate derivatives psi_j^t of the last simulate call
+ * (Eq. piecewise-linear-surrogate-gradient), [batch][T][n_rec], 0 where the
+ * neuron is refractory or the sample has ended.  Needs record_psi = 1.
+ */
+eprop_status eprop_read_surrogate(eprop_net *net, float *psi, int32_t is_device);
 
 /* Counters of the last simulate call. */
 typedef struct eprop_stats {

@@ -75,7 +75,7 @@ class _State(ctypes.Structure):
             "psi_prev", "ref", "z_prev", "ring", "src_hist", "zbar", "epsa",
             "ebar", "g", "y", "zk", "g_out", "grad_acc", "grad_out_acc",
             "counters", "g_abs", "g_out_abs", "grad_abs_acc", "grad_out_abs_acc",
-            "y_abs")]
+            "y_abs", "g_lsens", "g_out_lsens", "grad_lsens_acc", "grad_out_lsens_acc")]
 
 
 def _load():
@@ -85,7 +85,7 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_simulate.restype = ctypes.c_int
             lib.oracle_simulate.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_State),
-                                            ctypes.c_int32] + [ctypes.c_void_p] * 13
+                                            ctypes.c_int32] + [ctypes.c_void_p] * 14
             lib.oracle_eligibility_step.restype = ctypes.c_double
             lib.oracle_eligibility_step.argtypes = [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3
             _lib = lib
@@ -152,6 +152,10 @@ class Oracle:
         self.grad_abs_acc = z(self.nnz)
         self.grad_out_abs_acc = z((N, K))
         self.y_abs = z((B, K))
+        self.g_lsens = z(self.nnz)
+        self.g_out_lsens = z((N, K))
+        self.grad_lsens_acc = z(self.nnz)
+        self.grad_out_lsens_acc = z((N, K))
 
     def _cfg(self, T):
         s = self.spec
@@ -177,15 +181,17 @@ class Oracle:
                      "psi_prev", "ref", "z_prev", "ring", "src_hist", "zbar",
                      "epsa", "ebar", "g", "y", "zk", "g_out", "grad_acc",
                      "grad_out_acc", "counters", "g_abs", "g_out_abs", "grad_abs_acc",
-                     "grad_out_abs_acc", "y_abs"):
+                     "grad_out_abs_acc", "y_abs", "g_lsens", "g_out_lsens", "grad_lsens_acc",
+                     "grad_out_lsens_acc"):
             setattr(st, name, _p(getattr(self, name)))
         st.fb = _p(self.fb)
         return st
 
     def simulate(self, T, x_ptr, x_ids, targets, window=None, lengths=None,
-                 forced=None, record=False):
+                 forced=None, record=False, forced_psi=None):
         """Run T steps; returns a dict with y [B,T,K], loss [B], raster
-        [B,T,N] (uint8), margin [B,T,N] (v - v_th) and, if record, psi and L."""
+        [B,T,N] (uint8), margin [B,T,N] (v - v_th) and, if record, psi and L.
+        forced / forced_psi teacher-force the spikes / the surrogate values."""
         s = self.spec
         B, N, K = s.batch, s.n_rec, s.n_out
         if s.update_interval and T % s.update_interval:
@@ -197,6 +203,7 @@ class Oracle:
         win = None if window is None else np.ascontiguousarray(window, dtype=np.uint8).reshape(B, T)
         lens = np.full(B, T, np.int32) if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
         fz = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8).reshape(B, T, N)
+        fpsi = None if forced_psi is None else np.ascontiguousarray(forced_psi, dtype=np.float64).reshape(B, T, N)
         out = dict(y=np.zeros((B, T, K)), loss=np.zeros(B),
                    raster=np.zeros((B, T, N), np.uint8), margin=np.zeros((B, T, N)),
                    y_abs=np.zeros((B, T, K)))
@@ -209,7 +216,8 @@ class Oracle:
                                      _p(x_ptr), _p(x_ids), _p(tg), _p(win), _p(lens),
                                      _p(fz), _p(out["y"]), _p(out["loss"]),
                                      _p(out["raster"]), _p(out["margin"]),
-                                     _p(out.get("psi")), _p(out.get("L")), _p(out["y_abs"]))
+                                     _p(out.get("psi")), _p(out.get("L")), _p(out["y_abs"]),
+                                     _p(fpsi))
         if rc:
             raise MemoryError("oracle_simulate failed")
         return out
@@ -228,6 +236,15 @@ class Oracle:
         g, go = self.grad_abs_acc.copy(), self.grad_out_abs_acc.copy()
         self.grad_abs_acc[:] = 0.0
         self.grad_out_abs_acc[:] = 0.0
+        return g, go
+
+    def take_grad_sensitivities(self):
+        """sum_t Lsens^t |ebar^t| (and sum_t Esens_k^t zbar_kappa,j^t for W_out)
+        matching `take_grads`: the gradients' first-order sensitivity to a
+        relative perturbation of the error signals; resets them."""
+        g, go = self.grad_lsens_acc.copy(), self.grad_out_lsens_acc.copy()
+        self.grad_lsens_acc[:] = 0.0
+        self.grad_out_lsens_acc[:] = 0.0
         return g, go
 
 

@@ -43,7 +43,14 @@
  * the sum of the magnitudes of the terms of every accumulated sum: sum_t
  * |g^t| per weight and |y| accumulated with |W_out| (the condition of each
  * sum: FP32 rounding of a sum is bounded relative to it, not to the sum's
- * possibly cancelled value).  They do not feed back into any result.
+ * possibly cancelled value), and the sensitivity of each gradient to a
+ * relative perturbation of the error signal: sum_t Lsens_j^t |ebar^t| with
+ * Lsens_j^t = sum_k |B_jk| (|y|_k^t + |y*_k^t|).  They do not feed back into
+ * any result.
+ *
+ * Teacher forcing: `forced` replaces the spikes z; `forced_psi` (optional)
+ * replaces the surrogate values psi used by the traces, so that the trace
+ * and gradient arithmetic can be compared in isolation.
  */
 #include <math.h>
 #include <stdint.h>
@@ -87,6 +94,8 @@ typedef struct {
     double *g_abs, *g_out_abs;    /* sum_t |g^t| of the current window      */
     double *grad_abs_acc, *grad_out_abs_acc; /* the same, batch mean, summed */
     double *y_abs;                /* [B][K] kappa-filtered sum of |W_out| z  */
+    double *g_lsens, *g_out_lsens;        /* sensitivity sums, current window */
+    double *grad_lsens_acc, *grad_out_lsens_acc; /* the same, batch mean, summed */
 } oracle_state;
 
 /* SplitMix64 output function (Steele, Lea & Flood 2014). */
@@ -150,7 +159,7 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     const int32_t *lengths, const uint8_t *forced,
                     double *y_rec, double *loss, uint8_t *raster,
                     double *margin, double *psi_rec, double *L_rec,
-                    double *y_abs_rec) {
+                    double *y_abs_rec, const double *forced_psi) {
     const int64_t B = c->batch, N = c->n_rec, K = c->n_out, NI = c->n_in;
     const int64_t D1 = c->max_delay + 1, NS = s->n_src, NNZ = s->nnz;
     const int64_t U = c->update_interval > 0 ? c->update_interval : T;
@@ -159,8 +168,10 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
     double *L = (double *)calloc(N, sizeof(double));
     double *E = (double *)calloc(K, sizeof(double));
     double *pi = (double *)calloc(K, sizeof(double));
+    double *Esens = (double *)calloc(K, sizeof(double));
+    double *Ls = (double *)calloc(N, sizeof(double));
     uint8_t *z = (uint8_t *)calloc(N, 1);
-    if (!psi || !L || !E || !pi || !z) return 1;
+    if (!psi || !L || !E || !pi || !z || !Esens || !Ls) return 1;
     for (int64_t b = 0; b < B; ++b) loss[b] = 0.0;
 
     for (int32_t t = 1; t <= T; ++t) {
@@ -201,6 +212,7 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     z[j] = (!refractory && m > 0.0) ? 1 : 0;
                 double h = 1.0 - c->beta_sg * fabs(m);
                 psi[j] = refractory ? 0.0 : c->gamma * (h > 0.0 ? h : 0.0);
+                if (forced_psi) psi[j] = forced_psi[bt * N + j];
                 if (refractory) ref[j] -= 1;
                 if (z[j]) ref[j] = c->t_ref;
                 raster[bt * N + j] = z[j];
@@ -243,10 +255,15 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
             }
             /* learning signal */
             const double *Bm = c->feedback ? s->fb : s->w_out;
+            for (int64_t k = 0; k < K; ++k) Esens[k] = win * (y_abs[k] + fabs(tgt[k]));
             for (int64_t j = 0; j < N; ++j) {
-                double acc = 0.0;
-                for (int64_t k = 0; k < K; ++k) acc += Bm[j * K + k] * E[k];
+                double acc = 0.0, accs = 0.0;
+                for (int64_t k = 0; k < K; ++k) {
+                    acc += Bm[j * K + k] * E[k];
+                    accs += fabs(Bm[j * K + k]) * Esens[k];
+                }
                 L[j] = acc;
+                Ls[j] = accs;
                 if (L_rec) L_rec[bt * N + j] = acc;
             }
 
@@ -263,6 +280,7 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                         s->epsa + b * NNZ + q, s->ebar + b * NNZ + q);
                     s->g[q] += gt;
                     s->g_abs[q] += fabs(gt);
+                    s->g_lsens[q] += Ls[j] * fabs(s->ebar[b * NNZ + q]);
                 }
             }
             for (int64_t j = 0; j < N; ++j) {
@@ -271,6 +289,7 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     for (int64_t k = 0; k < K; ++k) {
                         s->g_out[j * K + k] += E[k] * zk[j];
                         s->g_out_abs[j * K + k] += fabs(E[k] * zk[j]);
+                        s->g_out_lsens[j * K + k] += Esens[k] * zk[j];
                     }
             }
             for (int64_t j = 0; j < N; ++j) {
@@ -297,6 +316,8 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 s->g[q] = 0.0;
                 s->grad_abs_acc[q] += s->g_abs[q] / (double)B;
                 s->g_abs[q] = 0.0;
+                s->grad_lsens_acc[q] += s->g_lsens[q] / (double)B;
+                s->g_lsens[q] = 0.0;
             }
             for (int64_t j = 0; j < N; ++j) {
                 if (!s->out_mask[j]) continue;
@@ -307,10 +328,12 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     s->g_out[j * K + k] = 0.0;
                     s->grad_out_abs_acc[j * K + k] += s->g_out_abs[j * K + k] / (double)B;
                     s->g_out_abs[j * K + k] = 0.0;
+                    s->grad_out_lsens_acc[j * K + k] += s->g_out_lsens[j * K + k] / (double)B;
+                    s->g_out_lsens[j * K + k] = 0.0;
                 }
             }
         }
     }
-    free(psi); free(L); free(E); free(pi); free(z);
+    free(psi); free(L); free(E); free(pi); free(z); free(Esens); free(Ls);
     return 0;
 }

@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "abi_version", "n_in", "n_rec", "n_out", "batch", "neuron_model", "t_ref", "loss",
         "feedback", "update_interval", "continuous", "max_delay", "trace_dtype",
-        "record_grad", "record_raster", "n_drive_thr", "launch_mode", "trace_kernel",
+        "record_grad", "record_raster", "record_psi", "n_drive_thr", "launch_mode", "trace_kernel",
         "blocks_per_sm", "profile")] + [
         (n, ctypes.c_float) for n in (
             "dt", "tau_m", "tau_a", "beta_a", "v_th", "tau_out", "kappa_e", "gamma",
@@ -65,7 +65,8 @@ class Synapses(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("eprop_create_network", "eprop_set_inputs_targets", "eprop_simulate",
-           "eprop_read_weights_grads", "eprop_readout", "eprop_get_stats", "eprop_sync",
+           "eprop_read_weights_grads", "eprop_readout", "eprop_read_surrogate",
+           "eprop_get_stats", "eprop_sync",
            "eprop_destroy", "eprop_last_error")
 
 
@@ -86,6 +87,7 @@ def load_library(path: str = LIB_PATH):
     lib.eprop_read_weights_grads.argtypes = [vp, i32, vp, vp, i32]
     lib.eprop_readout.argtypes = [vp, vp, vp, vp, i32]
     lib.eprop_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.eprop_read_surrogate.argtypes = [vp, vp, i32]
     lib.eprop_sync.argtypes = [vp]
     lib.eprop_destroy.argtypes = [vp]
     lib.eprop_destroy.restype = None
@@ -100,7 +102,7 @@ def load_library(path: str = LIB_PATH):
 
 def make_config(spec, launch_mode: int = 1, trace_dtype: int = 0, record_grad: int = 1,
                 record_raster: int = 0, trace_kernel: int = 0, blocks_per_sm: int = 0,
-                profile: int = 0) -> Config:
+                profile: int = 0, record_psi: int = 0) -> Config:
     """C configuration from a `workloads.configs.Spec`-like object."""
     c = Config()
     c.abi_version = ABI_VERSION
@@ -108,6 +110,7 @@ def make_config(spec, launch_mode: int = 1, trace_dtype: int = 0, record_grad: i
     c.neuron_model, c.t_ref, c.loss, c.feedback = spec.neuron_model, spec.t_ref, spec.loss, spec.feedback
     c.update_interval, c.continuous, c.max_delay = spec.update_interval, spec.continuous, spec.max_delay
     c.trace_dtype, c.record_grad, c.record_raster = trace_dtype, record_grad, record_raster
+    c.record_psi = record_psi
     c.launch_mode = launch_mode
     c.trace_kernel, c.blocks_per_sm, c.profile = trace_kernel, blocks_per_sm, profile
     c.dt, c.tau_m, c.tau_a = spec.dt, spec.tau_m, spec.tau_a
@@ -248,6 +251,13 @@ class Network:
         self._check(self.lib.eprop_readout(self.h, y.ctypes.data, loss.ctypes.data,
                                            None if r is None else r.ctypes.data, 0))
         return (y, loss, r) if raster else (y, loss)
+
+    def surrogate(self):
+        """psi [batch, T, n_rec] of the last call (needs record_psi=1)."""
+        s = self.spec
+        psi = np.zeros((s.batch, self.T, s.n_rec), np.float32)
+        self._check(self.lib.eprop_read_surrogate(self.h, psi.ctypes.data, 0))
+        return psi
 
     def stats(self) -> dict:
         st = Stats()

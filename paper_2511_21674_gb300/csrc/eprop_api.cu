@@ -228,7 +228,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     n.alif = c.neuron_model == 1; n.t_ref = c.t_ref; n.loss = c.loss; n.feedback = c.feedback;
     n.has_state = (c.continuous || c.update_interval > 0) ? 1 : 0;
     n.trace_bf16 = c.trace_dtype == 1; n.record_grad = c.record_grad != 0;
-    n.record_raster = c.record_raster != 0; n.n_thr = c.drive_weight != 0.f ? c.n_drive_thr : 0;
+    n.record_raster = c.record_raster != 0; n.record_psi = c.record_psi != 0; n.n_thr = c.drive_weight != 0.f ? c.n_drive_thr : 0;
     const double alpha = std::exp(-(double)c.dt / c.tau_m);
     const double kappa = std::exp(-(double)c.dt / c.tau_out);
     const double kappa_e = c.kappa_e < 0.f ? kappa : (double)c.kappa_e;
@@ -431,6 +431,7 @@ extern "C" eprop_status eprop_set_inputs_targets(eprop_net *net, const int64_t *
         IA(lengths, int, B);
         IA(y_rec, float, B * T * K);
         if (n.record_raster) IA(rec_raster, uint32_t, B * ((T + 31) / 32) * N);
+        if (n.record_psi) IA(rec_psi, float, B * T * N);
 #undef IA
         net->x_cap = cap;
     }
@@ -668,6 +669,18 @@ extern "C" eprop_status eprop_readout(eprop_net *net, float *y, float *loss_per_
         CK(net, cudaMemcpyAsync(raster, net->tmp_raster, bytes, kind, st));
     }
     CK(net, cudaStreamSynchronize(st));
+    return EPROP_OK;
+}
+
+extern "C" eprop_status eprop_read_surrogate(eprop_net *net, float *psi, int32_t is_device) {
+    if (!net || !psi) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    if (!net->n.record_psi) return fail(net, EPROP_EINVAL, "surrogate values need record_psi = 1");
+    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    const long long cnt = (long long)net->cfg.batch * net->T_in * net->cfg.n_rec;
+    CK(net, cudaMemcpyAsync(psi, net->n.rec_psi, cnt * 4,
+                            is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, net->st));
+    CK(net, cudaStreamSynchronize(net->st));
     return EPROP_OK;
 }
 

@@ -45,7 +45,7 @@ struct Net {
     int n_in, n_rec, n_out, n_src, B, D, U, RW, RS, RC;
     long long nnz;
     // model switches
-    int alif, t_ref, loss, feedback, has_state, trace_bf16, record_grad, record_raster;
+    int alif, t_ref, loss, feedback, has_state, trace_bf16, record_grad, record_raster, record_psi;
     int n_thr, T;             // T of the current call
     // constants (float, computed on the host in double)
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
@@ -92,6 +92,7 @@ struct Net {
     const int *lengths;
     const uint8_t *forced;
     uint32_t *rec_raster;     // [B][T/32+1][N] bits (record_raster)
+    float *rec_psi;           // [B][T][N] (record_psi)
     unsigned long long *events;
     unsigned int *err_flags;  // bit 0: catch-up ring overflow
     Clock *clock;
@@ -192,10 +193,22 @@ __device__ __forceinline__ RowInfo row_info(const Net &n, const uint32_t *words,
         ri.zbar_a0 = z_p * pow_alpha(n, a0 - a_p);
     }
     ri.s_first = kNoSpike;
-    if (want_first) {
+    if (want_first) {            // first set bit in [lim + 1, a0 + U - d], word by word
         const int hi = a0 + n.U - d;
-        for (int s = (lim + 1 > 1 ? lim + 1 : 1); s <= hi; ++s)
-            if (bit_at(words, n.RW, s)) { ri.s_first = s; break; }
+        const int mask = n.RW * 32 - 1;
+        int r = lim + 1 > 1 ? lim + 1 : 1;
+        while (r <= hi) {
+            const int p = r & mask;
+            const int bit = p & 31;
+            const int span = min(31 - bit, hi - r);
+            uint32_t m = words[p >> 5] >> bit;
+            if (span < 31) m &= (2u << span) - 1u;
+            if (m) {
+                ri.s_first = r + __ffs(m) - 1;
+                break;
+            }
+            r += span + 1;
+        }
     }
     return ri;
 }

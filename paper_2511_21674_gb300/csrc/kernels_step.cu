@@ -53,6 +53,7 @@ __global__ void neuron_kernel(Net n, int i) {
     float *psi_slot = n.psi_hist + ((long long)b * (n.U + 1) + (r - a0)) * n.n_rec + j;
     if (i > n.lengths[b]) {      // sample already finished: frozen, silent
         *psi_slot = 0.0f;
+        if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
         return;
     }
     const long long t_abs = abs_step(n, i);
@@ -102,7 +103,9 @@ __global__ void neuron_kernel(Net n, int i) {
     if (n.forced) z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
     else z = (!refractory && m > 0.0f) ? 1 : 0;
     const float h = 1.0f - n.beta_sg * fabsf(m);
-    *psi_slot = refractory ? 0.0f : n.gamma * fmaxf(h, 0.0f);
+    const float psi = refractory ? 0.0f : n.gamma * fmaxf(h, 0.0f);
+    *psi_slot = psi;
+    if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = psi;
     if (refractory) ref -= 1;
     if (z) ref = n.t_ref;
     n.ref[nb] = ref;

@@ -336,8 +336,10 @@ def sparse_balanced(seed: int = 1236, n_rec: int = 100_000, k_in: int = 1000,
                     drive_weight: float = 0.04, drive_rate: float = 1.2,
                     name: str = "sparse_balanced", **over) -> dict:
     """E/I network with fixed in-degree and delays 1..5, numpy build."""
+    # lr 1e-6 keeps the firing rate near its configured value while the
+    # weights learn (1e-4 drives the network into a high-rate state)
     spec = Spec(name=name, n_in=0, n_rec=n_rec, n_out=n_out, T=T,
-                feedback=1, lr=1e-4, max_delay=5, drive_weight=drive_weight,
+                feedback=1, lr=1e-6, max_delay=5, drive_weight=drive_weight,
                 drive_rate=drive_rate, drive_seed=seed * 7919 + 17, seed=seed)
     for key, val in over.items():
         setattr(spec, key, val)
@@ -364,7 +366,7 @@ def sparse_balanced(seed: int = 1236, n_rec: int = 100_000, k_in: int = 1000,
 def million_sparse_spec(n_rec: int = 1_000_000, T: int = 1000, n_out: int = 100,
                         seed: int = 1237, **over) -> Spec:
     spec = Spec(name="million_sparse", n_in=0, n_rec=n_rec, n_out=n_out, T=T,
-                feedback=1, update_interval=100, continuous=1, lr=1e-4,
+                feedback=1, update_interval=100, continuous=1, lr=1e-6,
                 max_delay=5, drive_weight=0.03, drive_rate=1.25,
                 drive_seed=seed * 7919 + 17, seed=seed)
     for key, val in over.items():
