@@ -1,5 +1,6 @@
 // C ABI of libeprop (see include/eprop.h): argument checks, device memory,
 // and the launch schedule of one simulate call.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,7 +25,7 @@ struct eprop_net {
     std::vector<void *> in_allocs;      // per-T input buffers
     long long nnz_in = 0;
     int U_alloc = 0, T_alloc = 0, T_in = 0, U_fixed = 0;
-    int trace_mode = 0;                 // 0 streaming, 1 batched
+    int trace_mode = 0;                 // 0 window work queue, 1 batched
     int qp_stride = 2;
     long long x_cap = 0;
     long long max_in_per_step = 0;
@@ -144,7 +145,8 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     const double qp_bytes = (double)U * N * net->qp_stride * 4.0 * B;
     if (c.trace_kernel == 1) net->trace_mode = 0;
     else if (c.trace_kernel == 2) net->trace_mode = 1;
-    else net->trace_mode = (B > 1 || (!n.has_state && qp_bytes <= 64.0 * 1024 * 1024)) ? 1 : 0;
+    else net->trace_mode = B > 1 ? 1 : 0;
+    (void)qp_bytes;
     n.RS = net->trace_mode == 0 ? U + D + 1 : 2;
     n.RC = 0;
     if (n.has_state) {
@@ -166,6 +168,7 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     WA(E_win, float, B * U * K);
     WA(Ebar_win, float, B * U * K);
     WA(qp, float, B * (long long)U * N * net->qp_stride);
+    WA(win_off, long long, U + D + 2);
     if (n.has_state) WA(coef, float, (long long)n.RC * N * (c.neuron_model == 1 ? 8 : 4));
 #undef WA
     net->U_alloc = U;
@@ -268,6 +271,9 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             for (long long i = 0; i < S; ++i)
                 if (hp[i + 1] < hp[i]) { s = fail(nullptr, EPROP_EINVAL, "row_ptr must be non-decreasing"); goto fail_out; }
             net->nnz_in = hp[c.n_in];
+            long long mx = 0;
+            for (long long i = 0; i < S; ++i) mx = std::max(mx, hp[i + 1] - hp[i]);
+            n.segs = (int)std::max(1LL, (mx + eprop::kSeg - 1) / eprop::kSeg);
         }
         uint32_t *td;
         FA(tgt_d, uint32_t, nnz);
@@ -509,7 +515,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     if (!c.continuous) L += 1;                       // anchor fill
     eprop::launch_begin_call(n, c.continuous, st);
     L += 1;
-    const int grid_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 4) * net->sm_count;
+    const int grid_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 6) * net->sm_count;
     const int nw = T / U;
     if (c.profile && (int)net->ev.size() < 2 * nw) {
         for (int q = (int)net->ev.size(); q < 2 * nw; ++q) {
@@ -533,10 +539,8 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
                 LT += 1;
             } else {
-                // ascending emission steps: a synapse's first arrival of the
-                // window (which restores its stored state) precedes its others
-                for (int e = U + n.D - 1; e >= 1; --e) eprop::launch_trace_stream(n, i, e, grid_rows, st);
-                LT += U + n.D - 1;
+                eprop::launch_trace_window(n, i, grid_rows, st);
+                LT += 2;
             }
             if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin + 1], st, cudaEventRecordExternal);
             eprop::launch_readout_weights(n, i, st);

@@ -29,6 +29,9 @@
 namespace eprop {
 
 constexpr int kMaxDelay = 8;
+constexpr int kSeg = 256;          // synapses per work item of the row kernels
+constexpr int kSegPerLane = kSeg / 32;
+constexpr int kSpikeCap = 64;      // spikes of one row cached per warp
 constexpr int kMaxOut = 1024;
 constexpr double kFixScale = 4294967296.0;          // 2^32
 constexpr float kFixInv = 2.3283064365386963e-10f;  // 2^-32
@@ -47,6 +50,7 @@ struct Net {
     // model switches
     int alif, t_ref, loss, feedback, has_state, trace_bf16, record_grad, record_raster, record_psi;
     int n_thr, T;             // T of the current call
+    int segs;                 // work items per row: ceil(max out-degree / kSeg)
     // constants (float, computed on the host in double)
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
     float alpha_lo, rho_lo;   // alpha - (float)alpha, rho - (float)rho
@@ -84,6 +88,7 @@ struct Net {
     // window tables
     float *qp;
     float *coef;
+    long long *win_off;       // [U + D + 1] work-item offsets of the window
     // inputs of the current call
     const long long *x_ptr;
     const int *x_ids;

@@ -16,7 +16,7 @@ void launch_begin_call(const Net &n, int continuous, cudaStream_t st);
 void launch_end_call(const Net &n, int T, cudaStream_t st);
 void launch_filter_error(const Net &n, int i_end, cudaStream_t st);
 int launch_tables(const Net &n, int i_end, cudaStream_t st);
-void launch_trace_stream(const Net &n, int i_end, int e, int grid_x, cudaStream_t st);
+void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st);
 void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st);
 void launch_readout_weights(const Net &n, int i_end, cudaStream_t st);
 void launch_rollover(const Net &n, int i_end, cudaStream_t st);

@@ -216,17 +216,19 @@ __global__ void readout_error_kernel(Net n, int i) {
     if (threadIdx.x == 0) n.loss_acc[b] += tot;
 }
 
-// K2: transmission of the spikes of call step i.  One warp per spiking
-// source row; lanes stride over the row's synapses (coalesced 4-byte
-// streams).  The weight carried is the weight in effect at emission: with
-// per-synapse lazy updates, the gradient of update windows that closed
-// since the synapse's last arrival is added on the fly (read-only).
+// K2: transmission of the spikes of call step i.  Work items are (spiking
+// source row, segment of kSeg synapses); a warp handles one item with
+// kSegPerLane synapses per lane, loads hoisted for memory-level parallelism
+// (coalesced 4-byte streams).  The weight carried is the weight in effect at
+// emission: with per-synapse lazy updates, the gradient of update windows
+// that closed since the synapse's last arrival is added on the fly
+// (read-only).  Arrivals are summed in exact int64 fixed point.
 template <bool ALIF, bool STATE>
-__global__ void deliver_kernel(Net n, int i) {
+__global__ void __launch_bounds__(256) deliver_kernel(Net n, int i) {
     __shared__ RowInfo info[8][kMaxDelay + 1];
     __shared__ unsigned long long ev_block;
     const int b = blockIdx.y;
-    if (i > n.lengths[b]) return;
+    if (i > n.lengths[b]) return;            // whole block: same sample
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) ev_block = 0ULL;
     __syncthreads();
@@ -239,26 +241,44 @@ __global__ void deliver_kernel(Net n, int i) {
     const int *ids = n.list_ids + ((long long)b * n.RS + slot) * n.n_src;
     const int D1 = n.D + 1;
     long long *ring_b = n.ring + (long long)b * D1 * n.n_rec;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int row = gw; row < cnt; row += nw) {
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long items = (long long)cnt * n.segs;
+    for (long long it = gw; it < items; it += nw) {
+        const int row = (int)(it / n.segs), seg = (int)(it % n.segs);
         const int src = ids[row];
-        const long long q0 = n.row_ptr[src], q1 = n.row_ptr[src + 1];
-        ev_warp += (unsigned long long)(q1 - q0);
+        const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
+        const long long q0 = rb + (long long)seg * kSeg;
+        if (q0 >= re) continue;
+        const long long q1 = min(re, q0 + kSeg);
+        if (seg == 0 && lane == 0) ev_warp += (unsigned long long)(re - rb);
         if (STATE) {
             if (lane >= 1 && lane <= n.D)
                 info[warp][lane] = row_info(n, src_words(n, b, src), n.anchor_t[(long long)b * n.n_src + src],
                                             n.anchor_z[(long long)b * n.n_src + src], a0, lane, false);
             __syncwarp();
         }
-        for (long long q = q0 + lane; q < q1; q += 32) {
-            const uint32_t td = n.tgt_d[q];
-            const int j = (int)(td & 0xFFFFFFu);
-            const int d = (int)(td >> 24);
-            float wv = n.w[q];
-            if (STATE) {
+        uint32_t td[kSegPerLane];
+        float wv[kSegPerLane];
+#pragma unroll
+        for (int u = 0; u < kSegPerLane; ++u) {
+            const long long q = q0 + lane + 32 * u;
+            td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kSegPerLane; ++u) {
+            const long long q = q0 + lane + 32 * u;
+            wv[u] = q < q1 ? n.w[q] : 0.f;
+        }
+        if (STATE) {
+#pragma unroll
+            for (int u = 0; u < kSegPerLane; ++u) {
+                if (td[u] == 0u) continue;
+                const int d = (int)(td[u] >> 24);
                 const RowInfo ri = info[warp][d];
                 if (ri.b_prev != kNoSpike && ri.b_prev < a0) {
+                    const long long q = q0 + lane + 32 * u;
+                    const int j = (int)(td[u] & 0xFFFFFFu);
                     float zbar = ri.zbar_bp;
                     float ebar = load_trace(n.ebar, q, n.trace_bf16);
                     float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.0f;
@@ -270,10 +290,16 @@ __global__ void deliver_kernel(Net n, int i) {
                         k0 = k1 - n.RC;
                     }
                     for (int k = k0; k < k1; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
-                    wv -= n.lr * G;
+                    wv[u] -= n.lr * G;
                 }
             }
-            const long long fx = __float2ll_rn(wv * 4294967296.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < kSegPerLane; ++u) {
+            if (td[u] == 0u) continue;
+            const int j = (int)(td[u] & 0xFFFFFFu);
+            const int d = (int)(td[u] >> 24);
+            const long long fx = __float2ll_rn(wv[u] * 4294967296.0f);
             atomicAdd(reinterpret_cast<unsigned long long *>(
                           &ring_b[(long long)((t_abs + d) % D1) * n.n_rec + j]),
                       (unsigned long long)fx);

@@ -17,6 +17,8 @@
 // and an arrival costs one table lookup instead of a loop over the history.
 // The paper's event-driven algorithm (Algorithm 5) instead loops over the
 // archived psi/L history of the inter-spike interval; the sums are the same.
+#include <type_traits>
+
 #include "eprop_internal.cuh"
 #include "eprop_launch.h"
 
@@ -134,30 +136,38 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
         return acc;
     };
     const float *psi = n.psi_hist + (long long)b * (U + 1) * N + j;
-    const float alpha = n.alpha, rho = n.rho, beta = n.beta_a, ke = n.kappa_e;
-    float pn = psi[(long long)U * N];          // psi^b
-    const float psi_b = pn;
+    // The adjoint sweep is the per-window reduction of the gradient.  For
+    // ALIF the eligibility psi (zbar - beta eps_a) is a near-cancellation of
+    // two long-memory traces, so the sweep runs in FP64 there (FP32 loses up
+    // to 1e-1 relative on some elements over a few hundred steps); the LIF
+    // sweep has no such cancellation and runs in FP32.
+    using R = typename std::conditional<ALIF, double, float>::type;
+    const R alpha = (R)n.alpha + (R)n.alpha_lo;
+    const R rho = ALIF ? (R)n.rho + (R)n.rho_lo : (R)0;
+    const R beta = n.beta_a;
+    const R ke = n.kappa_e;
+    R pn = psi[(long long)U * N];          // psi^b
+    const float psi_b = psi[(long long)U * N];
     // adjoint of G (mz, ma, me); of ebar^b (ez, ea, ee); of eps_a^b (az, aa, ae)
-    float mz = 0.f, ma = 0.f, me = Lat(U);
-    float ez = 0.f, ea = 0.f, ee = 1.f;
-    float az = 0.f, aa = 1.f, ae = 0.f;
+    R mz = 0, ma = 0, me = Lat(U);
+    R ez = 0, ea = 0, ee = 1;
+    R az = 0, aa = 1, ae = 0;
     long long qbase = ((long long)b * U) * N + j;
     if (ALIF) {
         reinterpret_cast<float4 *>(n.qp)[qbase + (long long)(U - 1) * N] =
-            make_float4(mz + pn * me, ez + pn * ee, az + pn * ae, 0.f);
+            make_float4((float)(mz + pn * me), (float)(ez + pn * ee), (float)(az + pn * ae), 0.f);
     } else {
         reinterpret_cast<float2 *>(n.qp)[qbase + (long long)(U - 1) * N] =
-            make_float2(mz + pn * me, ez + pn * ee);
+            make_float2((float)(mz + pn * me), (float)(ez + pn * ee));
     }
     for (int u = U - 1; u >= 0; --u) {
-        const float p = psi[(long long)u * N];       // psi^{a0+u}
+        const R p = psi[(long long)u * N];       // psi^{a0+u}
         // x -> (A^{u+1})^T x
-        float nz, na, ne;
         if (ALIF) {
-            const float g1 = alpha - beta * p, g2 = rho - beta * p;
-            nz = alpha * mz + p * ma + pn * g1 * me;
-            na = g2 * ma - beta * pn * g2 * me;
-            ne = ke * me;
+            const R g1 = alpha - beta * p, g2 = rho - beta * p;
+            R nz = alpha * mz + p * ma + pn * g1 * me;
+            R na = g2 * ma - beta * pn * g2 * me;
+            R ne = ke * me;
             mz = nz; ma = na; me = ne;
             nz = alpha * ez + p * ea + pn * g1 * ee;
             na = g2 * ea - beta * pn * g2 * ee;
@@ -174,13 +184,13 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
             ee = ke * ee;
         }
         if (u >= 1) {
-            me += Lat(u);
+            me += (R)Lat(u);
             if (ALIF) {
                 reinterpret_cast<float4 *>(n.qp)[qbase + (long long)(u - 1) * N] =
-                    make_float4(mz + p * me, ez + p * ee, az + p * ae, 0.f);
+                    make_float4((float)(mz + p * me), (float)(ez + p * ee), (float)(az + p * ae), 0.f);
             } else {
                 reinterpret_cast<float2 *>(n.qp)[qbase + (long long)(u - 1) * N] =
-                    make_float2(mz + p * me, ez + p * ee);
+                    make_float2((float)(mz + p * me), (float)(ez + p * ee));
             }
         }
         pn = p;
@@ -190,92 +200,212 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
         const int slot = (a0 / U) % n.RC;
         if (ALIF) {
             float4 *c = reinterpret_cast<float4 *>(n.coef) + ((long long)slot * N + j) * 2;
-            c[0] = make_float4(mz, ma, me, az);
-            c[1] = make_float4(aa, ez, ea, 0.f);
+            c[0] = make_float4((float)mz, (float)ma, (float)me, (float)az);
+            c[1] = make_float4((float)aa, (float)ez, (float)ea, 0.f);
         } else {
-            reinterpret_cast<float4 *>(n.coef)[(long long)slot * N + j] = make_float4(mz, me, ez, 0.f);
+            reinterpret_cast<float4 *>(n.coef)[(long long)slot * N + j] =
+                make_float4((float)mz, (float)me, (float)ez, 0.f);
         }
     }
     n.psi_hist[(long long)b * (U + 1) * N + j] = psi_b;     // slot 0 of the next window
 }
 
-// event-driven synapse trace + gradient, streaming form: one launch per
-// emission step s = b - e of the window's arrivals, rows = sources that spiked
-// at s; every synapse of the row whose arrival s + d lies in the window is
-// advanced in closed form and its weight updated.  Table slabs of the
-// arrival steps s+1..s+D stay resident in L2 while the record streams pass.
+// Work-item offsets of one window: for the emission steps s = s_lo..s_hi
+// whose spikes arrive in the window, off[k] = sum_{k' < k} rows(s_lo + k') *
+// segs (every spiking row contributes `segs` segments of kSeg synapses).
+__global__ void window_offsets_kernel(Net n, int i_end) {
+    const int r_end = run_step_w(n, i_end);
+    const int a0 = r_end - n.U;
+    const int s_lo = max(a0 + 1 - n.D, 1);
+    const int nsteps = r_end - 1 - s_lo + 1;
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int k = 0; k < nsteps; ++k) {
+            n.win_off[k] = acc;
+            acc += (long long)n.list_cnt[(s_lo + k) % n.RS] * n.segs;
+        }
+        n.win_off[nsteps > 0 ? nsteps : 0] = acc;
+    }
+}
+
+__device__ __forceinline__ bool any_spike(const uint32_t *words, int RW, int lo, int hi) {
+    const int mask = RW * 32 - 1;
+    int r = lo < 1 ? 1 : lo;
+    while (r <= hi) {
+        const int p = r & mask;
+        const int bit = p & 31;
+        const int span = min(31 - bit, hi - r);
+        uint32_t m = words[p >> 5] >> bit;
+        if (span < 31) m &= (2u << span) - 1u;
+        if (m) return true;
+        r += span + 1;
+    }
+    return false;
+}
+
+// Event-driven synapse trace + gradient of one update window (the metric
+// kernel).  Work items are (spiking row, segment of kSeg synapses) in
+// ascending emission step; the item of a row's first spike among the
+// window's emission steps advances every synapse of its segment over all of
+// the row's arrivals in the window, in order, so each synapse is touched by
+// exactly one warp per window.  A synapse's first arrival restores its state
+// from the end of the window of its previous arrival (catch-up through the
+// skipped windows' coefficients); every arrival a adds Q(a) to the window's
+// gradient and Pe(a), Pa(a) to the state.  Record streams are read once
+// (tgt_d evict-first); the table slabs of the steps in flight stay in L2.
 template <bool ALIF, bool STATE>
-__global__ void __launch_bounds__(256) trace_stream_kernel(Net n, int i_end, int e) {
+__global__ void __launch_bounds__(256) trace_window_kernel(Net n, int i_end) {
+    extern __shared__ long long off[];
     __shared__ RowInfo info[8][kMaxDelay + 1];
+    __shared__ int spk[8][kSpikeCap];
     const int U = n.U, N = n.n_rec;
     const int r_end = run_step_w(n, i_end);
     const int a0 = r_end - U;
-    const int s = r_end - e;
-    if (s < 1) return;
+    const int s_lo = max(a0 + 1 - n.D, 1);
+    const int s_hi = r_end - 1;
+    const int nsteps = s_hi - s_lo + 1;
+    if (nsteps <= 0) return;
+    for (int k = threadIdx.x; k <= nsteps; k += blockDim.x) off[k] = n.win_off[k];
+    __syncthreads();
+    const long long total = off[nsteps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = s % n.RS;
-    const int cnt = n.list_cnt[slot];
-    const int *ids = n.list_ids + (long long)slot * n.n_src;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int nw = gridDim.x * (blockDim.x >> 5);
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     const int kW = a0 / U;
     const float step = n.lr * n.inv_B;
-    for (int row = gw; row < cnt; row += nw) {
-        const int src = ids[row];
-        const long long q0 = n.row_ptr[src], q1 = n.row_ptr[src + 1];
-        if (STATE) {
-            if (lane >= 1 && lane <= n.D)
-                info[warp][lane] = row_info(n, src_words_c(n, 0, src), n.anchor_t[src],
-                                            n.anchor_z[src], a0, lane, true);
-            __syncwarp();
+    for (long long it = gw; it < total; it += nw) {
+        int lo = 0, hi = nsteps;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= it) lo = mid; else hi = mid;
         }
-        for (long long q = q0 + lane; q < q1; q += 32) {
-            const uint32_t td = __ldcs(n.tgt_d + q);
-            const int j = (int)(td & 0xFFFFFFu);
-            const int d = (int)(td >> 24);
-            const int a = s + d;
-            if (a <= a0 || a > r_end) continue;
-            const long long qi = (long long)(a - a0 - 1) * N + j;
-            float Q, Pe, Pa = 0.f;
-            if (ALIF) {
-                const float4 t = reinterpret_cast<const float4 *>(n.qp)[qi];
-                Q = t.x; Pe = t.y; Pa = t.z;
-            } else {
-                const float2 t = reinterpret_cast<const float2 *>(n.qp)[qi];
-                Q = t.x; Pe = t.y;
-            }
-            float G;
-            if (STATE) {
-                const RowInfo ri = info[warp][d];
-                float ebar = 0.f, epsa = 0.f;
-                G = 0.f;
-                if (s == ri.s_first) {
-                    if (ri.b_prev != kNoSpike) {
-                        float zbar = ri.zbar_bp;
-                        ebar = load_trace(n.ebar, q, n.trace_bf16);
-                        if (ALIF) epsa = load_trace(n.epsa, q, n.trace_bf16);
-                        int k0 = ri.b_prev / U;
-                        if (kW - k0 > n.RC - 1) {
-                            atomicOr(n.err_flags, 1u);
-                            k0 = kW - (n.RC - 1);
-                        }
-                        for (int k = k0; k <= kW; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
-                    }
-                } else {
-                    ebar = load_trace(n.ebar, q, n.trace_bf16);
-                    if (ALIF) epsa = load_trace(n.epsa, q, n.trace_bf16);
+        const int s = s_lo + lo;
+        const long long rem = it - off[lo];
+        const int row = (int)(rem / n.segs), seg = (int)(rem % n.segs);
+        const int src = n.list_ids[(long long)(s % n.RS) * n.n_src + row];
+        const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
+        const long long q0 = rb + (long long)seg * kSeg;
+        if (q0 >= re) continue;
+        const long long q1 = min(re, q0 + kSeg);
+        const uint32_t *words = src_words_c(n, 0, src);
+        if (any_spike(words, n.RW, s_lo, s - 1)) continue;   // another item owns the row
+        int ns = 0;
+        if (lane == 0) {             // the row's spikes in [s, s_hi], ascending
+            const int mask = n.RW * 32 - 1;
+            int r = s;
+            while (r <= s_hi) {
+                const int p = r & mask;
+                const int bit = p & 31;
+                const int span = min(31 - bit, s_hi - r);
+                uint32_t m = words[p >> 5] >> bit;
+                if (span < 31) m &= (2u << span) - 1u;
+                while (m) {
+                    if (ns < kSpikeCap) spk[warp][ns] = r + __ffs(m) - 1;
+                    ++ns;
+                    m &= m - 1;
                 }
-                G += Q;
-                ebar += Pe;
-                store_trace(n.ebar, q, ebar, n.trace_bf16);
-                if (ALIF) store_trace(n.epsa, q, epsa + Pa, n.trace_bf16);
-            } else {
-                G = Q;
+                r += span + 1;
             }
-            n.w[q] -= step * G;
+        }
+        ns = __shfl_sync(0xffffffffu, ns, 0);
+        if (STATE && lane >= 1 && lane <= n.D)
+            info[warp][lane] = row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false);
+        __syncwarp();
+        uint32_t td[kSegPerLane];
+#pragma unroll
+        for (int u = 0; u < kSegPerLane; ++u) {
+            const long long q = q0 + lane + 32 * u;
+            td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
+        }
+        float wv[kSegPerLane], eb[kSegPerLane], ep[kSegPerLane];
+        int c0[kSegPerLane];
+        const bool listed = ns <= kSpikeCap;
+#pragma unroll
+        for (int u = 0; u < kSegPerLane; ++u) {
+            const long long q = q0 + lane + 32 * u;
+            const int d = (int)(td[u] >> 24);
+            bool has = false;
+            int c = 0;
+            if (td[u] != 0u) {
+                if (listed) {       // first listed spike whose arrival lies after a0
+                    while (c < ns && spk[warp][c] + d <= a0) ++c;
+                    has = c < ns && spk[warp][c] + d <= r_end;
+                } else {
+                    has = any_spike(words, n.RW, max(s, a0 + 1 - d), r_end - d);
+                }
+            }
+            c0[u] = has ? c : -1;
+            wv[u] = has ? n.w[q] : 0.f;
+            eb[u] = (STATE && has) ? load_trace(n.ebar, q, n.trace_bf16) : 0.f;
+            ep[u] = (STATE && ALIF && has) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kSegPerLane; ++u) {
+            if (c0[u] < 0) continue;
+            const long long q = q0 + lane + 32 * u;
+            const int j = (int)(td[u] & 0xFFFFFFu);
+            const int d = (int)(td[u] >> 24);
+            float G = 0.f, ebar = eb[u], epsa = ep[u];
+            if (STATE) {            // the window's first arrival: restore the state
+                const RowInfo ri = info[warp][d];
+                if (ri.b_prev != kNoSpike) {
+                    float zbar = ri.zbar_bp;
+                    int k0 = ri.b_prev / U;
+                    if (kW - k0 > n.RC - 1) {
+                        atomicOr(n.err_flags, 1u);
+                        k0 = kW - (n.RC - 1);
+                    }
+                    for (int k = k0; k <= kW; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                } else {
+                    ebar = 0.f;
+                    epsa = 0.f;
+                }
+            }
+            const long long qrow = (long long)(-a0 - 1) * N + j;   // + a * N
+            if (listed) {
+                for (int c = c0[u]; c < ns; ++c) {
+                    const int a = spk[warp][c] + d;
+                    if (a > r_end) break;
+                    if (ALIF) {
+                        const float4 t = reinterpret_cast<const float4 *>(n.qp)[qrow + (long long)a * N];
+                        G += t.x; ebar += t.y; epsa += t.z;
+                    } else {
+                        const float2 t = reinterpret_cast<const float2 *>(n.qp)[qrow + (long long)a * N];
+                        G += t.x; ebar += t.y;
+                    }
+                }
+            } else {                // rows with more spikes than the cache holds
+                const int mask = n.RW * 32 - 1;
+                const int hi = r_end - d;
+                int r = max(s, a0 + 1 - d);
+                while (r <= hi) {
+                    const int p = r & mask;
+                    const int bit = p & 31;
+                    const int span = min(31 - bit, hi - r);
+                    uint32_t m = words[p >> 5] >> bit;
+                    if (span < 31) m &= (2u << span) - 1u;
+                    while (m) {
+                        const int a = r + __ffs(m) - 1 + d;
+                        m &= m - 1;
+                        if (ALIF) {
+                            const float4 t = reinterpret_cast<const float4 *>(n.qp)[qrow + (long long)a * N];
+                            G += t.x; ebar += t.y; epsa += t.z;
+                        } else {
+                            const float2 t = reinterpret_cast<const float2 *>(n.qp)[qrow + (long long)a * N];
+                            G += t.x; ebar += t.y;
+                        }
+                    }
+                    r += span + 1;
+                }
+            }
+            n.w[q] = wv[u] - step * G;
+            if (STATE) {
+                store_trace(n.ebar, q, ebar, n.trace_bf16);
+                if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
+            }
             if (n.record_grad) n.grad[q] += n.inv_B * G;
         }
-        if (STATE) __syncwarp();
+        __syncwarp();
     }
 }
 
@@ -473,6 +603,11 @@ void prepare_kernel_attributes() {
     const int limit = 200 * 1024;
     cudaFuncSetAttribute(tables_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(tables_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    const int tl = 160 * 1024;
+    cudaFuncSetAttribute(trace_window_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
+    cudaFuncSetAttribute(trace_window_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
+    cudaFuncSetAttribute(trace_window_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
+    cudaFuncSetAttribute(trace_window_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
 }
 
 void launch_begin_call(const Net &n, int continuous, cudaStream_t st) {
@@ -501,13 +636,15 @@ int launch_tables(const Net &n, int i_end, cudaStream_t st) {
     return 0;
 }
 
-void launch_trace_stream(const Net &n, int i_end, int e, int grid_x, cudaStream_t st) {
+void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st) {
+    window_offsets_kernel<<<1, 32, 0, st>>>(n, i_end);
+    const size_t sm = (size_t)(n.U + n.D + 1) * sizeof(long long);
     if (n.has_state) {
-        if (n.alif) trace_stream_kernel<true, true><<<grid_x, 256, 0, st>>>(n, i_end, e);
-        else trace_stream_kernel<false, true><<<grid_x, 256, 0, st>>>(n, i_end, e);
+        if (n.alif) trace_window_kernel<true, true><<<grid_x, 256, sm, st>>>(n, i_end);
+        else trace_window_kernel<false, true><<<grid_x, 256, sm, st>>>(n, i_end);
     } else {
-        if (n.alif) trace_stream_kernel<true, false><<<grid_x, 256, 0, st>>>(n, i_end, e);
-        else trace_stream_kernel<false, false><<<grid_x, 256, 0, st>>>(n, i_end, e);
+        if (n.alif) trace_window_kernel<true, false><<<grid_x, 256, sm, st>>>(n, i_end);
+        else trace_window_kernel<false, false><<<grid_x, 256, sm, st>>>(n, i_end);
     }
 }
 

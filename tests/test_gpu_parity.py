@@ -129,7 +129,7 @@ def _replica(continuous, T, **kw):
     base = dict(n_rec=4000, k_in=400, J=0.025, n_out=10, T=T, lr=1e-5)
     base.update(kw)
     if continuous:
-        return C.million_sparse(**base)
+        return C.million_sparse(drive_rate=1.25, **base)
     return C.sparse_balanced(n_coupled=500, drive_weight=0.03, drive_rate=1.25, **base)
 
 
@@ -179,11 +179,11 @@ def test_event_classification_alif_batch_uneven_lengths():
 
 def test_sparse_replica_single_window_batched_kernel():
     W = _replica(False, 400)
-    rep = run_parity(W)
+    rep = run_parity(W, gpu_kw=dict(trace_kernel=2))
     assert rep["events"] > 0
 
 
-def test_sparse_replica_single_window_streaming_kernel():
+def test_sparse_replica_single_window_window_kernel():
     W = _replica(False, 400)
     rep = run_parity(W, gpu_kw=dict(trace_kernel=1))
     assert rep["events"] > 0

@@ -365,9 +365,10 @@ def sparse_balanced(seed: int = 1236, n_rec: int = 100_000, k_in: int = 1000,
 
 def million_sparse_spec(n_rec: int = 1_000_000, T: int = 1000, n_out: int = 100,
                         seed: int = 1237, **over) -> Spec:
+    # drive 0.03 x Poisson(0.85) per step: ~5 Hz at 1e6 neurons, in-degree 1000
     spec = Spec(name="million_sparse", n_in=0, n_rec=n_rec, n_out=n_out, T=T,
                 feedback=1, update_interval=100, continuous=1, lr=1e-6,
-                max_delay=5, drive_weight=0.03, drive_rate=1.25,
+                max_delay=5, drive_weight=0.03, drive_rate=0.85,
                 drive_seed=seed * 7919 + 17, seed=seed)
     for key, val in over.items():
         setattr(spec, key, val)
