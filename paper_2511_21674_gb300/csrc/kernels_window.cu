@@ -243,6 +243,50 @@ __device__ __forceinline__ bool any_spike(const uint32_t *words, int RW, int lo,
     return false;
 }
 
+
+// Rare paths of the trace kernel kept out of line (instruction-cache
+// footprint of the unrolled hot loop).
+template <bool ALIF>
+__device__ __noinline__ float catch_up(const Net n, int j, int k0, int kW, float zbar, float &epsa,
+                                       float &ebar) {
+    float G = 0.f;
+    if (kW - k0 > n.RC - 1) {
+        atomicOr(n.err_flags, 1u);
+        k0 = kW - (n.RC - 1);
+    }
+    for (int k = k0; k <= kW; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+    return G;
+}
+
+template <bool ALIF>
+__device__ __noinline__ float scan_arrivals(const Net n, const uint32_t *words, int lo, int hi, int d,
+                                            long long qrow, float &ebar, float &epsa) {
+    const int N = n.n_rec;
+    const int mask = n.RW * 32 - 1;
+    float G = 0.f;
+    int r = lo;
+    while (r <= hi) {
+        const int p = r & mask;
+        const int bit = p & 31;
+        const int span = min(31 - bit, hi - r);
+        uint32_t m = words[p >> 5] >> bit;
+        if (span < 31) m &= (2u << span) - 1u;
+        while (m) {
+            const int a = r + __ffs(m) - 1 + d;
+            m &= m - 1;
+            if (ALIF) {
+                const float4 t = reinterpret_cast<const float4 *>(n.qp)[qrow + (long long)a * N];
+                G += t.x; ebar += t.y; epsa += t.z;
+            } else {
+                const float2 t = reinterpret_cast<const float2 *>(n.qp)[qrow + (long long)a * N];
+                G += t.x; ebar += t.y;
+            }
+        }
+        r += span + 1;
+    }
+    return G;
+}
+
 // Event-driven synapse trace + gradient of one update window (the metric
 // kernel).  Work items are (spiking row, segment of kSeg synapses) in
 // ascending emission step; the item of a row's first spike among the
@@ -254,7 +298,7 @@ __device__ __forceinline__ bool any_spike(const uint32_t *words, int RW, int lo,
 // gradient and Pe(a), Pa(a) to the state.  Record streams are read once
 // (tgt_d evict-first); the table slabs of the steps in flight stay in L2.
 template <bool ALIF, bool STATE>
-__global__ void __launch_bounds__(256) trace_window_kernel(Net n, int i_end) {
+__global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) {
     extern __shared__ long long off[];
     __shared__ RowInfo info[8][kMaxDelay + 1];
     __shared__ int spk[8][kSpikeCap];
@@ -349,13 +393,7 @@ __global__ void __launch_bounds__(256) trace_window_kernel(Net n, int i_end) {
             if (STATE) {            // the window's first arrival: restore the state
                 const RowInfo ri = info[warp][d];
                 if (ri.b_prev != kNoSpike) {
-                    float zbar = ri.zbar_bp;
-                    int k0 = ri.b_prev / U;
-                    if (kW - k0 > n.RC - 1) {
-                        atomicOr(n.err_flags, 1u);
-                        k0 = kW - (n.RC - 1);
-                    }
-                    for (int k = k0; k <= kW; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                    G = catch_up<ALIF>(n, j, ri.b_prev / U, kW, ri.zbar_bp, epsa, ebar);
                 } else {
                     ebar = 0.f;
                     epsa = 0.f;
@@ -375,28 +413,7 @@ __global__ void __launch_bounds__(256) trace_window_kernel(Net n, int i_end) {
                     }
                 }
             } else {                // rows with more spikes than the cache holds
-                const int mask = n.RW * 32 - 1;
-                const int hi = r_end - d;
-                int r = max(s, a0 + 1 - d);
-                while (r <= hi) {
-                    const int p = r & mask;
-                    const int bit = p & 31;
-                    const int span = min(31 - bit, hi - r);
-                    uint32_t m = words[p >> 5] >> bit;
-                    if (span < 31) m &= (2u << span) - 1u;
-                    while (m) {
-                        const int a = r + __ffs(m) - 1 + d;
-                        m &= m - 1;
-                        if (ALIF) {
-                            const float4 t = reinterpret_cast<const float4 *>(n.qp)[qrow + (long long)a * N];
-                            G += t.x; ebar += t.y; epsa += t.z;
-                        } else {
-                            const float2 t = reinterpret_cast<const float2 *>(n.qp)[qrow + (long long)a * N];
-                            G += t.x; ebar += t.y;
-                        }
-                    }
-                    r += span + 1;
-                }
+                G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - d), r_end - d, d, qrow, ebar, epsa);
             }
             n.w[q] = wv[u] - step * G;
             if (STATE) {
