@@ -18,8 +18,9 @@
 //     presynaptic trace sum_s alpha^{t-s} right after it
 //   per-step spike lists (ring of RS steps) [B][RS][S] i32 + counts
 //   window tables [B][U][N] float2 (LIF: Q, Pe) or float4 (ALIF: Q, Pe, Pa)
-//   window coefficients (ring of RC windows) [RC][N] float4 (LIF) or
-//     2 x float4 (ALIF)
+//   window coefficients (ring of RC windows) [N][RC] float4 (LIF) or
+//     2 x float4 (ALIF): neuron-major, so a catch-up over consecutive
+//     windows reads contiguous entries
 //   readout: W_out [N][K], B [N][K], y [B][K], error window [B][U][K]
 #pragma once
 #include <cuda_runtime.h>
@@ -151,13 +152,18 @@ __device__ __forceinline__ bool bit_at(const uint32_t *words, int RW, int r) {
     return (words[p >> 5] >> (p & 31)) & 1u;
 }
 
+// Record streams are touched once per event: evict-first loads and
+// streaming stores keep them from displacing the lookup tables in L2.
 __device__ __forceinline__ float load_trace(const void *base, long long q, int bf16) {
-    if (bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[q]);
-    return reinterpret_cast<const float *>(base)[q];
+    if (bf16) {
+        const unsigned short h = __ldcs(reinterpret_cast<const unsigned short *>(base) + q);
+        return __bfloat162float(__ushort_as_bfloat16(h));
+    }
+    return __ldcs(reinterpret_cast<const float *>(base) + q);
 }
 __device__ __forceinline__ void store_trace(void *base, long long q, float x, int bf16) {
-    if (bf16) reinterpret_cast<__nv_bfloat16 *>(base)[q] = __float2bfloat16_rn(x);
-    else reinterpret_cast<float *>(base)[q] = x;
+    if (bf16) __stcs(reinterpret_cast<unsigned short *>(base) + q, __bfloat16_as_ushort(__float2bfloat16_rn(x)));
+    else __stcs(reinterpret_cast<float *>(base) + q, x);
 }
 
 // Presynaptic summary of one source row for one delay d, relative to the
@@ -225,7 +231,7 @@ __device__ __forceinline__ void apply_window(const Net &n, long long j, int k, f
                                              float &epsa, float &ebar, float &G) {
     const int slot = k % n.RC;
     if (ALIF) {
-        const float4 *c = reinterpret_cast<const float4 *>(n.coef) + ((long long)slot * n.n_rec + j) * 2;
+        const float4 *c = reinterpret_cast<const float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
         const float4 c0 = c[0], c1 = c[1];   // (cz, ca, ce, maz), (maa, mez, mea, -)
         G += c0.x * zbar + c0.y * epsa + c0.z * ebar;
         const float ea = c0.w * zbar + c1.x * epsa;
@@ -233,7 +239,7 @@ __device__ __forceinline__ void apply_window(const Net &n, long long j, int k, f
         epsa = ea;
         ebar = ee;
     } else {
-        const float4 c = reinterpret_cast<const float4 *>(n.coef)[(long long)slot * n.n_rec + j];
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(n.coef) + (long long)j * n.RC + slot);
         G += c.x * zbar + c.y * ebar;        // (cz, ce, mez, -)
         ebar = c.z * zbar + n.kappaeU * ebar;
     }

@@ -243,21 +243,19 @@ __global__ void __launch_bounds__(256) deliver_kernel(Net n, int i) {
     long long *ring_b = n.ring + (long long)b * D1 * n.n_rec;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long items = (long long)cnt * n.segs;
-    for (long long it = gw; it < items; it += nw) {
-        const int row = (int)(it / n.segs), seg = (int)(it % n.segs);
+    for (long long row = gw; row < cnt; row += nw) {
         const int src = ids[row];
         const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
-        const long long q0 = rb + (long long)seg * kSeg;
-        if (q0 >= re) continue;
-        const long long q1 = min(re, q0 + kSeg);
-        if (seg == 0 && lane == 0) ev_warp += (unsigned long long)(re - rb);
+        if (re <= rb) continue;
+        if (lane == 0) ev_warp += (unsigned long long)(re - rb);
         if (STATE) {
             if (lane >= 1 && lane <= n.D)
                 info[warp][lane] = row_info(n, src_words(n, b, src), n.anchor_t[(long long)b * n.n_src + src],
                                             n.anchor_z[(long long)b * n.n_src + src], a0, lane, false);
             __syncwarp();
         }
+        for (long long q0 = rb; q0 < re; q0 += kSeg) {
+        const long long q1 = min(re, q0 + kSeg);
         uint32_t td[kSegPerLane];
         float wv[kSegPerLane];
 #pragma unroll
@@ -268,7 +266,7 @@ __global__ void __launch_bounds__(256) deliver_kernel(Net n, int i) {
 #pragma unroll
         for (int u = 0; u < kSegPerLane; ++u) {
             const long long q = q0 + lane + 32 * u;
-            wv[u] = q < q1 ? n.w[q] : 0.f;
+            wv[u] = q < q1 ? __ldcs(n.w + q) : 0.f;
         }
         if (STATE) {
 #pragma unroll
@@ -304,6 +302,7 @@ __global__ void __launch_bounds__(256) deliver_kernel(Net n, int i) {
                           &ring_b[(long long)((t_abs + d) % D1) * n.n_rec + j]),
                       (unsigned long long)fx);
         }
+        }                            // segments of the row
         if (STATE) __syncwarp();
     }
     if (lane == 0 && ev_warp) atomicAdd(&ev_block, ev_warp);

@@ -199,11 +199,11 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
     if (n.has_state) {
         const int slot = (a0 / U) % n.RC;
         if (ALIF) {
-            float4 *c = reinterpret_cast<float4 *>(n.coef) + ((long long)slot * N + j) * 2;
+            float4 *c = reinterpret_cast<float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
             c[0] = make_float4((float)mz, (float)ma, (float)me, (float)az);
             c[1] = make_float4((float)aa, (float)ez, (float)ea, 0.f);
         } else {
-            reinterpret_cast<float4 *>(n.coef)[(long long)slot * N + j] =
+            reinterpret_cast<float4 *>(n.coef)[(long long)j * n.RC + slot] =
                 make_float4((float)mz, (float)me, (float)ez, 0.f);
         }
     }
@@ -211,8 +211,7 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
 }
 
 // Work-item offsets of one window: for the emission steps s = s_lo..s_hi
-// whose spikes arrive in the window, off[k] = sum_{k' < k} rows(s_lo + k') *
-// segs (every spiking row contributes `segs` segments of kSeg synapses).
+// whose spikes arrive in the window, off[k] = sum_{k' < k} rows(s_lo + k').
 __global__ void window_offsets_kernel(Net n, int i_end) {
     const int r_end = run_step_w(n, i_end);
     const int a0 = r_end - n.U;
@@ -222,7 +221,7 @@ __global__ void window_offsets_kernel(Net n, int i_end) {
         long long acc = 0;
         for (int k = 0; k < nsteps; ++k) {
             n.win_off[k] = acc;
-            acc += (long long)n.list_cnt[(s_lo + k) % n.RS] * n.segs;
+            acc += (long long)n.list_cnt[(s_lo + k) % n.RS];
         }
         n.win_off[nsteps > 0 ? nsteps : 0] = acc;
     }
@@ -324,13 +323,10 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
             if (off[mid] <= it) lo = mid; else hi = mid;
         }
         const int s = s_lo + lo;
-        const long long rem = it - off[lo];
-        const int row = (int)(rem / n.segs), seg = (int)(rem % n.segs);
+        const int row = (int)(it - off[lo]);
         const int src = n.list_ids[(long long)(s % n.RS) * n.n_src + row];
         const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
-        const long long q0 = rb + (long long)seg * kSeg;
-        if (q0 >= re) continue;
-        const long long q1 = min(re, q0 + kSeg);
+        if (re <= rb) continue;
         const uint32_t *words = src_words_c(n, 0, src);
         if (any_spike(words, n.RW, s_lo, s - 1)) continue;   // another item owns the row
         int ns = 0;
@@ -355,6 +351,8 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
         if (STATE && lane >= 1 && lane <= n.D)
             info[warp][lane] = row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false);
         __syncwarp();
+        for (long long q0 = rb; q0 < re; q0 += kSeg) {
+        const long long q1 = min(re, q0 + kSeg);
         uint32_t td[kSegPerLane];
 #pragma unroll
         for (int u = 0; u < kSegPerLane; ++u) {
@@ -379,7 +377,7 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
                 }
             }
             c0[u] = has ? c : -1;
-            wv[u] = has ? n.w[q] : 0.f;
+            wv[u] = has ? __ldcs(n.w + q) : 0.f;
             eb[u] = (STATE && has) ? load_trace(n.ebar, q, n.trace_bf16) : 0.f;
             ep[u] = (STATE && ALIF && has) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
         }
@@ -415,13 +413,14 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
             } else {                // rows with more spikes than the cache holds
                 G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - d), r_end - d, d, qrow, ebar, epsa);
             }
-            n.w[q] = wv[u] - step * G;
+            __stcs(n.w + q, wv[u] - step * G);
             if (STATE) {
                 store_trace(n.ebar, q, ebar, n.trace_bf16);
                 if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
             }
             if (n.record_grad) n.grad[q] += n.inv_B * G;
         }
+        }                            // segments of the row
         __syncwarp();
     }
 }
