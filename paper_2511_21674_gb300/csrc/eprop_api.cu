@@ -162,8 +162,9 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
         n.field = reinterpret_cast<decltype(n.field)>(p);                        \
     } while (0)
     WA(bits, uint32_t, B * S * n.RW);
-    WA(list_ids, int, B * n.RS * S);
-    WA(list_cnt, int, B * n.RS);
+    n.list_cap = (int)((((S + 255) / 256) + eprop::kBkt - 1) / eprop::kBkt * 256);
+    WA(list_ids, int, B * n.RS * eprop::kBkt * (long long)n.list_cap);
+    WA(list_cnt, int, B * n.RS * eprop::kBkt);
     WA(psi_hist, float, B * (U + 1) * N);
     WA(E_win, float, B * U * K);
     WA(Ebar_win, float, B * U * K);
@@ -497,7 +498,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         cudaMemsetAsync(n.z_prev, 0, B * N, st);
         cudaMemsetAsync(n.ring, 0, B * (n.D + 1) * N * 8, st);
         cudaMemsetAsync(n.bits, 0, B * S * n.RW * 4, st);
-        cudaMemsetAsync(n.list_cnt, 0, B * n.RS * 4, st);
+        cudaMemsetAsync(n.list_cnt, 0, B * n.RS * eprop::kBkt * 4, st);
         cudaMemsetAsync(n.y, 0, B * K * 4, st);
         cudaMemsetAsync(n.y_acc, 0, B * K * 8, st);
         cudaMemsetAsync(n.zk, 0, 2 * B * N * 4, st);

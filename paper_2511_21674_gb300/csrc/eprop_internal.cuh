@@ -16,7 +16,9 @@
 //   source spike bits [B][S][RW] u32: a ring of RW*32 >= U+D steps per source
 //   source anchor [B][S]: last spike before the ring range and the
 //     presynaptic trace sum_s alpha^{t-s} right after it
-//   per-step spike lists (ring of RS steps) [B][RS][S] i32 + counts
+//   per-step spike lists (ring of RS steps) [B][RS][kBkt][cap] i32 with
+//     counts [B][RS][kBkt]: a source appends to bucket (src >> 8) % kBkt, so
+//     the appends of one step spread over kBkt counters
 //   window tables [B][U][N] float2 (LIF: Q, Pe) or float4 (ALIF: Q, Pe, Pa)
 //   window coefficients (ring of RC windows) [N][RC] float4 (LIF) or
 //     2 x float4 (ALIF): neuron-major, so a catch-up over consecutive
@@ -30,7 +32,7 @@
 namespace eprop {
 
 constexpr int kMaxDelay = 8;
-constexpr int kSeg = 256;          // synapses per work item of the row kernels
+constexpr int kSeg = 128;          // synapses per segment of the row kernels
 constexpr int kSegPerLane = kSeg / 32;
 constexpr int kSpikeCap = 64;      // spikes of one row cached per warp
 constexpr int kMaxOut = 1024;
@@ -51,7 +53,8 @@ struct Net {
     // model switches
     int alif, t_ref, loss, feedback, has_state, trace_bf16, record_grad, record_raster, record_psi;
     int n_thr, T;             // T of the current call
-    int segs;                 // work items per row: ceil(max out-degree / kSeg)
+    int segs;                 // segments per row: ceil(max out-degree / kSeg)
+    int list_cap;             // entries per spike-list bucket
     // constants (float, computed on the host in double)
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
     float alpha_lo, rho_lo;   // alpha - (float)alpha, rho - (float)rho
@@ -105,6 +108,38 @@ struct Net {
 };
 
 // ----------------------------------------------------------------- helpers
+
+constexpr int kBkt = 32;           // spike-list buckets per step
+
+__device__ __forceinline__ long long list_index(const Net &n, int b, int slot) {
+    return (long long)(b * n.RS + slot) * kBkt;
+}
+
+// Warp-cooperative view of the kBkt buckets of one spike list: lane k holds
+// the inclusive prefix of the counts of buckets 0..k.
+struct BucketScan {
+    int incl, total;
+};
+__device__ __forceinline__ BucketScan bucket_scan(const int *cnt) {
+    const int lane = threadIdx.x & 31;
+    int v = cnt[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    BucketScan bs;
+    bs.incl = v;
+    bs.total = __shfl_sync(0xffffffffu, v, 31);
+    return bs;
+}
+// Entry r (warp-uniform, < total) of the list: its source id.
+__device__ __forceinline__ int bucket_entry(const Net &n, const int *ids, const BucketScan &bs, int r) {
+    const int bk = __popc(__ballot_sync(0xffffffffu, bs.incl <= r));
+    const int prev = __shfl_sync(0xffffffffu, bs.incl, bk > 0 ? bk - 1 : 0);
+    const int idx = r - (bk > 0 ? prev : 0);
+    return ids[(long long)bk * n.list_cap + idx];
+}
 
 // TwoSum (Knuth): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -222,6 +257,41 @@ __device__ __forceinline__ RowInfo row_info(const Net &n, const uint32_t *words,
         }
     }
     return ri;
+}
+
+// Coefficients of one window of one neuron: LIF (cz, ce, mez, -); ALIF
+// (cz, ca, ce, maz), (maa, mez, mea, -).
+struct Coef {
+    float4 c0, c1;
+};
+template <bool ALIF>
+__device__ __forceinline__ Coef load_coef(const Net &n, long long j, int k) {
+    Coef c;
+    const int slot = k % n.RC;
+    if (ALIF) {
+        const float4 *p = reinterpret_cast<const float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
+        c.c0 = __ldg(p);
+        c.c1 = __ldg(p + 1);
+    } else {
+        c.c0 = __ldg(reinterpret_cast<const float4 *>(n.coef) + (long long)j * n.RC + slot);
+        c.c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return c;
+}
+template <bool ALIF>
+__device__ __forceinline__ void apply_coef(const Net &n, const Coef &c, float &zbar, float &epsa,
+                                           float &ebar, float &G) {
+    if (ALIF) {
+        G += c.c0.x * zbar + c.c0.y * epsa + c.c0.z * ebar;
+        const float ea = c.c0.w * zbar + c.c1.x * epsa;
+        const float ee = c.c1.y * zbar + c.c1.z * epsa + n.kappaeU * ebar;
+        epsa = ea;
+        ebar = ee;
+    } else {
+        G += c.c0.x * zbar + c.c0.y * ebar;
+        ebar = c.c0.z * zbar + n.kappaeU * ebar;
+    }
+    zbar *= n.alphaU;
 }
 
 // Window transfer of one synapse state x = (zbar, eps_a, ebar) over window

@@ -23,9 +23,9 @@ __device__ __forceinline__ void mark_spike(const Net &n, int b, int src, int r) 
     const uint32_t m = 1u << (p & 31);
     const uint32_t old = atomicOr(wd, m);
     if (old & m) return;
-    const int slot = r % n.RS;
-    const int pos = atomicAdd(&n.list_cnt[(long long)b * n.RS + slot], 1);
-    n.list_ids[((long long)b * n.RS + slot) * n.n_src + pos] = src;
+    const long long li = list_index(n, b, r % n.RS) + ((src >> 8) & (kBkt - 1));
+    const int pos = atomicAdd(&n.list_cnt[li], 1);
+    n.list_ids[li * n.list_cap + pos] = src;
 }
 
 // K9: input spikes of call step i ------------------------------------------
@@ -123,24 +123,40 @@ __global__ void neuron_kernel(Net n, int i) {
 // K3a: readout input sum_j W_out[j][k] z_j^t in exact fixed point; one CTA per
 // (chunk of the step's spike list, sample); thread = readout k.
 __global__ void readout_accum_kernel(Net n, int i, int chunk) {
+    __shared__ int srcs[64];
+    __shared__ int total_s;
     const int b = blockIdx.y;
     if (i > n.lengths[b]) return;
     const int r = run_step(n, i);
-    const int slot = r % n.RS;
-    const int cnt = n.list_cnt[(long long)b * n.RS + slot];
-    const int *ids = n.list_ids + ((long long)b * n.RS + slot) * n.n_src;
-    for (int c0 = blockIdx.x * chunk; c0 < cnt; c0 += gridDim.x * chunk) {
-        const int c1 = min(c0 + chunk, cnt);
+    const long long li = list_index(n, b, r % n.RS);
+    const int *cnt = n.list_cnt + li;
+    const int *ids = n.list_ids + li * n.list_cap;
+    BucketScan bs;
+    if (threadIdx.x < 32) {
+        bs = bucket_scan(cnt);
+        if (threadIdx.x == 0) total_s = bs.total;
+    }
+    __syncthreads();
+    const int total = total_s;
+    for (int c0 = blockIdx.x * chunk; c0 < total; c0 += gridDim.x * chunk) {
+        const int c1 = min(c0 + chunk, total);
+        if (threadIdx.x < 32)
+            for (int c = c0; c < c1; ++c) {
+                const int src = bucket_entry(n, ids, bs, c);
+                if (threadIdx.x == 0) srcs[c - c0] = src;
+            }
+        __syncthreads();
         for (int k = threadIdx.x; k < n.n_out; k += blockDim.x) {
             long long acc = 0;
-            for (int c = c0; c < c1; ++c) {
-                const int src = ids[c];
+            for (int c = 0; c < c1 - c0; ++c) {
+                const int src = srcs[c];
                 if (src < n.n_in) continue;
                 acc += __float2ll_rn(n.w_out[(long long)(src - n.n_in) * n.n_out + k] * 4294967296.0f);
             }
             if (acc) atomicAdd(reinterpret_cast<unsigned long long *>(&n.y_acc[(long long)b * n.n_out + k]),
                                (unsigned long long)acc);
         }
+        __syncthreads();
     }
 }
 
@@ -182,7 +198,7 @@ __global__ void readout_error_kernel(Net n, int i) {
     float *E = n.E_win + ((long long)b * n.U + (r - a0 - 1)) * n.n_out;
     // the list slot of step r + 1 was last used RS steps ago; every reader of
     // it has finished (RS = U + D + 1 covers the window's trace launches)
-    if (threadIdx.x == 0) n.list_cnt[(long long)b * n.RS + (r + 1) % n.RS] = 0;
+    if (threadIdx.x < kBkt) n.list_cnt[list_index(n, b, (r + 1) % n.RS) + threadIdx.x] = 0;
     if (i > n.lengths[b]) {      // after the sample's end: no error, no output
         if (has_k) {
             E[k] = 0.0f;
@@ -224,7 +240,7 @@ __global__ void readout_error_kernel(Net n, int i) {
 // that closed since the synapse's last arrival is added on the fly
 // (read-only).  Arrivals are summed in exact int64 fixed point.
 template <bool ALIF, bool STATE>
-__global__ void __launch_bounds__(256) deliver_kernel(Net n, int i) {
+__global__ void __launch_bounds__(256, 3) deliver_kernel(Net n, int i) {
     __shared__ RowInfo info[8][kMaxDelay + 1];
     __shared__ unsigned long long ev_block;
     const int b = blockIdx.y;
@@ -235,16 +251,17 @@ __global__ void __launch_bounds__(256) deliver_kernel(Net n, int i) {
     unsigned long long ev_warp = 0ULL;
     const int r = run_step(n, i);
     const int a0 = win_start(n, r);
+    const int k1 = a0 / n.U;                 // windows < k1 are closed
     const long long t_abs = abs_step(n, i);
-    const int slot = r % n.RS;
-    const int cnt = n.list_cnt[(long long)b * n.RS + slot];
-    const int *ids = n.list_ids + ((long long)b * n.RS + slot) * n.n_src;
+    const long long li = list_index(n, b, r % n.RS);
+    const int *ids = n.list_ids + li * n.list_cap;
+    const BucketScan bs = bucket_scan(n.list_cnt + li);
     const int D1 = n.D + 1;
     long long *ring_b = n.ring + (long long)b * D1 * n.n_rec;
-    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long row = gw; row < cnt; row += nw) {
-        const int src = ids[row];
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int row = gw; row < bs.total; row += nw) {
+        const int src = bucket_entry(n, ids, bs, row);
         const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
         if (re <= rb) continue;
         if (lane == 0) ev_warp += (unsigned long long)(re - rb);
@@ -255,54 +272,65 @@ __global__ void __launch_bounds__(256) deliver_kernel(Net n, int i) {
             __syncwarp();
         }
         for (long long q0 = rb; q0 < re; q0 += kSeg) {
-        const long long q1 = min(re, q0 + kSeg);
-        uint32_t td[kSegPerLane];
-        float wv[kSegPerLane];
-#pragma unroll
-        for (int u = 0; u < kSegPerLane; ++u) {
-            const long long q = q0 + lane + 32 * u;
-            td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < kSegPerLane; ++u) {
-            const long long q = q0 + lane + 32 * u;
-            wv[u] = q < q1 ? __ldcs(n.w + q) : 0.f;
-        }
-        if (STATE) {
+            const long long q1 = min(re, q0 + kSeg);
+            uint32_t td[kSegPerLane];
+            float wv[kSegPerLane];
 #pragma unroll
             for (int u = 0; u < kSegPerLane; ++u) {
-                if (td[u] == 0u) continue;
-                const int d = (int)(td[u] >> 24);
-                const RowInfo ri = info[warp][d];
-                if (ri.b_prev != kNoSpike && ri.b_prev < a0) {
+                const long long q = q0 + lane + 32 * u;
+                td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
+                wv[u] = q < q1 ? __ldcs(n.w + q) : 0.f;
+            }
+            if (STATE) {
+                // lazily pending windows k0 .. k1-1: prefetch the trace and
+                // the first two windows' coefficients of every synapse
+                float eb[kSegPerLane], ea[kSegPerLane];
+                Coef cf0[kSegPerLane], cf1[kSegPerLane];
+                int k0s[kSegPerLane];
+#pragma unroll
+                for (int u = 0; u < kSegPerLane; ++u) {
+                    k0s[u] = -1;
+                    eb[u] = ea[u] = 0.f;
+                    if (td[u] == 0u) continue;
+                    const RowInfo ri = info[warp][td[u] >> 24];
+                    if (ri.b_prev == kNoSpike || ri.b_prev >= a0) continue;
                     const long long q = q0 + lane + 32 * u;
-                    const int j = (int)(td[u] & 0xFFFFFFu);
-                    float zbar = ri.zbar_bp;
-                    float ebar = load_trace(n.ebar, q, n.trace_bf16);
-                    float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.0f;
-                    float G = 0.0f;
+                    const long long j = td[u] & 0xFFFFFFu;
                     int k0 = ri.b_prev / n.U;
-                    const int k1 = a0 / n.U;           // windows k0 .. k1-1 closed, not applied
                     if (k1 - k0 > n.RC) {
                         atomicOr(n.err_flags, 1u);
                         k0 = k1 - n.RC;
                     }
-                    for (int k = k0; k < k1; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                    k0s[u] = k0;
+                    eb[u] = load_trace(n.ebar, q, n.trace_bf16);
+                    if (ALIF) ea[u] = load_trace(n.epsa, q, n.trace_bf16);
+                    cf0[u] = load_coef<ALIF>(n, j, k0);
+                    if (k0 + 1 < k1) cf1[u] = load_coef<ALIF>(n, j, k0 + 1);
+                }
+#pragma unroll
+                for (int u = 0; u < kSegPerLane; ++u) {
+                    if (k0s[u] < 0) continue;
+                    const int k0 = k0s[u];
+                    const long long j = td[u] & 0xFFFFFFu;
+                    float zbar = info[warp][td[u] >> 24].zbar_bp;
+                    float ebar = eb[u], epsa = ea[u], G = 0.f;
+                    apply_coef<ALIF>(n, cf0[u], zbar, epsa, ebar, G);
+                    if (k0 + 1 < k1) apply_coef<ALIF>(n, cf1[u], zbar, epsa, ebar, G);
+                    for (int k = k0 + 2; k < k1; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
                     wv[u] -= n.lr * G;
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < kSegPerLane; ++u) {
-            if (td[u] == 0u) continue;
-            const int j = (int)(td[u] & 0xFFFFFFu);
-            const int d = (int)(td[u] >> 24);
-            const long long fx = __float2ll_rn(wv[u] * 4294967296.0f);
-            atomicAdd(reinterpret_cast<unsigned long long *>(
-                          &ring_b[(long long)((t_abs + d) % D1) * n.n_rec + j]),
-                      (unsigned long long)fx);
+            for (int u = 0; u < kSegPerLane; ++u) {
+                if (td[u] == 0u) continue;
+                const int j = (int)(td[u] & 0xFFFFFFu);
+                const int d = (int)(td[u] >> 24);
+                const long long fx = __float2ll_rn(wv[u] * 4294967296.0f);
+                atomicAdd(reinterpret_cast<unsigned long long *>(
+                              &ring_b[(long long)((t_abs + d) % D1) * n.n_rec + j]),
+                          (unsigned long long)fx);
+            }
         }
-        }                            // segments of the row
         if (STATE) __syncwarp();
     }
     if (lane == 0 && ev_warp) atomicAdd(&ev_block, ev_warp);
@@ -325,12 +353,13 @@ void launch_neuron(const Net &n, int i, cudaStream_t st) {
 }
 
 void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
-    const int chunk = 32;
+    const int chunk = 64;
     int blocks = (n.n_src + chunk - 1) / chunk;
     const int cap = n.B > 1 ? 4 : 2 * sm_count;
     if (blocks > cap) blocks = cap;
     int th = ((n.n_out + 31) / 32) * 32;
     if (th > 256) th = 256;
+    if (th < 32) th = 32;
     readout_accum_kernel<<<dim3(blocks, n.B), th, 0, st>>>(n, i, chunk);
     int th2 = ((n.n_out + 31) / 32) * 32;
     readout_error_kernel<<<n.B, th2, 0, st>>>(n, i);

@@ -217,14 +217,16 @@ __global__ void window_offsets_kernel(Net n, int i_end) {
     const int a0 = r_end - n.U;
     const int s_lo = max(a0 + 1 - n.D, 1);
     const int nsteps = r_end - 1 - s_lo + 1;
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int k = 0; k < nsteps; ++k) {
-            n.win_off[k] = acc;
-            acc += (long long)n.list_cnt[(s_lo + k) % n.RS];
-        }
-        n.win_off[nsteps > 0 ? nsteps : 0] = acc;
+    const int lane = threadIdx.x & 31;
+    long long acc = 0;
+    for (int k = 0; k < nsteps; ++k) {
+        int v = n.list_cnt[list_index(n, 0, (s_lo + k) % n.RS) + lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) n.win_off[k] = acc;
+        acc += v;
     }
+    if (lane == 0) n.win_off[nsteps > 0 ? nsteps : 0] = acc;
 }
 
 __device__ __forceinline__ bool any_spike(const uint32_t *words, int RW, int lo, int hi) {
@@ -316,6 +318,7 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     const int kW = a0 / U;
     const float step = n.lr * n.inv_B;
+    const long long qa = (long long)(-a0 - 1) * N;     // table index = qa + a * N + j
     for (long long it = gw; it < total; it += nw) {
         int lo = 0, hi = nsteps;
         while (hi - lo > 1) {
@@ -323,8 +326,9 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
             if (off[mid] <= it) lo = mid; else hi = mid;
         }
         const int s = s_lo + lo;
-        const int row = (int)(it - off[lo]);
-        const int src = n.list_ids[(long long)(s % n.RS) * n.n_src + row];
+        const long long li = list_index(n, 0, s % n.RS);
+        const BucketScan bs = bucket_scan(n.list_cnt + li);
+        const int src = bucket_entry(n, n.list_ids + li * n.list_cap, bs, (int)(it - off[lo]));
         const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
         if (re <= rb) continue;
         const uint32_t *words = src_words_c(n, 0, src);
@@ -348,78 +352,111 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
             }
         }
         ns = __shfl_sync(0xffffffffu, ns, 0);
+        const bool listed = ns <= kSpikeCap;
         if (STATE && lane >= 1 && lane <= n.D)
             info[warp][lane] = row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false);
         __syncwarp();
         for (long long q0 = rb; q0 < re; q0 += kSeg) {
-        const long long q1 = min(re, q0 + kSeg);
-        uint32_t td[kSegPerLane];
+            const long long q1 = min(re, q0 + kSeg);
+            uint32_t td[kSegPerLane];
 #pragma unroll
-        for (int u = 0; u < kSegPerLane; ++u) {
-            const long long q = q0 + lane + 32 * u;
-            td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
-        }
-        float wv[kSegPerLane], eb[kSegPerLane], ep[kSegPerLane];
-        int c0[kSegPerLane];
-        const bool listed = ns <= kSpikeCap;
-#pragma unroll
-        for (int u = 0; u < kSegPerLane; ++u) {
-            const long long q = q0 + lane + 32 * u;
-            const int d = (int)(td[u] >> 24);
-            bool has = false;
-            int c = 0;
-            if (td[u] != 0u) {
-                if (listed) {       // first listed spike whose arrival lies after a0
-                    while (c < ns && spk[warp][c] + d <= a0) ++c;
-                    has = c < ns && spk[warp][c] + d <= r_end;
-                } else {
-                    has = any_spike(words, n.RW, max(s, a0 + 1 - d), r_end - d);
-                }
+            for (int u = 0; u < kSegPerLane; ++u) {
+                const long long q = q0 + lane + 32 * u;
+                td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
             }
-            c0[u] = has ? c : -1;
-            wv[u] = has ? __ldcs(n.w + q) : 0.f;
-            eb[u] = (STATE && has) ? load_trace(n.ebar, q, n.trace_bf16) : 0.f;
-            ep[u] = (STATE && ALIF && has) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
-        }
+            // phase 1: which synapses have arrivals; issue every load they need
+            float wv[kSegPerLane], eb[kSegPerLane], ep[kSegPerLane];
+            float4 t0[kSegPerLane];          // table entry of the first arrival
+            Coef cf0[kSegPerLane], cf1[kSegPerLane];
+            int c0[kSegPerLane], k0s[kSegPerLane];
 #pragma unroll
-        for (int u = 0; u < kSegPerLane; ++u) {
-            if (c0[u] < 0) continue;
-            const long long q = q0 + lane + 32 * u;
-            const int j = (int)(td[u] & 0xFFFFFFu);
-            const int d = (int)(td[u] >> 24);
-            float G = 0.f, ebar = eb[u], epsa = ep[u];
-            if (STATE) {            // the window's first arrival: restore the state
-                const RowInfo ri = info[warp][d];
-                if (ri.b_prev != kNoSpike) {
-                    G = catch_up<ALIF>(n, j, ri.b_prev / U, kW, ri.zbar_bp, epsa, ebar);
-                } else {
-                    ebar = 0.f;
-                    epsa = 0.f;
-                }
-            }
-            const long long qrow = (long long)(-a0 - 1) * N + j;   // + a * N
-            if (listed) {
-                for (int c = c0[u]; c < ns; ++c) {
-                    const int a = spk[warp][c] + d;
-                    if (a > r_end) break;
-                    if (ALIF) {
-                        const float4 t = reinterpret_cast<const float4 *>(n.qp)[qrow + (long long)a * N];
-                        G += t.x; ebar += t.y; epsa += t.z;
+            for (int u = 0; u < kSegPerLane; ++u) {
+                const long long q = q0 + lane + 32 * u;
+                const int d = (int)(td[u] >> 24);
+                const long long j = td[u] & 0xFFFFFFu;
+                bool has = false;
+                int c = 0;
+                if (td[u] != 0u) {
+                    if (listed) {       // first listed spike whose arrival lies after a0
+                        while (c < ns && spk[warp][c] + d <= a0) ++c;
+                        has = c < ns && spk[warp][c] + d <= r_end;
                     } else {
-                        const float2 t = reinterpret_cast<const float2 *>(n.qp)[qrow + (long long)a * N];
-                        G += t.x; ebar += t.y;
+                        has = any_spike(words, n.RW, max(s, a0 + 1 - d), r_end - d);
                     }
                 }
-            } else {                // rows with more spikes than the cache holds
-                G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - d), r_end - d, d, qrow, ebar, epsa);
+                c0[u] = has ? c : -1;
+                k0s[u] = -1;
+                wv[u] = has ? __ldcs(n.w + q) : 0.f;
+                eb[u] = (STATE && has) ? load_trace(n.ebar, q, n.trace_bf16) : 0.f;
+                ep[u] = (STATE && ALIF && has) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+                t0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (has && listed) {
+                    const long long qi = qa + (long long)(spk[warp][c] + d) * N + j;
+                    if (ALIF) t0[u] = __ldg(reinterpret_cast<const float4 *>(n.qp) + qi);
+                    else {
+                        const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qi);
+                        t0[u] = make_float4(t.x, t.y, 0.f, 0.f);
+                    }
+                }
+                if (STATE && has) {
+                    const RowInfo ri = info[warp][d];
+                    if (ri.b_prev != kNoSpike) {
+                        int k0 = ri.b_prev / U;
+                        if (kW - k0 > n.RC - 1) {
+                            atomicOr(n.err_flags, 1u);
+                            k0 = kW - (n.RC - 1);
+                        }
+                        k0s[u] = k0;
+                        cf0[u] = load_coef<ALIF>(n, j, k0);
+                        if (k0 + 1 <= kW) cf1[u] = load_coef<ALIF>(n, j, k0 + 1);
+                    }
+                }
             }
-            __stcs(n.w + q, wv[u] - step * G);
-            if (STATE) {
-                store_trace(n.ebar, q, ebar, n.trace_bf16);
-                if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
+            // phase 2: closed-form advance and weight update
+#pragma unroll
+            for (int u = 0; u < kSegPerLane; ++u) {
+                if (c0[u] < 0) continue;
+                const long long q = q0 + lane + 32 * u;
+                const long long j = td[u] & 0xFFFFFFu;
+                const int d = (int)(td[u] >> 24);
+                float G = 0.f, ebar = eb[u], epsa = ep[u];
+                if (STATE) {            // the window's first arrival: restore the state
+                    const int k0 = k0s[u];
+                    if (k0 >= 0) {
+                        float zbar = info[warp][d].zbar_bp;
+                        apply_coef<ALIF>(n, cf0[u], zbar, epsa, ebar, G);
+                        if (k0 + 1 <= kW) apply_coef<ALIF>(n, cf1[u], zbar, epsa, ebar, G);
+                        for (int k = k0 + 2; k <= kW; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                    } else {
+                        ebar = 0.f;
+                        epsa = 0.f;
+                    }
+                }
+                if (listed) {
+                    G += t0[u].x;
+                    ebar += t0[u].y;
+                    if (ALIF) epsa += t0[u].z;
+                    for (int c = c0[u] + 1; c < ns; ++c) {
+                        const int a = spk[warp][c] + d;
+                        if (a > r_end) break;
+                        if (ALIF) {
+                            const float4 t = __ldg(reinterpret_cast<const float4 *>(n.qp) + qa + (long long)a * N + j);
+                            G += t.x; ebar += t.y; epsa += t.z;
+                        } else {
+                            const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qa + (long long)a * N + j);
+                            G += t.x; ebar += t.y;
+                        }
+                    }
+                } else {            // rows with more spikes than the cache holds
+                    G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - d), r_end - d, d, qa + j, ebar, epsa);
+                }
+                __stcs(n.w + q, wv[u] - step * G);
+                if (STATE) {
+                    store_trace(n.ebar, q, ebar, n.trace_bf16);
+                    if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
+                }
+                if (n.record_grad) n.grad[q] += n.inv_B * G;
             }
-            if (n.record_grad) n.grad[q] += n.inv_B * G;
-        }
         }                            // segments of the row
         __syncwarp();
     }
