@@ -277,9 +277,9 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             n.segs = (int)std::max(1LL, (mx + eprop::kSeg - 1) / eprop::kSeg);
         }
         uint32_t *td;
-        FA(tgt_d, uint32_t, nnz);
+        FA(tgt_d, uint32_t, nnz + 16);
         td = const_cast<uint32_t *>(n.tgt_d);
-        FA(w, float, nnz);
+        FA(w, float, nnz + 16);
         if (nnz > 0) {
             const int32_t *tg = syn->target;
             const uint8_t *dl = syn->delay;
@@ -312,8 +312,8 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             if (hflag & 2u) { s = fail(nullptr, EPROP_EINVAL, "synapse delay out of [1, max_delay]"); goto fail_out; }
         }
         if (n.has_state) {
-            FA(ebar, uint16_t, nnz * (n.trace_bf16 ? 1 : 2));
-            if (n.alif) FA(epsa, uint16_t, nnz * (n.trace_bf16 ? 1 : 2));
+            FA(ebar, uint16_t, (nnz + 16) * (n.trace_bf16 ? 1 : 2));
+            if (n.alif) FA(epsa, uint16_t, (nnz + 16) * (n.trace_bf16 ? 1 : 2));
         }
         if (n.record_grad) FA(grad, float, nnz);
         // neurons
@@ -361,6 +361,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             cudaMemcpy(thr, c.drive_thr, sizeof(c.drive_thr), cudaMemcpyHostToDevice);
         }
         eprop::prepare_kernel_attributes();
+        eprop::prepare_step_kernel_attributes();
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "network set-up"); goto fail_out; }
         if (c.update_interval > 0) {
@@ -717,6 +718,11 @@ extern "C" eprop_status eprop_sync(eprop_net *net) {
     CK(net, cudaGetLastError());
     unsigned int f = 0;
     CK(net, cudaMemcpy(&f, net->n.err_flags, 4, cudaMemcpyDeviceToHost));
+    if (f & 2u) {
+        net->bad = 1;
+        net->err = "a bounded wait for a bulk copy into shared memory gave up";
+        return EPROP_ETIMEOUT;
+    }
     if (f & 1u) net->err = "warning: a synapse skipped more update windows than the coefficient ring holds";
     return EPROP_OK;
 }

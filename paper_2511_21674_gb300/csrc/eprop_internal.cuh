@@ -55,6 +55,7 @@ struct Net {
     int n_thr, T;             // T of the current call
     int segs;                 // segments per row: ceil(max out-degree / kSeg)
     int list_cap;             // entries per spike-list bucket
+    int tables_psi_smem;      // tables kernel stages psi in shared memory
     // constants (float, computed on the host in double)
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
     float alpha_lo, rho_lo;   // alpha - (float)alpha, rho - (float)rho
@@ -108,6 +109,68 @@ struct Net {
 };
 
 // ----------------------------------------------------------------- helpers
+
+// ---- bulk asynchronous copies (TMA, 1-D) into shared memory, completed on
+// an mbarrier.  Every wait is bounded: after kWaitLimit polls the kernel
+// records an error flag (bit 1) and stops waiting.
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// dst, src and bytes multiples of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false (and error bit 1) when the limit is reached
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err) {
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(err, 2u);
+    return false;
+}
+
+// One pipeline stage of a row kernel: kChunk synapse records of one row.
+// Each stream is copied from the 16-byte-aligned start at or before the
+// chunk (q_al for 4-byte streams, q_al2 for 2-byte streams).
+constexpr int kChunk = 256;
+constexpr int kChunkPad = kChunk + 8;
+struct alignas(16) StageBuf {
+    uint32_t td[kChunkPad];
+    float w[kChunkPad];
+    uint32_t tr[kChunkPad];       // trace stream: kChunkPad floats or 2*kChunkPad bf16
+};
+struct StageDesc {
+    long long q0, q_al, q_al2;
+    int n, src, first, row;
+};
 
 constexpr int kBkt = 32;           // spike-list buckets per step
 

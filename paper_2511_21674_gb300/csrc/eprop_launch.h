@@ -12,6 +12,7 @@ void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st);
 void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st);
 
 void prepare_kernel_attributes();
+void prepare_step_kernel_attributes();
 void launch_begin_call(const Net &n, int continuous, cudaStream_t st);
 void launch_end_call(const Net &n, int T, cudaStream_t st);
 void launch_filter_error(const Net &n, int i_end, cudaStream_t st);

@@ -47,21 +47,33 @@ __global__ void neuron_kernel(Net n, int i) {
     const int b = blockIdx.y;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n.n_rec) return;
-    const int r = run_step(n, i);
-    const int a0 = win_start(n, r);
     const long long nb = (long long)b * n.n_rec + j;
+    // every load that does not depend on the clock is issued together with
+    // the clock and sample-length loads (one memory round trip)
+    const Clock ck = *n.clock;
+    const int len = n.lengths[b];
+    const uint8_t zp8 = n.z_prev[nb];
+    float v_hi = n.v[nb], v_lo = n.v_lo[nb];
+    float a_hi = 0.f, a_lo = 0.f;
+    if (n.alif) {
+        a_hi = n.a[nb];
+        a_lo = n.a_lo[nb];
+    }
+    int ref = n.ref[nb];
+    const int r = ck.r_base + i;
+    const int a0 = ((r - 1) / n.U) * n.U;
     float *psi_slot = n.psi_hist + ((long long)b * (n.U + 1) + (r - a0)) * n.n_rec + j;
-    if (i > n.lengths[b]) {      // sample already finished: frozen, silent
+    if (i > len) {               // sample already finished: frozen, silent
         *psi_slot = 0.0f;
         if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
         return;
     }
-    const long long t_abs = abs_step(n, i);
+    const long long t_abs = ck.t_abs_base + i;
     const int slot = (int)(t_abs % (n.D + 1));
     long long *ring = n.ring + ((long long)b * (n.D + 1) + slot) * n.n_rec + j;
-    // exact fixed-point input split into an FP32 pair
     const long long acc = *ring;
     *ring = 0;
+    // exact fixed-point input split into an FP32 pair
     const float acc_hi = (float)acc;
     float u_hi = acc_hi * kFixInv;
     float u_lo = (float)(acc - (long long)acc_hi) * kFixInv;
@@ -69,17 +81,16 @@ __global__ void neuron_kernel(Net n, int i) {
         const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
         const uint32_t u = (uint32_t)(h >> 32);
         int cnt = 0;
-        for (int m = 0; m < n.n_thr; ++m) cnt += (u >= n.drive_thr[m]);
+        for (int m = 0; m < n.n_thr; ++m) cnt += (u >= __ldg(n.drive_thr + m));
         const float dv = n.drive_weight * (float)cnt;
         const float de = fmaf(n.drive_weight, (float)cnt, -dv);
         float e;
         two_sum(u_hi, dv, u_hi, e);
         u_lo += e + de;
     }
-    const float zp = (float)n.z_prev[nb];
+    const float zp = (float)zp8;
     float vth = n.v_th, vth_lo = 0.0f;
     if (n.alif) {
-        float a_hi = n.a[nb], a_lo = n.a_lo[nb];
         comp_step(n.rho, n.rho_lo, zp, 0.0f, a_hi, a_lo);
         n.a[nb] = a_hi;
         n.a_lo[nb] = a_lo;
@@ -92,12 +103,10 @@ __global__ void neuron_kernel(Net n, int i) {
         two_sum(u_hi, -zp * vth, u_hi, e);
         u_lo += e - zp * vth_lo;
     }
-    float v_hi = n.v[nb], v_lo = n.v_lo[nb];
     comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi, v_lo);
     n.v[nb] = v_hi;
     n.v_lo[nb] = v_lo;
     const float m = (v_hi - vth) + (v_lo - vth_lo);
-    int ref = n.ref[nb];
     const bool refractory = ref > 0;
     int z;
     if (n.forced) z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
@@ -232,21 +241,68 @@ __global__ void readout_error_kernel(Net n, int i) {
     if (threadIdx.x == 0) n.loss_acc[b] += tot;
 }
 
-// K2: transmission of the spikes of call step i.  Work items are (spiking
-// source row, segment of kSeg synapses); a warp handles one item with
-// kSegPerLane synapses per lane, loads hoisted for memory-level parallelism
-// (coalesced 4-byte streams).  The weight carried is the weight in effect at
-// emission: with per-synapse lazy updates, the gradient of update windows
-// that closed since the synapse's last arrival is added on the fly
-// (read-only).  Arrivals are summed in exact int64 fixed point.
+// Issues the bulk copies of one chunk (cnt records from q0) into a stage
+// (one thread).  4-byte streams start at q_al = q0 rounded down to 4
+// elements, the 2-byte trace stream at q0 rounded down to 8 elements, so
+// every copy starts and ends on 16-byte boundaries (the record arrays are
+// padded past nnz).
+__device__ __forceinline__ void issue_chunk(const Net &n, StageBuf &sb, uint64_t *bar, long long q0, int cnt,
+                                            bool with_trace, StageDesc &dsc) {
+    const long long q_al = q0 & ~3LL;
+    const uint32_t n4 = (uint32_t)((q0 + cnt - q_al + 3) & ~3LL);
+    long long q_al2 = q_al;
+    uint32_t tr_bytes = 0;
+    if (with_trace) {
+        if (n.trace_bf16) {
+            q_al2 = q0 & ~7LL;
+            tr_bytes = (uint32_t)((q0 + cnt - q_al2 + 7) & ~7LL) * 2u;
+        } else {
+            tr_bytes = n4 * 4u;
+        }
+    }
+    mbar_expect_tx(bar, n4 * 8u + tr_bytes);
+    bulk_g2s(sb.td, n.tgt_d + q_al, n4 * 4u, bar);
+    bulk_g2s(sb.w, n.w + q_al, n4 * 4u, bar);
+    if (with_trace) {
+        if (n.trace_bf16) bulk_g2s(sb.tr, reinterpret_cast<const uint16_t *>(n.ebar) + q_al2, tr_bytes, bar);
+        else bulk_g2s(sb.tr, reinterpret_cast<const float *>(n.ebar) + q_al, tr_bytes, bar);
+    }
+    dsc.q0 = q0;
+    dsc.q_al = q_al;
+    dsc.q_al2 = q_al2;
+    dsc.n = cnt;
+}
+
+__device__ __forceinline__ float stage_trace(const Net &n, const StageBuf &sb, const StageDesc &d, long long q) {
+    if (n.trace_bf16)
+        return __bfloat162float(__ushort_as_bfloat16(reinterpret_cast<const uint16_t *>(sb.tr)[q - d.q_al2]));
+    return reinterpret_cast<const float *>(sb.tr)[q - d.q_al];
+}
+
+constexpr int kDStages = 3;
+
+// K2: transmission of the spikes of call step i.  Each warp walks its share
+// of the step's spiking rows as a sequence of chunks of kChunk synapse
+// records; a kDStages-deep pipeline of bulk copies (TMA, 1-D) streams the
+// records into shared memory while earlier chunks are delivered.  The
+// weight carried is the weight in effect at emission: with per-synapse lazy
+// updates, the gradient of update windows that closed since the synapse's
+// last arrival is added on the fly (read-only).  Arrivals are summed in
+// exact int64 fixed point.
 template <bool ALIF, bool STATE>
-__global__ void __launch_bounds__(256, 3) deliver_kernel(Net n, int i) {
-    __shared__ RowInfo info[8][kMaxDelay + 1];
+__global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ uint64_t bars[8][kDStages];
+    __shared__ StageDesc desc[8][kDStages];
+    __shared__ RowInfo info[8][kDStages][kMaxDelay + 1];
     __shared__ unsigned long long ev_block;
     const int b = blockIdx.y;
     if (i > n.lengths[b]) return;            // whole block: same sample
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kDStages;
     if (threadIdx.x == 0) ev_block = 0ULL;
+    if (lane < kDStages) mbar_init(&bars[warp][lane], 1);
+    fence_mbar_init();
     __syncthreads();
     unsigned long long ev_warp = 0ULL;
     const int r = run_step(n, i);
@@ -260,41 +316,74 @@ __global__ void __launch_bounds__(256, 3) deliver_kernel(Net n, int i) {
     long long *ring_b = n.ring + (long long)b * D1 * n.n_rec;
     const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
     const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int row = gw; row < bs.total; row += nw) {
-        const int src = bucket_entry(n, ids, bs, row);
-        const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
-        if (re <= rb) continue;
-        if (lane == 0) ev_warp += (unsigned long long)(re - rb);
-        if (STATE) {
-            if (lane >= 1 && lane <= n.D)
-                info[warp][lane] = row_info(n, src_words(n, b, src), n.anchor_t[(long long)b * n.n_src + src],
-                                            n.anchor_z[(long long)b * n.n_src + src], a0, lane, false);
-            __syncwarp();
+    // producer cursor (warp-uniform)
+    int prow = gw;
+    long long pq = 0, pre = 0;
+    int psrc = -1, pfirst = 0;
+    RowInfo rinfo;
+    unsigned vmask = 0;
+    for (int k = 0; k < kDStages; ++k) {
+        bool ok = true;
+        while (pq >= pre) {
+            if (prow >= bs.total) { ok = false; break; }
+            psrc = bucket_entry(n, ids, bs, prow);
+            pq = n.row_ptr[psrc];
+            pre = n.row_ptr[psrc + 1];
+            prow += nw;
+            pfirst = 1;
+            if (STATE && pre > pq && lane >= 1 && lane <= n.D)
+                rinfo = row_info(n, src_words(n, b, psrc), n.anchor_t[(long long)b * n.n_src + psrc],
+                                 n.anchor_z[(long long)b * n.n_src + psrc], a0, lane, false);
         }
-        for (long long q0 = rb; q0 < re; q0 += kSeg) {
-            const long long q1 = min(re, q0 + kSeg);
-            uint32_t td[kSegPerLane];
-            float wv[kSegPerLane];
+        if (!ok) break;
+        const int cnt = (int)min((long long)kChunk, pre - pq);
+        if (STATE && lane >= 1 && lane <= n.D) info[warp][k][lane] = rinfo;
+        if (lane == 0) {
+            issue_chunk(n, buf[k], &bars[warp][k], pq, cnt, STATE, desc[warp][k]);
+            desc[warp][k].first = pfirst;
+            desc[warp][k].row = (int)(pre - pq);
+        }
+        pq += cnt;
+        pfirst = 0;
+        vmask |= 1u << k;
+    }
+    __syncwarp();
+    int abort_c = -1;
+    for (int c = 0;; ++c) {
+        const int k = c % kDStages;
+        if (!((vmask >> k) & 1u)) break;
+        if (!mbar_wait(&bars[warp][k], (uint32_t)((c / kDStages) & 1), n.err_flags)) {
+            abort_c = c;
+            break;
+        }
+        const StageDesc d = desc[warp][k];
+        if (d.first && lane == 0) ev_warp += (unsigned long long)d.row;
+        const StageBuf &sb = buf[k];
+#pragma unroll 2
+        for (int h = 0; h < kChunk / 32; h += 4) {
+            uint32_t td[4];
+            float wv[4];
 #pragma unroll
-            for (int u = 0; u < kSegPerLane; ++u) {
-                const long long q = q0 + lane + 32 * u;
-                td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
-                wv[u] = q < q1 ? __ldcs(n.w + q) : 0.f;
+            for (int u = 0; u < 4; ++u) {
+                const int idx = lane + 32 * (h + u);
+                const long long q = d.q0 + idx;
+                td[u] = idx < d.n ? sb.td[q - d.q_al] : 0u;
+                wv[u] = idx < d.n ? sb.w[q - d.q_al] : 0.f;
             }
             if (STATE) {
-                // lazily pending windows k0 .. k1-1: prefetch the trace and
-                // the first two windows' coefficients of every synapse
-                float eb[kSegPerLane], ea[kSegPerLane];
-                Coef cf0[kSegPerLane], cf1[kSegPerLane];
-                int k0s[kSegPerLane];
+                // lazily pending windows k0 .. k1-1: prefetch the first two
+                // windows' coefficients, then advance
+                float eb[4];
+                Coef cf0[4], cf1[4];
+                int k0s[4];
 #pragma unroll
-                for (int u = 0; u < kSegPerLane; ++u) {
+                for (int u = 0; u < 4; ++u) {
                     k0s[u] = -1;
-                    eb[u] = ea[u] = 0.f;
+                    eb[u] = 0.f;
                     if (td[u] == 0u) continue;
-                    const RowInfo ri = info[warp][td[u] >> 24];
+                    const RowInfo ri = info[warp][k][td[u] >> 24];
                     if (ri.b_prev == kNoSpike || ri.b_prev >= a0) continue;
-                    const long long q = q0 + lane + 32 * u;
+                    const long long q = d.q0 + lane + 32 * (h + u);
                     const long long j = td[u] & 0xFFFFFFu;
                     int k0 = ri.b_prev / n.U;
                     if (k1 - k0 > n.RC) {
@@ -302,36 +391,71 @@ __global__ void __launch_bounds__(256, 3) deliver_kernel(Net n, int i) {
                         k0 = k1 - n.RC;
                     }
                     k0s[u] = k0;
-                    eb[u] = load_trace(n.ebar, q, n.trace_bf16);
-                    if (ALIF) ea[u] = load_trace(n.epsa, q, n.trace_bf16);
+                    eb[u] = stage_trace(n, sb, d, q);
                     cf0[u] = load_coef<ALIF>(n, j, k0);
                     if (k0 + 1 < k1) cf1[u] = load_coef<ALIF>(n, j, k0 + 1);
                 }
 #pragma unroll
-                for (int u = 0; u < kSegPerLane; ++u) {
+                for (int u = 0; u < 4; ++u) {
                     if (k0s[u] < 0) continue;
                     const int k0 = k0s[u];
+                    const long long q = d.q0 + lane + 32 * (h + u);
                     const long long j = td[u] & 0xFFFFFFu;
-                    float zbar = info[warp][td[u] >> 24].zbar_bp;
-                    float ebar = eb[u], epsa = ea[u], G = 0.f;
+                    float zbar = info[warp][k][td[u] >> 24].zbar_bp;
+                    float ebar = eb[u], G = 0.f;
+                    float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
                     apply_coef<ALIF>(n, cf0[u], zbar, epsa, ebar, G);
                     if (k0 + 1 < k1) apply_coef<ALIF>(n, cf1[u], zbar, epsa, ebar, G);
-                    for (int k = k0 + 2; k < k1; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                    for (int kk = k0 + 2; kk < k1; ++kk) apply_window<ALIF>(n, j, kk, zbar, epsa, ebar, G);
                     wv[u] -= n.lr * G;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kSegPerLane; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 if (td[u] == 0u) continue;
                 const int j = (int)(td[u] & 0xFFFFFFu);
-                const int d = (int)(td[u] >> 24);
+                const int dl = (int)(td[u] >> 24);
                 const long long fx = __float2ll_rn(wv[u] * 4294967296.0f);
                 atomicAdd(reinterpret_cast<unsigned long long *>(
-                              &ring_b[(long long)((t_abs + d) % D1) * n.n_rec + j]),
+                              &ring_b[(long long)((t_abs + dl) % D1) * n.n_rec + j]),
                           (unsigned long long)fx);
             }
         }
-        if (STATE) __syncwarp();
+        __syncwarp();
+        // refill stage k with the next chunk
+        vmask &= ~(1u << k);
+        bool ok = true;
+        while (pq >= pre) {
+            if (prow >= bs.total) { ok = false; break; }
+            psrc = bucket_entry(n, ids, bs, prow);
+            pq = n.row_ptr[psrc];
+            pre = n.row_ptr[psrc + 1];
+            prow += nw;
+            pfirst = 1;
+            if (STATE && pre > pq && lane >= 1 && lane <= n.D)
+                rinfo = row_info(n, src_words(n, b, psrc), n.anchor_t[(long long)b * n.n_src + psrc],
+                                 n.anchor_z[(long long)b * n.n_src + psrc], a0, lane, false);
+        }
+        if (ok) {
+            const int cnt = (int)min((long long)kChunk, pre - pq);
+            if (STATE && lane >= 1 && lane <= n.D) info[warp][k][lane] = rinfo;
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async();
+                issue_chunk(n, buf[k], &bars[warp][k], pq, cnt, STATE, desc[warp][k]);
+                desc[warp][k].first = pfirst;
+                desc[warp][k].row = (int)(pre - pq);
+            }
+            pq += cnt;
+            pfirst = 0;
+            vmask |= 1u << k;
+        }
+        __syncwarp();
+    }
+    if (abort_c >= 0) {                      // let copies in flight land first
+        for (int c = abort_c + 1; c < abort_c + kDStages; ++c)
+            if ((vmask >> (c % kDStages)) & 1u)
+                mbar_wait(&bars[warp][c % kDStages], (uint32_t)((c / kDStages) & 1), n.err_flags);
     }
     if (lane == 0 && ev_warp) atomicAdd(&ev_block, ev_warp);
     __syncthreads();
@@ -367,12 +491,20 @@ void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
 
 void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st) {
     const dim3 grid(grid_x, n.B);
+    const size_t sm = sizeof(StageBuf) * 8 * kDStages;
     if (n.has_state) {
-        if (n.alif) deliver_kernel<true, true><<<grid, 256, 0, st>>>(n, i);
-        else deliver_kernel<false, true><<<grid, 256, 0, st>>>(n, i);
+        if (n.alif) deliver_kernel<true, true><<<grid, 256, sm, st>>>(n, i);
+        else deliver_kernel<false, true><<<grid, 256, sm, st>>>(n, i);
     } else {
-        deliver_kernel<false, false><<<grid, 256, 0, st>>>(n, i);
+        deliver_kernel<false, false><<<grid, 256, sm, st>>>(n, i);
     }
+}
+
+void prepare_step_kernel_attributes() {
+    const int sm = (int)(sizeof(StageBuf) * 8 * kDStages);
+    cudaFuncSetAttribute(deliver_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(deliver_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(deliver_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 }  // namespace eprop

@@ -99,12 +99,21 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
     const float *Eg = n.E_win + (long long)b * U * K;
     float *Es = smem;
     float *Ls = smem + (e_in_smem ? U * K : 0);
-    if (e_in_smem) {
+    float *Ps = Ls + (l_in_smem ? U * blockDim.x : 0);     // psi [U+1][bd] (when it fits)
+    const bool psi_in_smem = n.tables_psi_smem;
+    if (e_in_smem)
         for (int q = threadIdx.x; q < U * K; q += blockDim.x) Es[q] = Eg[q];
-        __syncthreads();
+    const int j0 = blockIdx.x * blockDim.x;
+    if (psi_in_smem) {          // coalesced rows of the block's neurons, all loads in flight
+        const float *pg = n.psi_hist + (long long)b * (U + 1) * N;
+        for (int q = threadIdx.x; q < (U + 1) * (int)blockDim.x; q += blockDim.x) {
+            const int u = q / blockDim.x, c = q % blockDim.x;
+            Ps[q] = (j0 + c < N) ? pg[(long long)u * N + j0 + c] : 0.f;
+        }
     }
+    __syncthreads();
     const float *E = e_in_smem ? Es : Eg;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = j0 + threadIdx.x;
     if (j >= N) return;
     const float *Bj = n.fb + (long long)j * K;
     const int bd = blockDim.x, tid = threadIdx.x;
@@ -135,7 +144,10 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
         for (int k = 0; k < K; ++k) acc += Bj[k] * e[k];
         return acc;
     };
-    const float *psi = n.psi_hist + (long long)b * (U + 1) * N + j;
+    const float *psi_g = n.psi_hist + (long long)b * (U + 1) * N + j;
+    auto PSI = [&](int u) -> float {
+        return psi_in_smem ? Ps[u * bd + tid] : psi_g[(long long)u * N];
+    };
     // The adjoint sweep is the per-window reduction of the gradient.  For
     // ALIF the eligibility psi (zbar - beta eps_a) is a near-cancellation of
     // two long-memory traces, so the sweep runs in FP64 there (FP32 loses up
@@ -146,8 +158,8 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
     const R rho = ALIF ? (R)n.rho + (R)n.rho_lo : (R)0;
     const R beta = n.beta_a;
     const R ke = n.kappa_e;
-    R pn = psi[(long long)U * N];          // psi^b
-    const float psi_b = psi[(long long)U * N];
+    R pn = PSI(U);          // psi^b
+    const float psi_b = PSI(U);
     // adjoint of G (mz, ma, me); of ebar^b (ez, ea, ee); of eps_a^b (az, aa, ae)
     R mz = 0, ma = 0, me = Lat(U);
     R ez = 0, ea = 0, ee = 1;
@@ -161,7 +173,7 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
             make_float2((float)(mz + pn * me), (float)(ez + pn * ee));
     }
     for (int u = U - 1; u >= 0; --u) {
-        const R p = psi[(long long)u * N];       // psi^{a0+u}
+        const R p = PSI(u);       // psi^{a0+u}
         // x -> (A^{u+1})^T x
         if (ALIF) {
             const R g1 = alpha - beta * p, g2 = rho - beta * p;
@@ -298,11 +310,58 @@ __device__ __noinline__ float scan_arrivals(const Net n, const uint32_t *words, 
 // skipped windows' coefficients); every arrival a adds Q(a) to the window's
 // gradient and Pe(a), Pa(a) to the state.  Record streams are read once
 // (tgt_d evict-first); the table slabs of the steps in flight stay in L2.
+
+// Bulk copies of one chunk of synapse records into a stage (one thread);
+// see the delivery kernel for the alignment rule.
+__device__ __forceinline__ void issue_chunk_w(const Net &n, StageBuf &sb, uint64_t *bar, long long q0, int cnt,
+                                              bool with_trace, StageDesc &dsc) {
+    const long long q_al = q0 & ~3LL;
+    const uint32_t n4 = (uint32_t)((q0 + cnt - q_al + 3) & ~3LL);
+    long long q_al2 = q_al;
+    uint32_t tr_bytes = 0;
+    if (with_trace) {
+        if (n.trace_bf16) {
+            q_al2 = q0 & ~7LL;
+            tr_bytes = (uint32_t)((q0 + cnt - q_al2 + 7) & ~7LL) * 2u;
+        } else {
+            tr_bytes = n4 * 4u;
+        }
+    }
+    mbar_expect_tx(bar, n4 * 8u + tr_bytes);
+    bulk_g2s(sb.td, n.tgt_d + q_al, n4 * 4u, bar);
+    bulk_g2s(sb.w, n.w + q_al, n4 * 4u, bar);
+    if (with_trace) {
+        if (n.trace_bf16) bulk_g2s(sb.tr, reinterpret_cast<const uint16_t *>(n.ebar) + q_al2, tr_bytes, bar);
+        else bulk_g2s(sb.tr, reinterpret_cast<const float *>(n.ebar) + q_al, tr_bytes, bar);
+    }
+    dsc.q0 = q0;
+    dsc.q_al = q_al;
+    dsc.q_al2 = q_al2;
+    dsc.n = cnt;
+}
+
+__device__ __forceinline__ float stage_trace_w(const Net &n, const StageBuf &sb, const StageDesc &d, long long q) {
+    if (n.trace_bf16)
+        return __bfloat162float(__ushort_as_bfloat16(reinterpret_cast<const uint16_t *>(sb.tr)[q - d.q_al2]));
+    return reinterpret_cast<const float *>(sb.tr)[q - d.q_al];
+}
+
+constexpr int kTStages = 3;
+
+// shared-memory layout of the trace kernel (dynamic): per warp kTStages
+// stage buffers, then the window's work-item offsets
 template <bool ALIF, bool STATE>
-__global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) {
-    extern __shared__ long long off[];
-    __shared__ RowInfo info[8][kMaxDelay + 1];
-    __shared__ int spk[8][kSpikeCap];
+__global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ uint64_t bars[8][kTStages];
+    __shared__ StageDesc desc[8][kTStages];
+    __shared__ RowInfo info[8][kTStages][kMaxDelay + 1];
+    __shared__ int spk[8][kTStages][kSpikeCap];
+    __shared__ int nspk[8][kTStages];
+    __shared__ int rspk[8][kSpikeCap];          // the producer's current row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kTStages;
+    long long *off = reinterpret_cast<long long *>(dsm + sizeof(StageBuf) * 8 * kTStages);
     const int U = n.U, N = n.n_rec;
     const int r_end = run_step_w(n, i_end);
     const int a0 = r_end - U;
@@ -311,87 +370,135 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
     const int nsteps = s_hi - s_lo + 1;
     if (nsteps <= 0) return;
     for (int k = threadIdx.x; k <= nsteps; k += blockDim.x) off[k] = n.win_off[k];
+    if (lane < kTStages) mbar_init(&bars[warp][lane], 1);
+    fence_mbar_init();
     __syncthreads();
     const long long total = off[nsteps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     const int kW = a0 / U;
     const float step = n.lr * n.inv_B;
     const long long qa = (long long)(-a0 - 1) * N;     // table index = qa + a * N + j
-    for (long long it = gw; it < total; it += nw) {
-        int lo = 0, hi = nsteps;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (off[mid] <= it) lo = mid; else hi = mid;
-        }
-        const int s = s_lo + lo;
-        const long long li = list_index(n, 0, s % n.RS);
-        const BucketScan bs = bucket_scan(n.list_cnt + li);
-        const int src = bucket_entry(n, n.list_ids + li * n.list_cap, bs, (int)(it - off[lo]));
-        const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
-        if (re <= rb) continue;
-        const uint32_t *words = src_words_c(n, 0, src);
-        if (any_spike(words, n.RW, s_lo, s - 1)) continue;   // another item owns the row
-        int ns = 0;
-        if (lane == 0) {             // the row's spikes in [s, s_hi], ascending
-            const int mask = n.RW * 32 - 1;
-            int r = s;
-            while (r <= s_hi) {
-                const int p = r & mask;
-                const int bit = p & 31;
-                const int span = min(31 - bit, s_hi - r);
-                uint32_t m = words[p >> 5] >> bit;
-                if (span < 31) m &= (2u << span) - 1u;
-                while (m) {
-                    if (ns < kSpikeCap) spk[warp][ns] = r + __ffs(m) - 1;
-                    ++ns;
-                    m &= m - 1;
+    // producer cursor (warp-uniform): work item, current row and its range
+    long long pit = gw;
+    long long pq = 0, pre = 0;
+    int psrc = -1, ps = 0, pns = 0;
+    RowInfo rinfo;
+    unsigned vmask = 0;
+    // advances the producer to the next chunk; false when the window is done
+    auto next_row = [&]() -> bool {
+        while (pq >= pre) {
+            if (pit >= total) return false;
+            int lo = 0, hi = nsteps;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (off[mid] <= pit) lo = mid; else hi = mid;
+            }
+            const int s = s_lo + lo;
+            const long long li = list_index(n, 0, s % n.RS);
+            const BucketScan bs = bucket_scan(n.list_cnt + li);
+            const int src = bucket_entry(n, n.list_ids + li * n.list_cap, bs, (int)(pit - off[lo]));
+            pit += nw;
+            const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
+            if (re <= rb) continue;
+            const uint32_t *words = src_words_c(n, 0, src);
+            if (any_spike(words, n.RW, s_lo, s - 1)) continue;   // another item owns the row
+            int ns = 0;
+            if (lane == 0) {             // the row's spikes in [s, s_hi], ascending
+                const int mask = n.RW * 32 - 1;
+                int r = s;
+                while (r <= s_hi) {
+                    const int p = r & mask;
+                    const int bit = p & 31;
+                    const int span = min(31 - bit, s_hi - r);
+                    uint32_t m = words[p >> 5] >> bit;
+                    if (span < 31) m &= (2u << span) - 1u;
+                    while (m) {
+                        if (ns < kSpikeCap) rspk[warp][ns] = r + __ffs(m) - 1;
+                        ++ns;
+                        m &= m - 1;
+                    }
+                    r += span + 1;
                 }
-                r += span + 1;
             }
+            pns = __shfl_sync(0xffffffffu, ns, 0);
+            if (STATE && lane >= 1 && lane <= n.D)
+                rinfo = row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false);
+            psrc = src;
+            ps = s;
+            pq = rb;
+            pre = re;
         }
-        ns = __shfl_sync(0xffffffffu, ns, 0);
-        const bool listed = ns <= kSpikeCap;
-        if (STATE && lane >= 1 && lane <= n.D)
-            info[warp][lane] = row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false);
+        return true;
+    };
+    auto produce = [&](int k) {
+        const int cnt = (int)min((long long)kChunk, pre - pq);
+        if (STATE && lane >= 1 && lane <= n.D) info[warp][k][lane] = rinfo;
+        for (int c = lane; c < min(pns, kSpikeCap); c += 32) spk[warp][k][c] = rspk[warp][c];
+        if (lane == 0) nspk[warp][k] = pns;
         __syncwarp();
-        for (long long q0 = rb; q0 < re; q0 += kSeg) {
-            const long long q1 = min(re, q0 + kSeg);
-            uint32_t td[kSegPerLane];
-#pragma unroll
-            for (int u = 0; u < kSegPerLane; ++u) {
-                const long long q = q0 + lane + 32 * u;
-                td[u] = q < q1 ? __ldcs(n.tgt_d + q) : 0u;
-            }
+        if (lane == 0) {
+            fence_proxy_async();
+            issue_chunk_w(n, buf[k], &bars[warp][k], pq, cnt, STATE, desc[warp][k]);
+            desc[warp][k].src = psrc;
+            desc[warp][k].row = ps;
+        }
+        pq += cnt;
+    };
+    for (int k = 0; k < kTStages; ++k) {
+        if (!next_row()) break;
+        produce(k);
+        vmask |= 1u << k;
+    }
+    __syncwarp();
+    int abort_c = -1;
+    for (int c = 0;; ++c) {
+        const int k = c % kTStages;
+        if (!((vmask >> k) & 1u)) break;
+        if (!mbar_wait(&bars[warp][k], (uint32_t)((c / kTStages) & 1), n.err_flags)) {
+            abort_c = c;
+            break;
+        }
+        const StageDesc d = desc[warp][k];
+        const StageBuf &sb = buf[k];
+        const int ns = nspk[warp][k];
+        const bool listed = ns <= kSpikeCap;
+        const int s = d.row;
+        const uint32_t *words = src_words_c(n, 0, d.src);
+        const int *sp = spk[warp][k];
+#pragma unroll 1
+        for (int h = 0; h < kChunk / 32; h += 4) {
+            uint32_t td[4];
+            float wv[4], eb[4], ep[4];
+            float4 t0[4];
+            Coef cf0[4], cf1[4];
+            int c0[4], k0s[4];
             // phase 1: which synapses have arrivals; issue every load they need
-            float wv[kSegPerLane], eb[kSegPerLane], ep[kSegPerLane];
-            float4 t0[kSegPerLane];          // table entry of the first arrival
-            Coef cf0[kSegPerLane], cf1[kSegPerLane];
-            int c0[kSegPerLane], k0s[kSegPerLane];
 #pragma unroll
-            for (int u = 0; u < kSegPerLane; ++u) {
-                const long long q = q0 + lane + 32 * u;
-                const int d = (int)(td[u] >> 24);
+            for (int u = 0; u < 4; ++u) {
+                const int idx = lane + 32 * (h + u);
+                const long long q = d.q0 + idx;
+                td[u] = idx < d.n ? sb.td[q - d.q_al] : 0u;
+                const int dl = (int)(td[u] >> 24);
                 const long long j = td[u] & 0xFFFFFFu;
                 bool has = false;
-                int c = 0;
+                int cc = 0;
                 if (td[u] != 0u) {
                     if (listed) {       // first listed spike whose arrival lies after a0
-                        while (c < ns && spk[warp][c] + d <= a0) ++c;
-                        has = c < ns && spk[warp][c] + d <= r_end;
+                        while (cc < ns && sp[cc] + dl <= a0) ++cc;
+                        has = cc < ns && sp[cc] + dl <= r_end;
                     } else {
-                        has = any_spike(words, n.RW, max(s, a0 + 1 - d), r_end - d);
+                        has = any_spike(words, n.RW, max(s, a0 + 1 - dl), r_end - dl);
                     }
                 }
-                c0[u] = has ? c : -1;
+                c0[u] = has ? cc : -1;
                 k0s[u] = -1;
-                wv[u] = has ? __ldcs(n.w + q) : 0.f;
-                eb[u] = (STATE && has) ? load_trace(n.ebar, q, n.trace_bf16) : 0.f;
+                wv[u] = has ? sb.w[q - d.q_al] : 0.f;
+                eb[u] = (STATE && has) ? stage_trace_w(n, sb, d, q) : 0.f;
                 ep[u] = (STATE && ALIF && has) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
                 t0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (has && listed) {
-                    const long long qi = qa + (long long)(spk[warp][c] + d) * N + j;
+                    const long long qi = qa + (long long)(sp[cc] + dl) * N + j;
                     if (ALIF) t0[u] = __ldg(reinterpret_cast<const float4 *>(n.qp) + qi);
                     else {
                         const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qi);
@@ -399,7 +506,7 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
                     }
                 }
                 if (STATE && has) {
-                    const RowInfo ri = info[warp][d];
+                    const RowInfo ri = info[warp][k][dl];
                     if (ri.b_prev != kNoSpike) {
                         int k0 = ri.b_prev / U;
                         if (kW - k0 > n.RC - 1) {
@@ -414,19 +521,19 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
             }
             // phase 2: closed-form advance and weight update
 #pragma unroll
-            for (int u = 0; u < kSegPerLane; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 if (c0[u] < 0) continue;
-                const long long q = q0 + lane + 32 * u;
+                const long long q = d.q0 + lane + 32 * (h + u);
                 const long long j = td[u] & 0xFFFFFFu;
-                const int d = (int)(td[u] >> 24);
+                const int dl = (int)(td[u] >> 24);
                 float G = 0.f, ebar = eb[u], epsa = ep[u];
                 if (STATE) {            // the window's first arrival: restore the state
                     const int k0 = k0s[u];
                     if (k0 >= 0) {
-                        float zbar = info[warp][d].zbar_bp;
+                        float zbar = info[warp][k][dl].zbar_bp;
                         apply_coef<ALIF>(n, cf0[u], zbar, epsa, ebar, G);
                         if (k0 + 1 <= kW) apply_coef<ALIF>(n, cf1[u], zbar, epsa, ebar, G);
-                        for (int k = k0 + 2; k <= kW; ++k) apply_window<ALIF>(n, j, k, zbar, epsa, ebar, G);
+                        for (int kk = k0 + 2; kk <= kW; ++kk) apply_window<ALIF>(n, j, kk, zbar, epsa, ebar, G);
                     } else {
                         ebar = 0.f;
                         epsa = 0.f;
@@ -436,8 +543,8 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
                     G += t0[u].x;
                     ebar += t0[u].y;
                     if (ALIF) epsa += t0[u].z;
-                    for (int c = c0[u] + 1; c < ns; ++c) {
-                        const int a = spk[warp][c] + d;
+                    for (int cc = c0[u] + 1; cc < ns; ++cc) {
+                        const int a = sp[cc] + dl;
                         if (a > r_end) break;
                         if (ALIF) {
                             const float4 t = __ldg(reinterpret_cast<const float4 *>(n.qp) + qa + (long long)a * N + j);
@@ -448,7 +555,7 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
                         }
                     }
                 } else {            // rows with more spikes than the cache holds
-                    G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - d), r_end - d, d, qa + j, ebar, epsa);
+                    G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - dl), r_end - dl, dl, qa + j, ebar, epsa);
                 }
                 __stcs(n.w + q, wv[u] - step * G);
                 if (STATE) {
@@ -457,8 +564,19 @@ __global__ void __launch_bounds__(256, 3) trace_window_kernel(Net n, int i_end) 
                 }
                 if (n.record_grad) n.grad[q] += n.inv_B * G;
             }
-        }                            // segments of the row
+        }
         __syncwarp();
+        vmask &= ~(1u << k);
+        if (next_row()) {
+            produce(k);
+            vmask |= 1u << k;
+        }
+        __syncwarp();
+    }
+    if (abort_c >= 0) {                      // let copies in flight land first
+        for (int c = abort_c + 1; c < abort_c + kTStages; ++c)
+            if ((vmask >> (c % kTStages)) & 1u)
+                mbar_wait(&bars[warp][c % kTStages], (uint32_t)((c / kTStages) & 1), n.err_flags);
     }
 }
 
@@ -656,7 +774,7 @@ void prepare_kernel_attributes() {
     const int limit = 200 * 1024;
     cudaFuncSetAttribute(tables_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(tables_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
-    const int tl = 160 * 1024;
+    const int tl = 200 * 1024;
     cudaFuncSetAttribute(trace_window_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
@@ -679,19 +797,23 @@ int launch_tables(const Net &n, int i_end, cudaStream_t st) {
     const int bd = 128;
     const size_t e_bytes = (size_t)n.U * n.n_out * sizeof(float);
     const size_t l_bytes = (size_t)n.U * bd * sizeof(float);
+    const size_t p_bytes = (size_t)(n.U + 1) * bd * sizeof(float);
     const size_t limit = 200 * 1024;
     int e_in = e_bytes <= limit ? 1 : 0;
     int l_in = (n.n_out > 1 && (e_in ? e_bytes : 0) + l_bytes <= limit) ? 1 : 0;
-    const size_t sm = (e_in ? e_bytes : 0) + (l_in ? l_bytes : 0);
+    size_t sm = (e_in ? e_bytes : 0) + (l_in ? l_bytes : 0);
+    Net m = n;
+    m.tables_psi_smem = sm + p_bytes <= limit ? 1 : 0;
+    if (m.tables_psi_smem) sm += p_bytes;
     const dim3 grid((n.n_rec + bd - 1) / bd, n.B);
-    if (n.alif) tables_kernel<true><<<grid, bd, sm, st>>>(n, i_end, e_in, l_in);
-    else tables_kernel<false><<<grid, bd, sm, st>>>(n, i_end, e_in, l_in);
+    if (n.alif) tables_kernel<true><<<grid, bd, sm, st>>>(m, i_end, e_in, l_in);
+    else tables_kernel<false><<<grid, bd, sm, st>>>(m, i_end, e_in, l_in);
     return 0;
 }
 
 void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st) {
     window_offsets_kernel<<<1, 32, 0, st>>>(n, i_end);
-    const size_t sm = (size_t)(n.U + n.D + 1) * sizeof(long long);
+    const size_t sm = sizeof(StageBuf) * 8 * kTStages + (size_t)(n.U + n.D + 1) * sizeof(long long);
     if (n.has_state) {
         if (n.alif) trace_window_kernel<true, true><<<grid_x, 256, sm, st>>>(n, i_end);
         else trace_window_kernel<false, true><<<grid_x, 256, sm, st>>>(n, i_end);
