@@ -26,6 +26,7 @@ sums, reductions, event/time-driven invariant).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -88,6 +89,9 @@ def _load():
                                             ctypes.c_int32] + [ctypes.c_void_p] * 14
             lib.oracle_eligibility_step.restype = ctypes.c_double
             lib.oracle_eligibility_step.argtypes = [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3
+            lib.oracle_arrival_contrib.restype = None
+            lib.oracle_arrival_contrib.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int32, ctypes.c_int32,
+                                                                           ctypes.c_int64] + [ctypes.c_void_p] * 3
             _lib = lib
     return _lib
 
@@ -106,6 +110,54 @@ def eligibility_step(alpha, rho, beta_a, kappa_e, psi_prev, psi, L, arrive,
     base = st.ctypes.data
     return lib.oracle_eligibility_step(alpha, rho, beta_a, kappa_e, psi_prev,
                                        psi, L, arrive, base, base + 8, base + 16)
+
+
+def arrival_contrib(spec, psi, L, U=None):
+    """Q[a-1, j]: gradient contribution of one unit presynaptic arrival at
+    step a into neuron j, summed to the end of a's update window (width U,
+    default T), from the recorded surrogate values psi and learning signals
+    L ([T, N] of one sample) -- the per-event term of the event-driven update
+    (Sec. "From time-driven to event-driven e-prop")."""
+    lib = _load()
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    T, N = psi.shape
+    Q = np.zeros((T, N))
+    alpha = math.exp(-spec.dt / spec.tau_m)
+    rho = math.exp(-spec.dt / spec.tau_a)
+    kappa_e = math.exp(-spec.dt / spec.tau_out) if spec.kappa_e is None else float(spec.kappa_e)
+    beta = spec.beta_a if spec.neuron_model == 1 else 0.0
+    lib.oracle_arrival_contrib(alpha, rho, beta, kappa_e, T, U or T, N, _p(psi), _p(L), _p(Q))
+    return Q
+
+
+def arrival_magnitude(spec, ptr, col, delay, x_ptr, x_ids, lengths, raster, psi, L):
+    """Per synapse (CSR order), the batch mean over samples of sum_a |Q_j(a)|
+    over the synapse's arrivals a = s + d <= length (single update window):
+    the condition of the event-driven gradient sum."""
+    B, T, N = raster.shape
+    n_in = spec.n_in
+    out = np.zeros(len(col))
+    ptr = np.asarray(ptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    delay = np.asarray(delay, dtype=np.int64)
+    for b in range(B):
+        Qa = np.abs(arrival_contrib(spec, psi[b], L[b]))
+        ln = int(lengths[b])
+        src = np.zeros((ln, n_in + N), dtype=bool)
+        for t in range(ln):
+            src[t, x_ids[x_ptr[b * T + t]:x_ptr[b * T + t + 1]]] = True
+        src[:, n_in:] = raster[b, :ln].astype(bool)
+        for i in range(n_in + N):
+            steps = np.nonzero(src[:, i])[0] + 1
+            if steps.size == 0:
+                continue
+            q = np.arange(ptr[i], ptr[i + 1])
+            for s in steps:
+                a = s + delay[q]
+                ok = a <= ln
+                out[q[ok]] += Qa[a[ok] - 1, col[q[ok]]]
+    return out / B
 
 
 class Oracle:

@@ -134,6 +134,37 @@ double oracle_eligibility_step(double alpha, double rho, double beta_a,
     return L * (*ebar);
 }
 
+/* Contribution of one presynaptic arrival to a synapse gradient.  In the
+   event-driven form (Sec. "From time-driven to event-driven e-prop",
+   event-driven weight updates) the gradient of a synapse is a sum over its
+   presynaptic events, each weighted from the postsynaptic history: by
+   linearity of the eligibility recursion in zbar, an arrival at step a adds
+   Q_j(a) = sum_{t = a}^{b} L_j^t ebar^t, where ebar is the response of the
+   recursion above to one unit arrival at a from a zero state and b is the
+   last step of a's update window (width U).  Computed here from that
+   definition, one forward run of the recursion per (a, j).  psi, L: [T][N]
+   of one sample (row t-1 holds step t); Q: [T][N] (row a-1 holds a).  The
+   sum over a synapse's arrivals of |Q_j(a)| is the condition of the
+   event-driven sum, used by the parity tolerance. */
+void oracle_arrival_contrib(double alpha, double rho, double beta_a, double kappa_e,
+                            int32_t T, int32_t U, int64_t N, const double *psi,
+                            const double *L, double *Q) {
+    for (int32_t a = 1; a <= T; ++a) {
+        const int32_t b = ((a + U - 1) / U) * U < T ? ((a + U - 1) / U) * U : T;
+        for (int64_t j = 0; j < N; ++j) {
+            double zbar = 0.0, epsa = 0.0, ebar = 0.0, q = 0.0;
+            for (int32_t t = a; t <= b; ++t) {
+                const double pp = t > 1 ? psi[(int64_t)(t - 2) * N + j] : 0.0;
+                q += oracle_eligibility_step(alpha, rho, beta_a, kappa_e, pp,
+                                             psi[(int64_t)(t - 1) * N + j],
+                                             L[(int64_t)(t - 1) * N + j],
+                                             t == a ? 1.0 : 0.0, &zbar, &epsa, &ebar);
+            }
+            Q[(int64_t)(a - 1) * N + j] = q;
+        }
+    }
+}
+
 static void reset_state(const oracle_cfg *c, oracle_state *s) {
     int64_t B = c->batch, N = c->n_rec, K = c->n_out, D1 = c->max_delay + 1;
     memset(s->v, 0, sizeof(double) * B * N);

@@ -15,6 +15,8 @@ Agreement rules (written out here and in each test):
   oracle reports these magnitude sums: sum_t |g^t| per gradient element,
   the |W_out|-filtered |y| per readout step; a weight after updates is
   compared on |w_0| + lr * sum |g^t|; a loss on loss + sum |E| |y|_abs.
+  In single-window calls the magnitude sum also counts the per-arrival terms
+  the event-driven sum is formed from (oracle.arrival_magnitude).
   Gradients additionally carry 0.1 x their sensitivity to a relative
   perturbation of the error signal (sum_t Lsens^t |ebar^t|, i.e. an FP32
   error of 1e-6 relative on y and y*), for steps where y - y* cancels.

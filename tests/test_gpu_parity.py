@@ -9,7 +9,9 @@ on the same arrays:
 * oracle B is teacher-forced with the GPU's spikes and surrogate values; it
   checks every gradient and weight element of the trace/learning-signal
   arithmetic (relative 1e-5 of the magnitude sum of the element's terms plus
-  1e-6 of its sensitivity to the error signal, see `tests/parity.py`).
+  1e-6 of its sensitivity to the error signal, see `tests/parity.py`; in
+  single-window calls the terms include the per-arrival contributions the
+  event-driven sum is formed from).
 """
 from __future__ import annotations
 
@@ -49,7 +51,8 @@ def run_parity(W, calls=1, gpu_kw=None, check=True):
     rep = dict(ambiguous=0, mismatches=0, spikes=0, worst={}, rel_l2={})
     nnz_in = int(W["ptr"][s.n_in]) if s.n_in else 0
     nnz = int(W["ptr"][-1])
-    acc = {k: np.zeros(nnz) for k in ("gA", "gB", "magB", "sensB")}
+    acc = {k: np.zeros(nnz) for k in ("gA", "gB", "magB", "sensB", "arrB")}
+    single = not (s.continuous or s.update_interval > 0)
     acc.update({k: np.zeros((s.n_rec, s.n_out)) for k in ("goA", "goB", "gomB", "gosB")})
     prev = None
     for c in range(calls):
@@ -59,8 +62,15 @@ def run_parity(W, calls=1, gpu_kw=None, check=True):
         psi = net.surrogate()
         rA = orA.simulate(s.T, W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"],
                           forced=raster, record=True)
-        orB.simulate(s.T, W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"],
-                     forced=raster, forced_psi=psi)
+        rB = orB.simulate(s.T, W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"],
+                          forced=raster, forced_psi=psi, record=single)
+        if single:
+            # one update window per call: the kernels sum one table entry per
+            # presynaptic arrival, so each element's FP32 condition is the
+            # magnitude sum of those per-arrival terms
+            acc["arrB"] += oracle.arrival_magnitude(s, W["ptr"], W["col"], W["delay"], W["x_ptr"],
+                                                    W["x_ids"], W["lengths"], raster, rB["psi"],
+                                                    rB["L"])
         g, go = orA.take_grads()
         orA.take_grad_magnitudes(), orA.take_grad_sensitivities()
         acc["gA"] += g
@@ -102,7 +112,7 @@ def run_parity(W, calls=1, gpu_kw=None, check=True):
     net.close()
     res = {}
     for name, (sl, w, gw) in parts.items():
-        tol_g = acc["magB"][sl] + 0.1 * acc["sensB"][sl]
+        tol_g = acc["magB"][sl] + 0.1 * acc["sensB"][sl] + acc["arrB"][sl]
         res["g_" + name] = (gw, acc["gB"][sl], tol_g)
         res["w_" + name] = (w, orB.w[sl], w0[sl] + s.lr * tol_g)
         rep["rel_l2"]["e2e_g_" + name] = P.rel_l2(gw, acc["gA"][sl])
@@ -189,21 +199,48 @@ def test_sparse_replica_single_window_window_kernel():
     assert rep["events"] > 0
 
 
-def test_million_replica_continuous_windows():
+# state-carrying window forms: 1 = lazy (catch-up at the next arrival),
+# 3 = dense (every synapse advanced at every window end)
+STATE_KERNELS = [pytest.param(1, id="lazy"), pytest.param(3, id="dense")]
+
+
+@pytest.mark.parametrize("tk", STATE_KERNELS)
+def test_million_replica_continuous_windows(tk):
     # continuous dynamics, update window of 100 steps, three calls of 200
-    # steps: exercises the lazy catch-up of synapses across skipped windows
+    # steps: synapses cross windows with and without arrivals
     W = _replica(True, 200)
-    rep = run_parity(W, calls=3)
+    rep = run_parity(W, calls=3, gpu_kw=dict(trace_kernel=tk))
     assert rep["events"] > 0
 
 
-def test_windows_inside_a_call_without_continuity():
+@pytest.mark.parametrize("tk", STATE_KERNELS)
+def test_windows_inside_a_call_without_continuity(tk):
     W = _replica(True, 300)
     W["spec"].continuous = 0
-    run_parity(W, calls=2)
+    run_parity(W, calls=2, gpu_kw=dict(trace_kernel=tk))
 
 
-def test_alif_continuous_short_windows():
+@pytest.mark.parametrize("tk", STATE_KERNELS)
+def test_input_rows_with_more_spikes_than_the_row_cache(tk):
+    # two input neurons fire at every step: their rows carry more spikes per
+    # window than the per-warp spike cache holds (the bit-scan path)
+    W = C.pattern_regression(T=300)
+    s = W["spec"]
+    s.update_interval, s.continuous = 100, 1
+    ptr, ids = W["x_ptr"], W["x_ids"]
+    steps = [np.union1d(ids[ptr[t]:ptr[t + 1]], [0, 1]).astype(np.int32) for t in range(s.T)]
+    W["x_ptr"] = np.concatenate([[0], np.cumsum([len(x) for x in steps])]).astype(np.int64)
+    W["x_ids"] = np.concatenate(steps).astype(np.int32)
+    # an input that fires at every step feeds the FP32 rounding of its
+    # updated weights into the membrane at every step (the oracle keeps FP64
+    # weights); small weights keep that below the membrane's bound
+    W["w"] = np.asarray(W["w"]).copy()
+    W["w"][W["ptr"][0]:W["ptr"][2]] *= 0.1
+    run_parity(W, calls=2, gpu_kw=dict(trace_kernel=tk))
+
+
+@pytest.mark.parametrize("tk", STATE_KERNELS)
+def test_alif_continuous_short_windows(tk):
     W = C.event_classification(batch=1, T=240, len_lo=240, len_hi=240, n_rec=60,
                                side=8, events_per_300=400.0)
     s = W["spec"]
@@ -212,7 +249,7 @@ def test_alif_continuous_short_windows():
     rng = np.random.default_rng(0)
     W["targets"] = rng.normal(size=W["targets"].shape).astype(np.float32)
     W["window"][:] = 1
-    run_parity(W, calls=3)
+    run_parity(W, calls=3, gpu_kw=dict(trace_kernel=tk))
 
 
 def test_delays_refractory_and_decoupled_filter():
@@ -270,11 +307,12 @@ def test_single_step_samples_and_length_one():
     run_parity(W)
 
 
-def test_bf16_traces_report_error():
+@pytest.mark.parametrize("tk", STATE_KERNELS)
+def test_bf16_traces_report_error(tk):
     # form (1): traces stored in BF16, FP32 accumulation; error vs the FP64
     # oracle is reported, not gated at 1e-5
     W = _replica(True, 200)
-    rep = run_parity(W, calls=3, gpu_kw=dict(trace_dtype=1), check=False)
+    rep = run_parity(W, calls=3, gpu_kw=dict(trace_dtype=1, trace_kernel=tk), check=False)
     print("bf16 traces: rel_l2", {k: f"{v:.3g}" for k, v in rep["rel_l2"].items()},
           "decision mismatches", rep["mismatches"])
     assert rep["rel_l2"]["g_rec"] < 1e-2

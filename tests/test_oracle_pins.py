@@ -381,6 +381,36 @@ def test_event_driven_equals_time_driven(model):
     np.testing.assert_allclose(ge, g, rtol=1e-12, atol=1e-12 * np.abs(g).max())
 
 
+@pytest.mark.parametrize("model", [0, 1])
+def test_arrival_contributions_sum_to_the_gradient(model):
+    # linearity of the eligibility recursion in the presynaptic trace: the
+    # time-driven gradient of a synapse equals the sum, over its arrivals a,
+    # of the forward response Q_j(a) to one unit arrival at a (the per-event
+    # term of the event-driven update); |.| summed bounds |g| from above
+    net, x, tg, window, lengths = _random_small(model, 0, seed=50 + model, B=1, T=60,
+                                                max_delay=4)
+    s = net["spec"]
+    o = oracle.Oracle(s, net["ptr"], net["col"], net["w"], net["delay"], net["w_out"],
+                      net["out_mask"])
+    x_ptr, x_ids = raster_to_lists(x)
+    r = o.simulate(s.T, x_ptr, x_ids, tg, window, lengths, record=True)
+    g, _ = o.take_grads()
+    Q = oracle.arrival_contrib(s, r["psi"][0], r["L"][0])
+    src = _source_raster(s, x_ptr, x_ids, r["raster"], 0, s.T)
+    ge = np.zeros_like(g)
+    for i in range(src.shape[1]):
+        for st in np.nonzero(src[:, i])[0] + 1:
+            for q in range(int(net["ptr"][i]), int(net["ptr"][i + 1])):
+                a = int(st) + int(net["delay"][q])
+                if a <= s.T:
+                    ge[q] += Q[a - 1, int(net["col"][q])]
+    assert np.abs(g).max() > 0
+    np.testing.assert_allclose(ge, g, rtol=1e-12, atol=1e-12 * np.abs(g).max())
+    mag = oracle.arrival_magnitude(s, net["ptr"], net["col"], net["delay"], x_ptr, x_ids,
+                                   lengths, r["raster"], r["psi"], r["L"])
+    assert np.all(mag >= np.abs(g) * (1 - 1e-12))
+
+
 def test_index_flip_future_facing_form():
     # Eq. summation-future: sum_{t'} dL/dz^{t'} e^{t'}, with dL/dz^{t'} =
     # sum_k B_jk sum_{t >= t'} kappa^{t - t'} E_k^t, equals the oracle's causal
