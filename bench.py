@@ -335,7 +335,9 @@ def _run_ours(args, rank, world, local):
                       "BF16 traces: reported in DESIGN.md",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "trace_stream_kernel", "bytes_per_event": bytes_per_event,
+                     "kernel": "window_pass_kernel (active + idle rows, one pair per update window)",
+                     "bytes_per_event": bytes_per_event,
+                     "stream_bytes_per_window": nnz * bytes_per_event,
                      "peak_source": f"{peak_src} (hbm_gbs)",
                      "trace_ms_per_step": trace_ms / K, "trace_launches_per_step": trace_launches / K},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

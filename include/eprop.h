@@ -104,10 +104,16 @@ typedef struct eprop_config {
     int32_t launch_mode;      /* 0: launch every kernel of a simulate call;
                                  1: capture a call once in a CUDA graph and
                                  replay it for later calls with the same T   */
-    int32_t trace_kernel;     /* synapse-trace kernel: 0 auto, 1 window work
-                                 queue (batch 1), 2 batched single window
-                                 (no state carried between windows)          */
-    int32_t blocks_per_sm;    /* CTAs per SM of the row kernels; 0 = 6        */
+    int32_t trace_kernel;     /* synapse-trace kernel: 0 auto (2 for batch >
+                                 1, else 3 when state is carried, else 1);
+                                 1 lazy window work queue (batch 1): only
+                                 synapses with an arrival are touched, a
+                                 skipped window is caught up at the next
+                                 arrival; 2 batched single window (no state
+                                 carried between windows); 3 dense window
+                                 pass (batch 1): every synapse is advanced
+                                 at every window end                         */
+    int32_t blocks_per_sm;    /* CTAs per SM of the row kernels; 0 = 2        */
     int32_t profile;          /* 1: time the synapse-trace kernels of every
                                  window with CUDA events (see eprop_stats)    */
     float dt;                 /* ms                                           */

@@ -25,7 +25,7 @@ struct eprop_net {
     std::vector<void *> in_allocs;      // per-T input buffers
     long long nnz_in = 0;
     int U_alloc = 0, T_alloc = 0, T_in = 0, U_fixed = 0;
-    int trace_mode = 0;                 // 0 window work queue, 1 batched
+    int trace_mode = 0;                 // 0 window work queue, 1 batched, 2 dense window pass
     int qp_stride = 2;
     long long x_cap = 0;
     long long max_in_per_step = 0;
@@ -145,13 +145,23 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     const double qp_bytes = (double)U * N * net->qp_stride * 4.0 * B;
     if (c.trace_kernel == 1) net->trace_mode = 0;
     else if (c.trace_kernel == 2) net->trace_mode = 1;
-    else net->trace_mode = B > 1 ? 1 : 0;
+    else if (c.trace_kernel == 3) net->trace_mode = 2;
+    else net->trace_mode = B > 1 ? 1 : (n.has_state ? 2 : 0);
     (void)qp_bytes;
-    n.RS = net->trace_mode == 0 ? U + D + 1 : 2;
+    n.dense = net->trace_mode == 2 ? 1 : 0;
+    n.RS = net->trace_mode != 1 ? U + D + 1 : 2;
     n.RC = 0;
-    if (n.has_state) {
-        int rc = (3000 + U - 1) / U + 2;
-        n.RC = rc < 4 ? 4 : (rc > 64 ? 64 : rc);
+    if (n.has_state && n.dense) {
+        n.RC = 1;                       // only the current window's coefficients
+    } else if (n.has_state) {
+        // keep the coefficients of every window whose state can still matter:
+        // a state skipped for RC windows has decayed by exp(-RC U / tau) with
+        // the slowest synaptic time constant; RC is a power of two >= 4
+        const double tau = std::max({(double)c.tau_m, (double)c.tau_out,
+                                     c.neuron_model == 1 ? (double)c.tau_a : 0.0}) / c.dt;
+        int rc = 4;
+        while (rc < 256 && std::exp(-(double)rc * U / tau) > 1e-30) rc <<= 1;
+        n.RC = rc;
     }
     std::vector<void *> &o = net->win_allocs;
     void *p;
@@ -195,10 +205,10 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         return fail(nullptr, EPROP_EINVAL, "invalid enum or negative parameter");
     if (c.batch > 1 && (c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL, "batch > 1 needs continuous = 0 and update_interval = 0");
-    if (c.trace_kernel < 0 || c.trace_kernel > 2 || c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
-        return fail(nullptr, EPROP_EINVAL, "trace_kernel must be 0..2 and blocks_per_sm 0..64");
-    if (c.trace_kernel == 1 && c.batch > 1)
-        return fail(nullptr, EPROP_EINVAL, "the streaming trace kernel needs batch = 1");
+    if (c.trace_kernel < 0 || c.trace_kernel > 3 || c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
+        return fail(nullptr, EPROP_EINVAL, "trace_kernel must be 0..3 and blocks_per_sm 0..64");
+    if ((c.trace_kernel == 1 || c.trace_kernel == 3) && c.batch > 1)
+        return fail(nullptr, EPROP_EINVAL, "the window trace kernels need batch = 1");
     if (c.trace_kernel == 2 && (c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL, "the batched trace kernel cannot carry state between windows");
     if (c.n_drive_thr < 0 || c.n_drive_thr > EPROP_MAX_DRIVE_THR)
@@ -517,7 +527,10 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     if (!c.continuous) L += 1;                       // anchor fill
     eprop::launch_begin_call(n, c.continuous, st);
     L += 1;
-    const int grid_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 6) * net->sm_count;
+    // the delivery and trace kernels hold two 256-thread blocks per SM (launch
+    // bounds); their work queues are drained by whichever blocks are resident
+    const int grid_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 2) * net->sm_count;
+    const int pass_rows = 2 * net->sm_count;         // window pass: two blocks per SM
     const int nw = T / U;
     if (c.profile && (int)net->ev.size() < 2 * nw) {
         for (int q = (int)net->ev.size(); q < 2 * nw; ++q) {
@@ -540,6 +553,9 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             if (net->trace_mode == 1) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
                 LT += 1;
+            } else if (net->trace_mode == 2) {
+                eprop::launch_window_pass(n, i, pass_rows, st);
+                LT += 3;
             } else {
                 eprop::launch_trace_window(n, i, grid_rows, st);
                 LT += 2;
@@ -551,7 +567,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             nwin += 1;
         }
     }
-    if (!c.continuous && n.has_state) {
+    if (!c.continuous && n.has_state && !n.dense) {
         eprop::launch_flush(n, T, nullptr, nullptr, 0, n.nnz, 1, net->sm_count, st);
         L += 1;
     }
@@ -634,7 +650,7 @@ extern "C" eprop_status eprop_read_weights_grads(eprop_net *net, int32_t proj, f
     const long long q1 = proj == 0 ? net->nnz_in : n.nnz;
     const long long cnt = q1 - q0;
     if (cnt == 0) return EPROP_OK;
-    if (n.has_state && c.continuous && net->r_base > 0 && net->U_alloc > 0) {
+    if (n.has_state && !n.dense && c.continuous && net->r_base > 0 && net->U_alloc > 0) {
         eprop_status s = ensure_tmp(net, n.nnz);
         if (s != EPROP_OK) return s;
         eprop::launch_flush(n, 0, net->tmp_w, net->tmp_g, q0, q1, 0, net->sm_count, st);

@@ -52,10 +52,10 @@ struct Net {
     long long nnz;
     // model switches
     int alif, t_ref, loss, feedback, has_state, trace_bf16, record_grad, record_raster, record_psi;
+    int dense;                // 1: every synapse advanced at every window end (no catch-up)
     int n_thr, T;             // T of the current call
     int segs;                 // segments per row: ceil(max out-degree / kSeg)
     int list_cap;             // entries per spike-list bucket
-    int tables_psi_smem;      // tables kernel stages psi in shared memory
     // constants (float, computed on the host in double)
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
     float alpha_lo, rho_lo;   // alpha - (float)alpha, rho - (float)rho
@@ -269,10 +269,10 @@ __device__ __forceinline__ void store_trace(void *base, long long q, float x, in
 //   zbar_a0  presynaptic trace F_alpha of the arrivals up to a0, at a0
 //   b_prev   end of the window holding the last arrival <= a0 (kNoSpike: none)
 //   zbar_bp  trace at b_prev
-//   s_first  first spike whose arrival falls inside the window (kNoSpike: none)
+//   k_prev   index of the first window after b_prev (b_prev / U)
 struct RowInfo {
     float zbar_a0, zbar_bp;
-    int b_prev, s_first;
+    int b_prev, k_prev;      // k_prev = b_prev / U (window index after b_prev)
 };
 
 // Computes RowInfo for delay d from the source's spike bits and anchor.
@@ -294,31 +294,16 @@ __device__ __forceinline__ RowInfo row_info(const Net &n, const uint32_t *words,
         ri.zbar_a0 = 0.0f;
         ri.zbar_bp = 0.0f;
         ri.b_prev = kNoSpike;
+        ri.k_prev = 0;
     } else {
         const int a_p = s_p + d;
         const int b_p = ((a_p + n.U - 1) / n.U) * n.U;
         ri.b_prev = b_p;
+        ri.k_prev = b_p / n.U;
         ri.zbar_bp = z_p * pow_alpha(n, b_p - a_p);
         ri.zbar_a0 = z_p * pow_alpha(n, a0 - a_p);
     }
-    ri.s_first = kNoSpike;
-    if (want_first) {            // first set bit in [lim + 1, a0 + U - d], word by word
-        const int hi = a0 + n.U - d;
-        const int mask = n.RW * 32 - 1;
-        int r = lim + 1 > 1 ? lim + 1 : 1;
-        while (r <= hi) {
-            const int p = r & mask;
-            const int bit = p & 31;
-            const int span = min(31 - bit, hi - r);
-            uint32_t m = words[p >> 5] >> bit;
-            if (span < 31) m &= (2u << span) - 1u;
-            if (m) {
-                ri.s_first = r + __ffs(m) - 1;
-                break;
-            }
-            r += span + 1;
-        }
-    }
+    (void)want_first;
     return ri;
 }
 
@@ -330,7 +315,7 @@ struct Coef {
 template <bool ALIF>
 __device__ __forceinline__ Coef load_coef(const Net &n, long long j, int k) {
     Coef c;
-    const int slot = k % n.RC;
+    const int slot = k & (n.RC - 1);
     if (ALIF) {
         const float4 *p = reinterpret_cast<const float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
         c.c0 = __ldg(p);
@@ -362,7 +347,7 @@ __device__ __forceinline__ void apply_coef(const Net &n, const Coef &c, float &z
 template <bool ALIF>
 __device__ __forceinline__ void apply_window(const Net &n, long long j, int k, float &zbar,
                                              float &epsa, float &ebar, float &G) {
-    const int slot = k % n.RC;
+    const int slot = k & (n.RC - 1);
     if (ALIF) {
         const float4 *c = reinterpret_cast<const float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
         const float4 c0 = c[0], c1 = c[1];   // (cz, ca, ce, maz), (maa, mez, mea, -)

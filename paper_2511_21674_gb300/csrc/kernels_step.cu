@@ -296,11 +296,16 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
     __shared__ StageDesc desc[8][kDStages];
     __shared__ RowInfo info[8][kDStages][kMaxDelay + 1];
     __shared__ unsigned long long ev_block;
+    __shared__ long long ring_off[kMaxDelay + 1];
     const int b = blockIdx.y;
     if (i > n.lengths[b]) return;            // whole block: same sample
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kDStages;
     if (threadIdx.x == 0) ev_block = 0ULL;
+    if (threadIdx.x <= n.D) {                // ring slot of an arrival d steps ahead
+        const long long t_abs0 = abs_step(n, i);
+        ring_off[threadIdx.x] = (long long)((t_abs0 + threadIdx.x) % (n.D + 1)) * n.n_rec;
+    }
     if (lane < kDStages) mbar_init(&bars[warp][lane], 1);
     fence_mbar_init();
     __syncthreads();
@@ -308,7 +313,6 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
     const int r = run_step(n, i);
     const int a0 = win_start(n, r);
     const int k1 = a0 / n.U;                 // windows < k1 are closed
-    const long long t_abs = abs_step(n, i);
     const long long li = list_index(n, b, r % n.RS);
     const int *ids = n.list_ids + li * n.list_cap;
     const BucketScan bs = bucket_scan(n.list_cnt + li);
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
                     if (ri.b_prev == kNoSpike || ri.b_prev >= a0) continue;
                     const long long q = d.q0 + lane + 32 * (h + u);
                     const long long j = td[u] & 0xFFFFFFu;
-                    int k0 = ri.b_prev / n.U;
+                    int k0 = ri.k_prev;
                     if (k1 - k0 > n.RC) {
                         atomicOr(n.err_flags, 1u);
                         k0 = k1 - n.RC;
@@ -416,8 +420,7 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
                 const int j = (int)(td[u] & 0xFFFFFFu);
                 const int dl = (int)(td[u] >> 24);
                 const long long fx = __float2ll_rn(wv[u] * 4294967296.0f);
-                atomicAdd(reinterpret_cast<unsigned long long *>(
-                              &ring_b[(long long)((t_abs + dl) % D1) * n.n_rec + j]),
+                atomicAdd(reinterpret_cast<unsigned long long *>(&ring_b[ring_off[dl] + j]),
                           (unsigned long long)fx);
             }
         }
@@ -492,7 +495,7 @@ void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
 void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st) {
     const dim3 grid(grid_x, n.B);
     const size_t sm = sizeof(StageBuf) * 8 * kDStages;
-    if (n.has_state) {
+    if (n.has_state && !n.dense) {
         if (n.alif) deliver_kernel<true, true><<<grid, 256, sm, st>>>(n, i);
         else deliver_kernel<false, true><<<grid, 256, sm, st>>>(n, i);
     } else {

@@ -90,64 +90,21 @@ __global__ void filter_error_kernel(Net n) {
 // a per-thread shared-memory column, then a backward adjoint sweep writes
 // the per-step tables and the window coefficients.
 template <bool ALIF>
-__global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
-    extern __shared__ float smem[];
+__global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
+    constexpr int kTC = ALIF ? 16 : 32;     // window steps per chunk
+    constexpr int kKT = 32;                 // feedback columns per shared tile
+    __shared__ float Bs[128][kKT + 1];
     const int b = blockIdx.y;
     const int U = n.U, K = n.n_out, N = n.n_rec;
     const int r_end = run_step_w(n, i_end);
     const int a0 = r_end - U;
-    const float *Eg = n.E_win + (long long)b * U * K;
-    float *Es = smem;
-    float *Ls = smem + (e_in_smem ? U * K : 0);
-    float *Ps = Ls + (l_in_smem ? U * blockDim.x : 0);     // psi [U+1][bd] (when it fits)
-    const bool psi_in_smem = n.tables_psi_smem;
-    if (e_in_smem)
-        for (int q = threadIdx.x; q < U * K; q += blockDim.x) Es[q] = Eg[q];
-    const int j0 = blockIdx.x * blockDim.x;
-    if (psi_in_smem) {          // coalesced rows of the block's neurons, all loads in flight
-        const float *pg = n.psi_hist + (long long)b * (U + 1) * N;
-        for (int q = threadIdx.x; q < (U + 1) * (int)blockDim.x; q += blockDim.x) {
-            const int u = q / blockDim.x, c = q % blockDim.x;
-            Ps[q] = (j0 + c < N) ? pg[(long long)u * N + j0 + c] : 0.f;
-        }
-    }
-    __syncthreads();
-    const float *E = e_in_smem ? Es : Eg;
-    const int j = j0 + threadIdx.x;
-    if (j >= N) return;
-    const float *Bj = n.fb + (long long)j * K;
-    const int bd = blockDim.x, tid = threadIdx.x;
-    if (l_in_smem) {
-        for (int u = 0; u < U; ++u) Ls[u * bd + tid] = 0.0f;
-        for (int k0 = 0; k0 < K; k0 += 8) {
-            float f[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) f[c] = (k0 + c < K) ? Bj[k0 + c] : 0.0f;
-            const int kc = min(8, K - k0);
-            for (int u = 0; u < U; ++u) {
-                const float *e = E + u * K + k0;
-                float acc = Ls[u * bd + tid];
-                if (kc == 8) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) acc += f[c] * e[c];
-                } else {
-                    for (int c = 0; c < kc; ++c) acc += f[c] * e[c];
-                }
-                Ls[u * bd + tid] = acc;
-            }
-        }
-    }
-    auto Lat = [&](int u) -> float {      // L at window step u (1..U)
-        if (l_in_smem) return Ls[(u - 1) * bd + tid];
-        float acc = 0.0f;
-        const float *e = E + (u - 1) * K;
-        for (int k = 0; k < K; ++k) acc += Bj[k] * e[k];
-        return acc;
-    };
-    const float *psi_g = n.psi_hist + (long long)b * (U + 1) * N + j;
-    auto PSI = [&](int u) -> float {
-        return psi_in_smem ? Ps[u * bd + tid] : psi_g[(long long)u * N];
-    };
+    const float *E = n.E_win + (long long)b * U * K;
+    const int tid = threadIdx.x;
+    const int j0 = blockIdx.x * 128;
+    const int j = j0 + tid;
+    const bool act = j < N;
+    const float *psi_g = n.psi_hist + (long long)b * (U + 1) * N + (act ? j : 0);
+    const bool vec4 = (K & 3) == 0;
     // The adjoint sweep is the per-window reduction of the gradient.  For
     // ALIF the eligibility psi (zbar - beta eps_a) is a near-cancellation of
     // two long-memory traces, so the sweep runs in FP64 there (FP32 loses up
@@ -158,45 +115,93 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
     const R rho = ALIF ? (R)n.rho + (R)n.rho_lo : (R)0;
     const R beta = n.beta_a;
     const R ke = n.kappa_e;
-    R pn = PSI(U);          // psi^b
-    const float psi_b = PSI(U);
     // adjoint of G (mz, ma, me); of ebar^b (ez, ea, ee); of eps_a^b (az, aa, ae)
-    R mz = 0, ma = 0, me = Lat(U);
+    R mz = 0, ma = 0, me = 0;
     R ez = 0, ea = 0, ee = 1;
     R az = 0, aa = 1, ae = 0;
-    long long qbase = ((long long)b * U) * N + j;
-    if (ALIF) {
-        reinterpret_cast<float4 *>(n.qp)[qbase + (long long)(U - 1) * N] =
-            make_float4((float)(mz + pn * me), (float)(ez + pn * ee), (float)(az + pn * ae), 0.f);
-    } else {
-        reinterpret_cast<float2 *>(n.qp)[qbase + (long long)(U - 1) * N] =
-            make_float2((float)(mz + pn * me), (float)(ez + pn * ee));
-    }
-    for (int u = U - 1; u >= 0; --u) {
-        const R p = PSI(u);       // psi^{a0+u}
-        // x -> (A^{u+1})^T x
-        if (ALIF) {
-            const R g1 = alpha - beta * p, g2 = rho - beta * p;
-            R nz = alpha * mz + p * ma + pn * g1 * me;
-            R na = g2 * ma - beta * pn * g2 * me;
-            R ne = ke * me;
-            mz = nz; ma = na; me = ne;
-            nz = alpha * ez + p * ea + pn * g1 * ee;
-            na = g2 * ea - beta * pn * g2 * ee;
-            ne = ke * ee;
-            ez = nz; ea = na; ee = ne;
-            nz = alpha * az + p * aa + pn * g1 * ae;
-            na = g2 * aa - beta * pn * g2 * ae;
-            ne = ke * ae;
-            az = nz; aa = na; ae = ne;
-        } else {
-            mz = alpha * mz + alpha * pn * me;
-            me = ke * me;
-            ez = alpha * ez + alpha * pn * ee;
-            ee = ke * ee;
+    R pn = 0;
+    const float psi_b = act ? psi_g[(long long)U * N] : 0.f;
+    const long long qbase = ((long long)b * U) * N + j;
+    // Steps are taken backwards in chunks of kTC.  A chunk's learning
+    // signals L^t = sum_k B_jk E_k^t are formed in registers from feedback
+    // tiles staged in shared memory (coalesced rows of the block's neurons)
+    // and the window errors E (the same address for every thread); then the
+    // recursion runs over the chunk in registers.
+    for (int u1 = U; u1 >= 1; u1 -= kTC) {
+        const int u0 = max(1, u1 - kTC + 1);            // chunk = steps u0..u1
+        float Lc[kTC], Pc[kTC + 1];
+#pragma unroll
+        for (int c = 0; c < kTC; ++c) {
+            const int u = u1 - c;
+            Lc[c] = 0.f;
+            Pc[c] = (act && u >= u0) ? psi_g[(long long)u * N] : 0.f;
         }
-        if (u >= 1) {
-            me += (R)Lat(u);
+        Pc[kTC] = act ? psi_g[(long long)(u0 - 1) * N] : 0.f;   // psi of the step before the chunk
+        for (int k0 = 0; k0 < K; k0 += kKT) {
+            const int kt = min(kKT, K - k0);
+            __syncthreads();
+            for (int q = tid; q < 128 * kKT; q += 128) {
+                const int r = q / kKT, cc = q % kKT;
+                const int jr = j0 + r;
+                Bs[r][cc] = (jr < N && cc < kt) ? n.fb[(long long)jr * K + k0 + cc] : 0.f;
+            }
+            __syncthreads();
+            int kk = 0;
+            if (vec4) {
+                for (; kk + 4 <= kt; kk += 4) {
+                    const float b0 = Bs[tid][kk], b1 = Bs[tid][kk + 1], b2 = Bs[tid][kk + 2], b3 = Bs[tid][kk + 3];
+#pragma unroll
+                    for (int c = 0; c < kTC; ++c) {
+                        const int u = u1 - c;
+                        if (u >= u0) {
+                            const float4 e = __ldg(reinterpret_cast<const float4 *>(E + (long long)(u - 1) * K + k0 + kk));
+                            Lc[c] = fmaf(b0, e.x, Lc[c]);
+                            Lc[c] = fmaf(b1, e.y, Lc[c]);
+                            Lc[c] = fmaf(b2, e.z, Lc[c]);
+                            Lc[c] = fmaf(b3, e.w, Lc[c]);
+                        }
+                    }
+                }
+            }
+            for (; kk < kt; ++kk) {
+                const float b0 = Bs[tid][kk];
+#pragma unroll
+                for (int c = 0; c < kTC; ++c) {
+                    const int u = u1 - c;
+                    if (u >= u0) Lc[c] = fmaf(b0, __ldg(E + (long long)(u - 1) * K + k0 + kk), Lc[c]);
+                }
+            }
+        }
+        if (!act) continue;
+#pragma unroll
+        for (int c = 0; c < kTC; ++c) {
+            const int u = u1 - c;
+            if (u < u0) break;
+            const R p = Pc[c];                               // psi^{a0+u}
+            if (u < U) {
+                // x -> (A^{u+1})^T x with A^{u+1} from psi^u = p, psi^{u+1} = pn
+                if (ALIF) {
+                    const R g1 = alpha - beta * p, g2 = rho - beta * p;
+                    R nz = alpha * mz + p * ma + pn * g1 * me;
+                    R na = g2 * ma - beta * pn * g2 * me;
+                    R ne = ke * me;
+                    mz = nz; ma = na; me = ne;
+                    nz = alpha * ez + p * ea + pn * g1 * ee;
+                    na = g2 * ea - beta * pn * g2 * ee;
+                    ne = ke * ee;
+                    ez = nz; ea = na; ee = ne;
+                    nz = alpha * az + p * aa + pn * g1 * ae;
+                    na = g2 * aa - beta * pn * g2 * ae;
+                    ne = ke * ae;
+                    az = nz; aa = na; ae = ne;
+                } else {
+                    mz = alpha * mz + alpha * pn * me;
+                    me = ke * me;
+                    ez = alpha * ez + alpha * pn * ee;
+                    ee = ke * ee;
+                }
+            }
+            me += (R)Lc[c];
             if (ALIF) {
                 reinterpret_cast<float4 *>(n.qp)[qbase + (long long)(u - 1) * N] =
                     make_float4((float)(mz + p * me), (float)(ez + p * ee), (float)(az + p * ae), 0.f);
@@ -204,12 +209,37 @@ __global__ void tables_kernel(Net n, int i_end, int e_in_smem, int l_in_smem) {
                 reinterpret_cast<float2 *>(n.qp)[qbase + (long long)(u - 1) * N] =
                     make_float2((float)(mz + p * me), (float)(ez + p * ee));
             }
+            pn = p;
         }
-        pn = p;
+        if (u0 == 1) {
+            // step a0 (u = 0): the window coefficients c = (A^{a0+1})^T mu^{a0+1}
+            const R p = Pc[kTC];
+            if (ALIF) {
+                const R g1 = alpha - beta * p, g2 = rho - beta * p;
+                R nz = alpha * mz + p * ma + pn * g1 * me;
+                R na = g2 * ma - beta * pn * g2 * me;
+                R ne = ke * me;
+                mz = nz; ma = na; me = ne;
+                nz = alpha * ez + p * ea + pn * g1 * ee;
+                na = g2 * ea - beta * pn * g2 * ee;
+                ne = ke * ee;
+                ez = nz; ea = na; ee = ne;
+                nz = alpha * az + p * aa + pn * g1 * ae;
+                na = g2 * aa - beta * pn * g2 * ae;
+                ne = ke * ae;
+                az = nz; aa = na; ae = ne;
+            } else {
+                mz = alpha * mz + alpha * pn * me;
+                me = ke * me;
+                ez = alpha * ez + alpha * pn * ee;
+                ee = ke * ee;
+            }
+        }
     }
+    if (!act) return;
     // window coefficients: c = (mz, ma, me), Phi rows (ez, ea, .) and (az, aa, .)
     if (n.has_state) {
-        const int slot = (a0 / U) % n.RC;
+        const int slot = (a0 / U) & (n.RC - 1);
         if (ALIF) {
             float4 *c = reinterpret_cast<float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
             c[0] = make_float4((float)mz, (float)ma, (float)me, (float)az);
@@ -508,7 +538,7 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
                 if (STATE && has) {
                     const RowInfo ri = info[warp][k][dl];
                     if (ri.b_prev != kNoSpike) {
-                        int k0 = ri.b_prev / U;
+                        int k0 = ri.k_prev;
                         if (kW - k0 > n.RC - 1) {
                             atomicOr(n.err_flags, 1u);
                             k0 = kW - (n.RC - 1);
@@ -562,6 +592,216 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
                     store_trace(n.ebar, q, ebar, n.trace_bf16);
                     if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
                 }
+                if (n.record_grad) n.grad[q] += n.inv_B * G;
+            }
+        }
+        __syncwarp();
+        vmask &= ~(1u << k);
+        if (next_row()) {
+            produce(k);
+            vmask |= 1u << k;
+        }
+        __syncwarp();
+    }
+    if (abort_c >= 0) {                      // let copies in flight land first
+        for (int c = abort_c + 1; c < abort_c + kTStages; ++c)
+            if ((vmask >> (c % kTStages)) & 1u)
+                mbar_wait(&bars[warp][c % kTStages], (uint32_t)((c / kTStages) & 1), n.err_flags);
+    }
+}
+
+// Dense form of the window update.  Every synapse is advanced to the end
+// of every window, so the stored weight and traces are always those of the
+// window start and spike delivery reads the weight as it is (no catch-up).
+// The state x = (zbar, eps_a, ebar) at a0 passes through the window's
+// coefficients (G += c . x, x <- Phi x); each arrival a in the window adds
+// Q(a) to G and Pe(a), Pa(a) to the traces (event-driven weight update from
+// the archived postsynaptic history, Sec. "From time-driven to event-driven
+// e-prop"; the per-window tables stand for that history).
+// ACTIVE = true: rows with a spike whose arrival can fall in the window,
+// taken from the per-step spike lists in ascending emission step (the row
+// belongs to its first such spike), so the table slabs in use stay in L2;
+// ACTIVE = false: all other rows, in index order (state advance only).
+// Per warp a kTStages-deep pipeline of bulk copies brings the (j|d, w, ebar)
+// streams of the next chunks into shared memory while the current chunk is
+// advanced; what stays on the critical path are the targets' window
+// coefficients (L2-resident) and, in the active pass, the table entries.
+template <bool ALIF, bool ACTIVE>
+__global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ uint64_t bars[8][kTStages];
+    __shared__ StageDesc desc[8][kTStages];
+    __shared__ float zbs[8][kTStages][kMaxDelay + 1];
+    __shared__ int spk[8][ACTIVE ? kTStages : 1][kSpikeCap];
+    __shared__ int nspk[8][kTStages];
+    __shared__ int rspk[8][kSpikeCap];          // the producer's current row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kTStages;
+    long long *off = reinterpret_cast<long long *>(dsm + sizeof(StageBuf) * 8 * kTStages);
+    const int U = n.U, N = n.n_rec;
+    const int r_end = run_step_w(n, i_end);
+    const int a0 = r_end - U;
+    const int s_lo = max(a0 + 1 - n.D, 1);
+    const int s_hi = r_end - 1;
+    const int nsteps = s_hi - s_lo + 1;
+    if (ACTIVE && nsteps <= 0) return;
+    if (ACTIVE)
+        for (int k = threadIdx.x; k <= nsteps; k += blockDim.x) off[k] = n.win_off[k];
+    if (lane < kTStages) mbar_init(&bars[warp][lane], 1);
+    fence_mbar_init();
+    __syncthreads();
+    const long long total = ACTIVE ? off[nsteps] : (long long)n.n_src;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const float step = n.lr * n.inv_B;
+    const long long qa = (long long)(-a0 - 1) * N;     // table index = qa + a * N + j
+    // producer cursor (warp-uniform): work item, current row and its range
+    long long pit = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    long long pq = 0, pre = 0;
+    int psrc = -1, ps = s_lo, pns = 0;
+    float pzb = 0.f;            // lane d: zbar at a0 of the row's delay-d synapses
+    unsigned vmask = 0;
+    auto next_row = [&]() -> bool {
+        while (pq >= pre) {
+            if (pit >= total) return false;
+            int src, s = s_lo;
+            if (ACTIVE) {
+                int lo = 0, hi = nsteps;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (off[mid] <= pit) lo = mid; else hi = mid;
+                }
+                s = s_lo + lo;
+                const long long li = list_index(n, 0, s % n.RS);
+                const BucketScan bs = bucket_scan(n.list_cnt + li);
+                src = bucket_entry(n, n.list_ids + li * n.list_cap, bs, (int)(pit - off[lo]));
+            } else {
+                src = (int)pit;
+            }
+            pit += nw;
+            const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
+            if (re <= rb) continue;
+            const uint32_t *words = src_words_c(n, 0, src);
+            if (ACTIVE) {
+                if (any_spike(words, n.RW, s_lo, s - 1)) continue;     // another item owns the row
+            } else {
+                if (nsteps > 0 && any_spike(words, n.RW, s_lo, s_hi)) continue;   // active pass
+            }
+            if (ACTIVE) {
+                int ns = 0;
+                if (lane == 0) {         // the row's spikes in [s, s_hi], ascending
+                    const int mask = n.RW * 32 - 1;
+                    int r = s;
+                    while (r <= s_hi) {
+                        const int p = r & mask;
+                        const int bit = p & 31;
+                        const int span = min(31 - bit, s_hi - r);
+                        uint32_t m = words[p >> 5] >> bit;
+                        if (span < 31) m &= (2u << span) - 1u;
+                        while (m) {
+                            if (ns < kSpikeCap) rspk[warp][ns] = r + __ffs(m) - 1;
+                            ++ns;
+                            m &= m - 1;
+                        }
+                        r += span + 1;
+                    }
+                }
+                pns = __shfl_sync(0xffffffffu, ns, 0);
+            }
+            pzb = (lane >= 1 && lane <= n.D)
+                      ? row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false).zbar_a0
+                      : 0.f;
+            psrc = src;
+            ps = s;
+            pq = rb;
+            pre = re;
+        }
+        return true;
+    };
+    auto produce = [&](int k) {
+        const int cnt = (int)min((long long)kChunk, pre - pq);
+        if (lane <= n.D) zbs[warp][k][lane] = pzb;
+        if (ACTIVE) {
+            for (int c = lane; c < min(pns, kSpikeCap); c += 32) spk[warp][k][c] = rspk[warp][c];
+            if (lane == 0) nspk[warp][k] = pns;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async();
+            issue_chunk_w(n, buf[k], &bars[warp][k], pq, cnt, true, desc[warp][k]);
+            desc[warp][k].src = psrc;
+            desc[warp][k].row = ps;
+        }
+        pq += cnt;
+    };
+    for (int k = 0; k < kTStages; ++k) {
+        if (!next_row()) break;
+        produce(k);
+        vmask |= 1u << k;
+    }
+    __syncwarp();
+    int abort_c = -1;
+    for (int c = 0;; ++c) {
+        const int k = c % kTStages;
+        if (!((vmask >> k) & 1u)) break;
+        if (!mbar_wait(&bars[warp][k], (uint32_t)((c / kTStages) & 1), n.err_flags)) {
+            abort_c = c;
+            break;
+        }
+        const StageDesc d = desc[warp][k];
+        const StageBuf &sb = buf[k];
+        const int ns = ACTIVE ? nspk[warp][k] : 0;
+        const bool listed = ns <= kSpikeCap;
+        const int *sp = spk[warp][ACTIVE ? k : 0];
+        constexpr int kB = ALIF ? 4 : 8;       // synapses per lane in flight
+#pragma unroll 1
+        for (int h = 0; h < kChunk / 32; h += kB) {
+            uint32_t td[kB];
+            float wv[kB], zr[kB], eb[kB], ep[kB];
+            Coef cf[kB];
+            bool live[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int idx = lane + 32 * (h + u);
+                const long long q = d.q0 + idx;
+                const bool in = idx < d.n;
+                td[u] = in ? sb.td[q - d.q_al] : 0u;
+                zr[u] = zbs[warp][k][td[u] >> 24];
+                wv[u] = in ? sb.w[q - d.q_al] : 0.f;
+                eb[u] = in ? stage_trace_w(n, sb, d, q) : 0.f;
+                ep[u] = (ALIF && in) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+                live[u] = in && (ACTIVE || zr[u] != 0.f || eb[u] != 0.f || ep[u] != 0.f);
+                if (live[u]) cf[u] = load_coef<ALIF>(n, td[u] & 0xFFFFFFu, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                if (!live[u]) continue;
+                const long long q = d.q0 + lane + 32 * (h + u);
+                const long long j = td[u] & 0xFFFFFFu;
+                const int dl = (int)(td[u] >> 24);
+                float G = 0.f, zbar = zr[u], ebar = eb[u], epsa = ep[u];
+                apply_coef<ALIF>(n, cf[u], zbar, epsa, ebar, G);
+                if (ACTIVE) {
+                    if (listed) {
+                        for (int cc = 0; cc < ns; ++cc) {
+                            const int a = sp[cc] + dl;
+                            if (a <= a0) continue;
+                            if (a > r_end) break;
+                            if (ALIF) {
+                                const float4 t = __ldg(reinterpret_cast<const float4 *>(n.qp) + qa + (long long)a * N + j);
+                                G += t.x; ebar += t.y; epsa += t.z;
+                            } else {
+                                const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qa + (long long)a * N + j);
+                                G += t.x; ebar += t.y;
+                            }
+                        }
+                    } else {            // rows with more spikes than the cache holds
+                        G += scan_arrivals<ALIF>(n, src_words_c(n, 0, d.src), max(d.row, a0 + 1 - dl),
+                                                 r_end - dl, dl, qa + j, ebar, epsa);
+                    }
+                }
+                if (G != 0.f) __stcs(n.w + q, wv[u] - step * G);
+                store_trace(n.ebar, q, ebar, n.trace_bf16);
+                if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
                 if (n.record_grad) n.grad[q] += n.inv_B * G;
             }
         }
@@ -727,7 +967,7 @@ __global__ void flush_kernel(Net n, int i_end, float *w_dst, float *g_dst, long 
                 float zbar = ri.zbar_bp;
                 float ebar = load_trace(n.ebar, q, n.trace_bf16);
                 float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
-                int k0 = ri.b_prev / U;
+                int k0 = ri.k_prev;
                 const int k1 = a0 / U;
                 if (k1 - k0 > n.RC) {
                     atomicOr(n.err_flags, 1u);
@@ -771,10 +1011,11 @@ __global__ void unpack_raster_kernel(Net n, unsigned char *dst) {
 // ----------------------------------------------------------------- launches
 
 void prepare_kernel_attributes() {
-    const int limit = 200 * 1024;
-    cudaFuncSetAttribute(tables_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
-    cudaFuncSetAttribute(tables_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     const int tl = 200 * 1024;
+    cudaFuncSetAttribute(window_pass_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
+    cudaFuncSetAttribute(window_pass_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
+    cudaFuncSetAttribute(window_pass_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
+    cudaFuncSetAttribute(window_pass_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
@@ -795,19 +1036,9 @@ void launch_filter_error(const Net &n, int i_end, cudaStream_t st) {
 
 int launch_tables(const Net &n, int i_end, cudaStream_t st) {
     const int bd = 128;
-    const size_t e_bytes = (size_t)n.U * n.n_out * sizeof(float);
-    const size_t l_bytes = (size_t)n.U * bd * sizeof(float);
-    const size_t p_bytes = (size_t)(n.U + 1) * bd * sizeof(float);
-    const size_t limit = 200 * 1024;
-    int e_in = e_bytes <= limit ? 1 : 0;
-    int l_in = (n.n_out > 1 && (e_in ? e_bytes : 0) + l_bytes <= limit) ? 1 : 0;
-    size_t sm = (e_in ? e_bytes : 0) + (l_in ? l_bytes : 0);
-    Net m = n;
-    m.tables_psi_smem = sm + p_bytes <= limit ? 1 : 0;
-    if (m.tables_psi_smem) sm += p_bytes;
     const dim3 grid((n.n_rec + bd - 1) / bd, n.B);
-    if (n.alif) tables_kernel<true><<<grid, bd, sm, st>>>(m, i_end, e_in, l_in);
-    else tables_kernel<false><<<grid, bd, sm, st>>>(m, i_end, e_in, l_in);
+    if (n.alif) tables_kernel<true><<<grid, bd, 0, st>>>(n, i_end);
+    else tables_kernel<false><<<grid, bd, 0, st>>>(n, i_end);
     return 0;
 }
 
@@ -820,6 +1051,19 @@ void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st) {
     } else {
         if (n.alif) trace_window_kernel<true, false><<<grid_x, 256, sm, st>>>(n, i_end);
         else trace_window_kernel<false, false><<<grid_x, 256, sm, st>>>(n, i_end);
+    }
+}
+
+void launch_window_pass(const Net &n, int i_end, int grid_x, cudaStream_t st) {
+    window_offsets_kernel<<<1, 32, 0, st>>>(n, i_end);
+    const size_t sb = sizeof(StageBuf) * 8 * kTStages;
+    const size_t sm = sb + (size_t)(n.U + n.D + 2) * sizeof(long long);
+    if (n.alif) {
+        window_pass_kernel<true, true><<<grid_x, 256, sm, st>>>(n, i_end);
+        window_pass_kernel<true, false><<<grid_x, 256, sb, st>>>(n, i_end);
+    } else {
+        window_pass_kernel<false, true><<<grid_x, 256, sm, st>>>(n, i_end);
+        window_pass_kernel<false, false><<<grid_x, 256, sb, st>>>(n, i_end);
     }
 }
 
