@@ -286,7 +286,20 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
             }
             /* learning signal */
             const double *Bm = c->feedback ? s->fb : s->w_out;
-            for (int64_t k = 0; k < K; ++k) Esens[k] = win * (y_abs[k] + fabs(tgt[k]));
+            /* sensitivity of E_k to a relative perturbation of the readout
+               (its inputs summed in magnitude, y_abs) and of the target:
+               MSE  E_k = y_k - y*_k:      |y|_abs,k + |y*_k|;
+               CE   E_k = pi_k - pi*_k:    d pi_k = pi_k (dy_k - sum_l pi_l dy_l),
+                    so pi_k (|y|_abs,k + sum_l pi_l |y|_abs,l) + pi_k + pi*_k
+                    (the last two: rounding of pi_k and of the difference) */
+            if (c->loss == 0) {
+                for (int64_t k = 0; k < K; ++k) Esens[k] = win * (y_abs[k] + fabs(tgt[k]));
+            } else {
+                double pya = 0.0;
+                for (int64_t k = 0; k < K; ++k) pya += pi[k] * y_abs[k];
+                for (int64_t k = 0; k < K; ++k)
+                    Esens[k] = win * (pi[k] * (y_abs[k] + pya) + pi[k] + fabs(tgt[k]));
+            }
             for (int64_t j = 0; j < N; ++j) {
                 double acc = 0.0, accs = 0.0;
                 for (int64_t k = 0; k < K; ++k) {
