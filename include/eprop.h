@@ -81,7 +81,9 @@ typedef struct eprop_net eprop_net; /* opaque; owned by the library */
  * External drive: n_j^t = #{m < n_drive_thr : u >= drive_thr[m]} with u the
  * upper 32 bits of h = mix(mix(mix(drive_seed ^ j) ^ t_abs) ^ sample),
  * mix = the SplitMix64 output function, t_abs = the network's absolute step
- * counter (1 for the first step after creation).
+ * counter (1 for the first step after creation).  drive_thr[0 .. n_drive_thr)
+ * must be non-decreasing (an inversion table of a CDF); creation fails with
+ * EPROP_EINVAL otherwise.
  */
 typedef struct eprop_config {
     int32_t abi_version;      /* must be EPROP_ABI_VERSION */

@@ -213,6 +213,9 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         return fail(nullptr, EPROP_EINVAL, "the batched trace kernel cannot carry state between windows");
     if (c.n_drive_thr < 0 || c.n_drive_thr > EPROP_MAX_DRIVE_THR)
         return fail(nullptr, EPROP_EINVAL, "n_drive_thr out of range");
+    for (int m = 1; m < c.n_drive_thr; ++m)
+        if (c.drive_thr[m] < c.drive_thr[m - 1])
+            return fail(nullptr, EPROP_EINVAL, "drive_thr must be non-decreasing");
     if (!(c.dt > 0.f) || !(c.tau_m > 0.f) || !(c.tau_out > 0.f) || (c.neuron_model == 1 && !(c.tau_a > 0.f)))
         return fail(nullptr, EPROP_EINVAL, "dt and time constants must be positive");
     if (syn->n_src != (int64_t)c.n_in + c.n_rec || syn->nnz < 0 || (syn->nnz > 0 && (!syn->row_ptr ||

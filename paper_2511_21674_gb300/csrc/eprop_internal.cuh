@@ -43,7 +43,7 @@ constexpr int kNoSpike = -1073741824;               // "no spike" time
 struct Clock {            // device-resident time base (graph-safe)
     long long t_abs_base; // absolute steps completed before the current call
     int r_base;           // steps since the last state reset before the call
-    int pad;
+    int ring0;            // t_abs_base mod (D + 1): ring slot of absolute step t_abs_base
 };
 
 struct Net {
@@ -131,12 +131,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// L2 policy for data read once (synapse record streams): evicted first, so
+// the streams do not push the tables and ring buffers out of L2
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 // dst, src and bytes multiples of 16
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(l2_evict_first())
         : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {

@@ -69,7 +69,7 @@ __global__ void neuron_kernel(Net n, int i) {
         return;
     }
     const long long t_abs = ck.t_abs_base + i;
-    const int slot = (int)(t_abs % (n.D + 1));
+    const int slot = (ck.ring0 + i) % (n.D + 1);
     long long *ring = n.ring + ((long long)b * (n.D + 1) + slot) * n.n_rec + j;
     const long long acc = *ring;
     *ring = 0;
@@ -80,8 +80,10 @@ __global__ void neuron_kernel(Net n, int i) {
     if (n.n_thr > 0) {
         const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
         const uint32_t u = (uint32_t)(h >> 32);
+        // thresholds are non-decreasing (checked at creation): the count of
+        // thresholds <= u is the index of the first one above u
         int cnt = 0;
-        for (int m = 0; m < n.n_thr; ++m) cnt += (u >= __ldg(n.drive_thr + m));
+        while (cnt < n.n_thr && u >= __ldg(n.drive_thr + cnt)) ++cnt;
         const float dv = n.drive_weight * (float)cnt;
         const float de = fmaf(n.drive_weight, (float)cnt, -dv);
         float e;
@@ -129,31 +131,35 @@ __global__ void neuron_kernel(Net n, int i) {
     }
 }
 
+constexpr int kReadoutChunk = 16;    // spikes per readout block and round
+
 // K3a: readout input sum_j W_out[j][k] z_j^t in exact fixed point; one CTA per
 // (chunk of the step's spike list, sample); thread = readout k.
 __global__ void readout_accum_kernel(Net n, int i, int chunk) {
-    __shared__ int srcs[64];
-    __shared__ int total_s;
+    __shared__ int srcs[kReadoutChunk];
+    __shared__ int incl[kBkt];
     const int b = blockIdx.y;
     if (i > n.lengths[b]) return;
     const int r = run_step(n, i);
     const long long li = list_index(n, b, r % n.RS);
     const int *cnt = n.list_cnt + li;
     const int *ids = n.list_ids + li * n.list_cap;
-    BucketScan bs;
     if (threadIdx.x < 32) {
-        bs = bucket_scan(cnt);
-        if (threadIdx.x == 0) total_s = bs.total;
+        const BucketScan bs = bucket_scan(cnt);
+        incl[threadIdx.x] = bs.incl;
     }
     __syncthreads();
-    const int total = total_s;
+    const int total = incl[kBkt - 1];
     for (int c0 = blockIdx.x * chunk; c0 < total; c0 += gridDim.x * chunk) {
         const int c1 = min(c0 + chunk, total);
-        if (threadIdx.x < 32)
-            for (int c = c0; c < c1; ++c) {
-                const int src = bucket_entry(n, ids, bs, c);
-                if (threadIdx.x == 0) srcs[c - c0] = src;
-            }
+        // every entry of the chunk resolved in parallel: bucket = first
+        // bucket whose inclusive count exceeds the entry's rank
+        for (int t = threadIdx.x; t < c1 - c0; t += blockDim.x) {
+            const int c = c0 + t;
+            int bk = 0;
+            while (incl[bk] <= c) ++bk;
+            srcs[t] = ids[(long long)bk * n.list_cap + (c - (bk > 0 ? incl[bk - 1] : 0))];
+        }
         __syncthreads();
         for (int k = threadIdx.x; k < n.n_out; k += blockDim.x) {
             long long acc = 0;
@@ -302,10 +308,8 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kDStages;
     if (threadIdx.x == 0) ev_block = 0ULL;
-    if (threadIdx.x <= n.D) {                // ring slot of an arrival d steps ahead
-        const long long t_abs0 = abs_step(n, i);
-        ring_off[threadIdx.x] = (long long)((t_abs0 + threadIdx.x) % (n.D + 1)) * n.n_rec;
-    }
+    if (threadIdx.x <= n.D)                  // ring slot of an arrival d steps ahead
+        ring_off[threadIdx.x] = (long long)((n.clock->ring0 + i + (int)threadIdx.x) % (n.D + 1)) * n.n_rec;
     if (lane < kDStages) mbar_init(&bars[warp][lane], 1);
     fence_mbar_init();
     __syncthreads();
@@ -480,7 +484,7 @@ void launch_neuron(const Net &n, int i, cudaStream_t st) {
 }
 
 void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
-    const int chunk = 64;
+    const int chunk = kReadoutChunk;
     int blocks = (n.n_src + chunk - 1) / chunk;
     const int cap = n.B > 1 ? 4 : 2 * sm_count;
     if (blocks > cap) blocks = cap;

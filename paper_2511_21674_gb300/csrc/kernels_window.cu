@@ -64,6 +64,7 @@ __global__ void end_call_kernel(Net n, int T) {
     if (threadIdx.x == 0) {
         n.clock->t_abs_base += T;
         n.clock->r_base += T;
+        n.clock->ring0 = (int)((n.clock->ring0 + (long long)T) % (n.D + 1));
     }
 }
 
@@ -878,32 +879,41 @@ __global__ void __launch_bounds__(256) trace_batched_kernel(Net n) {
 // readout weights: g_kj = sum_b [zk_j^{a0} C_k + sum_{spikes s in window} Ebar_k(s)]
 // (Eq. eprop-output-new-subs-rewritten), one thread per (j, k).
 __global__ void readout_weights_kernel(Net n, int i_end) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per recurrent neuron j, lanes over the readouts k (coalesced
+    // rows of W_out); the neuron's spikes in the window are scanned once per
+    // group of 32 readouts
+    const int lane = threadIdx.x & 31;
+    const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int K = n.n_out, N = n.n_rec, U = n.U;
-    if (idx >= (long long)N * K) return;
-    const int j = (int)(idx / K), k = (int)(idx % K);
+    if (j >= N) return;
     const int r_end = run_step_w(n, i_end);
     const int a0 = r_end - U;
     const int par = (a0 / U) & 1;
     const float *zk_cur = n.zk + (long long)par * n.B * N;
     float *zk_nxt = n.zk + (long long)(par ^ 1) * n.B * N;
     const float kU = exp2f(n.log2_kappa * (float)U);
-    float g = 0.f;
-    for (int b = 0; b < n.B; ++b) {
-        const float z0 = zk_cur[(long long)b * N + j];
-        const float *Eb = n.Ebar_win + (long long)b * U * K + k;
-        float gb = z0 * n.Cwin[b * K + k];
-        float zn = kU * z0;
-        for_each_spike(src_words_c(n, b, n.n_in + j), n.RW, a0 + 1, r_end, [&](int st) {
-            gb += Eb[(long long)(st - a0 - 1) * K];
-            zn += exp2f(n.log2_kappa * (float)(r_end - st));
-        });
-        g += gb;
-        if (k == 0) zk_nxt[(long long)b * N + j] = zn;
-    }
-    if (n.out_mask[j]) {
-        n.w_out[idx] -= n.lr * n.inv_B * g;
-        if (n.record_grad) n.grad_out[idx] += n.inv_B * g;
+    const bool upd = n.out_mask[j] != 0;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        const bool has_k = k < K;
+        float g = 0.f;
+        for (int b = 0; b < n.B; ++b) {
+            const float z0 = zk_cur[(long long)b * N + j];
+            const float *Eb = n.Ebar_win + (long long)b * U * K + k;
+            float gb = has_k ? z0 * n.Cwin[b * K + k] : 0.f;
+            float zn = kU * z0;
+            for_each_spike(src_words_c(n, b, n.n_in + (int)j), n.RW, a0 + 1, r_end, [&](int st) {
+                if (has_k) gb += Eb[(long long)(st - a0 - 1) * K];
+                zn += exp2f(n.log2_kappa * (float)(r_end - st));
+            });
+            g += gb;
+            if (k0 == 0 && lane == 0) zk_nxt[(long long)b * N + j] = zn;
+        }
+        if (upd && has_k) {
+            const long long idx = j * K + k;
+            n.w_out[idx] -= n.lr * n.inv_B * g;
+            if (n.record_grad) n.grad_out[idx] += n.inv_B * g;
+        }
     }
 }
 
@@ -1075,8 +1085,7 @@ void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st) {
 }
 
 void launch_readout_weights(const Net &n, int i_end, cudaStream_t st) {
-    const long long tot = (long long)n.n_rec * n.n_out;
-    readout_weights_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, i_end);
+    readout_weights_kernel<<<(unsigned)(((long long)n.n_rec * 32 + 255) / 256), 256, 0, st>>>(n, i_end);
 }
 
 void launch_rollover(const Net &n, int i_end, cudaStream_t st) {

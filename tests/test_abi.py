@@ -98,6 +98,14 @@ def test_invalid_config_is_rejected_before_any_cuda_call(lib, kw, msg):
     assert msg in err
 
 
+def test_decreasing_drive_table_is_rejected(lib):
+    c = _cfg(drive_weight=0.1, n_drive_thr=3)
+    c.drive_thr[0], c.drive_thr[1], c.drive_thr[2] = 100, 50, 200
+    st, out, err = _create(lib, c)
+    assert st == 1 and not out.value
+    assert "non-decreasing" in err
+
+
 def test_inconsistent_synapse_arrays_rejected(lib):
     st, out, err = _create(lib, _cfg(), n_src=7)
     assert st == 1 and "synapse arrays" in err
