@@ -45,8 +45,9 @@
  * sum: FP32 rounding of a sum is bounded relative to it, not to the sum's
  * possibly cancelled value), and the sensitivity of each gradient to a
  * relative perturbation of the error signal: sum_t Lsens_j^t |ebar^t| with
- * Lsens_j^t = sum_k |B_jk| (|y|_k^t + |y*_k^t|).  They do not feed back into
- * any result.
+ * Lsens_j^t = sum_k |B_jk| Esens_k^t, Esens = |y|_k + |y*_k| for MSE and
+ * pi_k (|y|_k + sum_l pi_l |y|_l) + pi_k + pi*_k for softmax CE.  They do
+ * not feed back into any result.
  *
  * Teacher forcing: `forced` replaces the spikes z; `forced_psi` (optional)
  * replaces the surrogate values psi used by the traces, so that the trace
