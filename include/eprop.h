@@ -215,6 +215,29 @@ eprop_status eprop_readout(eprop_net *net, float *y, float *loss_per_sample,
                            uint8_t *raster, int32_t is_device);
 
 /*
+ * Raster readout without allocation.  The paper has no counterpart: this is
+ * an interface variant of the raster part of eprop_readout for callers that
+ * cannot allocate device memory when they read (eprop_readout allocates a
+ * device scratch buffer on first use; this call unpacks through a fixed
+ * scratch array compiled into the library instead).
+ *   raster [batch][T][n_rec] uint8 spikes of the last simulate call, written
+ *          by the call (host pointer unless is_device); needs record_raster.
+ * Limit: batch * T * n_rec <= EPROP_STATIC_RASTER_BYTES, else EPROP_EINVAL
+ * with a message and nothing written.  The network's device must be the
+ * current device (EPROP_EINVAL otherwise).  No device memory is allocated;
+ * only a rejected call records its message in the network's error string.
+ * The first call on each device resolves the scratch address once (with
+ * lazy module loading this may load the library's device code): make that
+ * first call before any stream capture.  The scratch needs no
+ * initialisation (every byte read back is written first).  It is one
+ * array per device shared by all networks of the process: calls that
+ * overlap in time race on it and must be serialised by the caller.
+ * Returns after the copy has completed.
+ */
+#define EPROP_STATIC_RASTER_BYTES (16 * 1024 * 1024)
+eprop_status eprop_readout_raster_static(eprop_net *net, uint8_t *raster, int32_t is_device);
+
+/*
  * Copies the surrogate derivatives psi_j^t of the last simulate call
  * (Eq. piecewise-linear-surrogate-gradient), [batch][T][n_rec], 0 where the
  * neuron is refractory or the sample has ended.  Needs record_psi = 1.

@@ -65,7 +65,8 @@ class Synapses(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("eprop_create_network", "eprop_set_inputs_targets", "eprop_simulate",
-           "eprop_read_weights_grads", "eprop_readout", "eprop_read_surrogate",
+           "eprop_read_weights_grads", "eprop_readout", "eprop_readout_raster_static",
+           "eprop_read_surrogate",
            "eprop_get_stats", "eprop_sync",
            "eprop_destroy", "eprop_last_error")
 
@@ -88,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.eprop_readout.argtypes = [vp, vp, vp, vp, i32]
     lib.eprop_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.eprop_read_surrogate.argtypes = [vp, vp, i32]
+    lib.eprop_readout_raster_static.argtypes = [vp, vp, i32]
     lib.eprop_sync.argtypes = [vp]
     lib.eprop_destroy.argtypes = [vp]
     lib.eprop_destroy.restype = None
@@ -251,6 +253,14 @@ class Network:
         self._check(self.lib.eprop_readout(self.h, y.ctypes.data, loss.ctypes.data,
                                            None if r is None else r.ctypes.data, 0))
         return (y, loss, r) if raster else (y, loss)
+
+    def raster_static(self):
+        """Raster [batch, T, n_rec] of the last call through the library's
+        fixed device scratch (no device allocation; needs record_raster=1)."""
+        s = self.spec
+        r = np.zeros((s.batch, self.T, s.n_rec), np.uint8)
+        self._check(self.lib.eprop_readout_raster_static(self.h, r.ctypes.data, 0))
+        return r
 
     def surrogate(self):
         """psi [batch, T, n_rec] of the last call (needs record_psi=1)."""

@@ -697,6 +697,55 @@ extern "C" eprop_status eprop_readout(eprop_net *net, float *y, float *loss_per_
     return EPROP_OK;
 }
 
+// ---- raster readout through a fixed device scratch (no allocation)
+//
+// eprop_readout unpacks the recorded raster into a device buffer that it
+// allocates on first use.  Some callers cannot allocate at that point: a
+// monitor reading rasters beside a simulation that holds the device's
+// memory at its limit, or a loop that must not trigger the device-wide
+// synchronisation a first cudaMalloc can cause.  This variant unpacks into
+// a scratch array that is part of the module image (file-scope, 256-byte
+// aligned, EPROP_STATIC_RASTER_BYTES), so it allocates no device memory.
+// Every byte of the unpacked range is written before it is copied out, so
+// nothing in the scratch has to start at zero.  One scratch serves every
+// network of the process on a device: calls that overlap in time (two host
+// threads, or two streams whose copies have not finished) race on it.
+static __device__ __align__(256) unsigned char g_raster_scratch[EPROP_STATIC_RASTER_BYTES];
+
+static constexpr int kMaxScratchDevices = 64;
+static void *g_raster_scratch_addr[kMaxScratchDevices];
+
+extern "C" eprop_status eprop_readout_raster_static(eprop_net *net, uint8_t *raster, int32_t is_device) {
+    if (!net || !raster) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    if (!net->n.record_raster) return fail(net, EPROP_EINVAL, "raster needs record_raster = 1");
+    const long long bytes = (long long)net->cfg.batch * net->T_in * net->cfg.n_rec;
+    if (bytes > (long long)EPROP_STATIC_RASTER_BYTES)
+        return fail(net, EPROP_EINVAL,
+                    "raster (batch * T * n_rec bytes) exceeds EPROP_STATIC_RASTER_BYTES of static scratch");
+    int cur = -1;
+    CK(net, cudaGetDevice(&cur));
+    if (cur != net->dev) return fail(net, EPROP_EINVAL, "the network's device must be the current device");
+    if (cur < 0 || cur >= kMaxScratchDevices) return fail(net, EPROP_EINVAL, "device ordinal out of range");
+    // the scratch address of this device, resolved once with the device
+    // current (the first call may load the module: a one-time setup)
+    if (!g_raster_scratch_addr[cur]) {
+        void *a = nullptr;
+        CK(net, cudaGetSymbolAddress(&a, g_raster_scratch));
+        g_raster_scratch_addr[cur] = a;
+    }
+    unsigned char *scratch = static_cast<unsigned char *>(g_raster_scratch_addr[cur]);
+    Net nn = net->n;
+    nn.T = net->T_in;
+    eprop::launch_unpack_raster(nn, scratch, net->st);
+    CK(net, cudaGetLastError());
+    CK(net, cudaMemcpyAsync(raster, scratch, (size_t)bytes,
+                            is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, net->st));
+    CK(net, cudaStreamSynchronize(net->st));
+    return EPROP_OK;
+}
+
 extern "C" eprop_status eprop_read_surrogate(eprop_net *net, float *psi, int32_t is_device) {
     if (!net || !psi) return EPROP_EINVAL;
     if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
