@@ -172,6 +172,15 @@ def barrier(world):
 # --------------------------------------------------------------- CPU oracle
 
 
+def workload_config(args, nnz, world=1):
+    """The workload one step runs (both arms report it)."""
+    return {"workload": f"million_sparse: {args.n_rec} LIF, in-degree {args.k_in} ({nnz} synapses), "
+                        f"delays 1-5, ~5 Hz, {args.n_out} readouts, update window 100, continuous",
+            "n_rec": args.n_rec, "k_in": args.k_in, "synapses": nnz, "T_per_step": args.T,
+            "trace_storage": args.trace_dtype, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (synapse records ~10 GB per step)"}
+
+
 def cpu_baseline(args, steps=1):
     """The FP64 oracle (test infrastructure, untuned) on a bounded sample of
     the same workload: cpu_sample_n neurons with the same in-degree, delays,
@@ -212,9 +221,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": K, "warmup": args.warmup,
             "ms_per_step": 1000.0 * sec_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "million_sparse (bounded sample on host cores)",
-                       "n_rec": args.cpu_sample_n, "k_in": args.k_in,
-                       "T": args.cpu_sample_T, "n_out": args.n_out},
+            "config": workload_config(args, args.n_rec * args.k_in, args.gpus),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"],
                              "value": res["value"], "unit": UNIT},
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -323,11 +330,7 @@ def _run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_max / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "million_sparse: 1e6 LIF, in-degree 1000 (1e9 synapses), "
-                               "delays 1-5, ~5 Hz, 100 readouts, update window 100, continuous",
-                   "n_rec": args.n_rec, "k_in": args.k_in, "synapses": nnz, "T_per_step": T,
-                   "trace_storage": args.trace_dtype, "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (synapse records ~10 GB per step)"},
+        "config": workload_config(args, nnz, world),
         "sim_time_per_wall_time": (T * spec.dt / 1000.0) / (ms_max / K / 1000.0),
         "events_per_step": events / K,
         "mean_rate_hz": events / K / nnz / (T * spec.dt / 1000.0),

@@ -260,6 +260,31 @@ typedef struct eprop_stats {
 /* Fills *out with the counters of the last simulate call (waits for it). */
 eprop_status eprop_get_stats(eprop_net *net, eprop_stats *out);
 
+/* Autotuner of the launch shapes (form 2: the shapes of a call are picked
+ * by measurement, not by a table).  The paper has no counterpart.  For each
+ * candidate it replays one simulate call of the current inputs (after one
+ * warm-up call that captures the CUDA graph in launch_mode 1), timed with
+ * CUDA events on the network's stream, and restores the complete network
+ * state (a device snapshot of every buffer and the host-side clock) after
+ * each; then it applies the fastest candidate and restores the state once
+ * more, so the network continues exactly as before the call.  Candidates:
+ * blocks_per_sm 1..4 of the row kernels (delivery and synapse trace) and,
+ * before the first simulate call of a batch-1 network that carries state,
+ * trace_kernel 3 (dense window pass) and 1 (lazy).  The snapshot needs as
+ * much device memory as the network holds (EPROP_ENOMEM otherwise).  out
+ * receives the chosen shape and every candidate's time (ms per call). */
+#define EPROP_TUNE_MAX 16
+typedef struct eprop_tune_result {
+    int32_t trace_kernel;
+    int32_t blocks_per_sm;
+    int32_t n_candidates;
+    int32_t cand_trace_kernel[EPROP_TUNE_MAX];
+    int32_t cand_blocks_per_sm[EPROP_TUNE_MAX];
+    double cand_ms[EPROP_TUNE_MAX];
+} eprop_tune_result;
+
+eprop_status eprop_autotune(eprop_net *net, eprop_tune_result *out);
+
 /* Waits for all issued work; returns EPROP_ECUDA / EPROP_ETIMEOUT on a
  * device error or a bounded wait that gave up. */
 eprop_status eprop_sync(eprop_net *net);

@@ -86,7 +86,7 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_simulate.restype = ctypes.c_int
             lib.oracle_simulate.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_State),
-                                            ctypes.c_int32] + [ctypes.c_void_p] * 14
+                                            ctypes.c_int32] + [ctypes.c_void_p] * 15
             lib.oracle_eligibility_step.restype = ctypes.c_double
             lib.oracle_eligibility_step.argtypes = [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3
             lib.oracle_arrival_contrib.restype = None
@@ -240,10 +240,11 @@ class Oracle:
         return st
 
     def simulate(self, T, x_ptr, x_ids, targets, window=None, lengths=None,
-                 forced=None, record=False, forced_psi=None):
+                 forced=None, record=False, forced_psi=None, E_override=None):
         """Run T steps; returns a dict with y [B,T,K], loss [B], raster
         [B,T,N] (uint8), margin [B,T,N] (v - v_th) and, if record, psi and L.
-        forced / forced_psi teacher-force the spikes / the surrogate values."""
+        forced / forced_psi teacher-force the spikes / the surrogate values;
+        E_override [B,T,K] replaces the error signal where window = 0."""
         s = self.spec
         B, N, K = s.batch, s.n_rec, s.n_out
         if s.update_interval and T % s.update_interval:
@@ -256,6 +257,7 @@ class Oracle:
         lens = np.full(B, T, np.int32) if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
         fz = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8).reshape(B, T, N)
         fpsi = None if forced_psi is None else np.ascontiguousarray(forced_psi, dtype=np.float64).reshape(B, T, N)
+        eov = None if E_override is None else np.ascontiguousarray(E_override, dtype=np.float64).reshape(B, T, K)
         out = dict(y=np.zeros((B, T, K)), loss=np.zeros(B),
                    raster=np.zeros((B, T, N), np.uint8), margin=np.zeros((B, T, N)),
                    y_abs=np.zeros((B, T, K)))
@@ -269,7 +271,7 @@ class Oracle:
                                      _p(fz), _p(out["y"]), _p(out["loss"]),
                                      _p(out["raster"]), _p(out["margin"]),
                                      _p(out.get("psi")), _p(out.get("L")), _p(out["y_abs"]),
-                                     _p(fpsi))
+                                     _p(fpsi), _p(eov))
         if rc:
             raise MemoryError("oracle_simulate failed")
         return out

@@ -49,6 +49,9 @@
  * pi_k (|y|_k + sum_l pi_l |y|_l) + pi_k + pi*_k for softmax CE.  They do
  * not feed back into any result.
  *
+ * E_override (optional, [B][T][K]): where window = 0, E^t is taken from it
+ * instead of from the loss (the learned predictor's error estimate).
+ *
  * Teacher forcing: `forced` replaces the spikes z; `forced_psi` (optional)
  * replaces the surrogate values psi used by the traces, so that the trace
  * and gradient arithmetic can be compared in isolation.
@@ -191,7 +194,8 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     const int32_t *lengths, const uint8_t *forced,
                     double *y_rec, double *loss, uint8_t *raster,
                     double *margin, double *psi_rec, double *L_rec,
-                    double *y_abs_rec, const double *forced_psi) {
+                    double *y_abs_rec, const double *forced_psi,
+                    const double *E_override) {
     const int64_t B = c->batch, N = c->n_rec, K = c->n_out, NI = c->n_in;
     const int64_t D1 = c->max_delay + 1, NS = s->n_src, NNZ = s->nnz;
     const int64_t U = c->update_interval > 0 ? c->update_interval : T;
@@ -301,6 +305,15 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 for (int64_t k = 0; k < K; ++k)
                     Esens[k] = win * (pi[k] * (y_abs[k] + pya) + pi[k] + fabs(tgt[k]));
             }
+            /* an external error signal where the target window is closed
+               (the learned predictor's form): it stands in for E there, in
+               the learning signal and the readout gradient; it enters as
+               given, so its sensitivity is its own magnitude */
+            if (E_override && win == 0.0)
+                for (int64_t k = 0; k < K; ++k) {
+                    E[k] = E_override[bt * K + k];
+                    Esens[k] = fabs(E[k]);
+                }
             for (int64_t j = 0; j < N; ++j) {
                 double acc = 0.0, accs = 0.0;
                 for (int64_t k = 0; k < K; ++k) {

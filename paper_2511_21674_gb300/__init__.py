@@ -62,13 +62,25 @@ class Synapses(ctypes.Structure):
                 ("weight", ctypes.c_void_p), ("delay", ctypes.c_void_p)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("trace_kernel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("n_candidates", ctypes.c_int32),
+                ("cand_trace_kernel", ctypes.c_int32 * 16), ("cand_blocks_per_sm", ctypes.c_int32 * 16),
+                ("cand_ms", ctypes.c_double * 16)]
+
+
 _lib = None
 
 EXPORTS = ("eprop_create_network", "eprop_set_inputs_targets", "eprop_simulate",
            "eprop_read_weights_grads", "eprop_readout", "eprop_readout_raster_static",
            "eprop_read_surrogate",
            "eprop_get_stats", "eprop_sync",
-           "eprop_destroy", "eprop_last_error")
+           "eprop_destroy", "eprop_last_error",
+           "eprop_predictor_create", "eprop_predictor_num_params", "eprop_predictor_forward",
+           "eprop_predictor_train_step", "eprop_predictor_read", "eprop_predictor_set_params",
+           "eprop_predictor_sync", "eprop_predictor_destroy", "eprop_predictor_last_error",
+           "eprop_attach_predictor", "eprop_read_predictor_inputs", "eprop_autotune",
+           "eprop_predictor_set_input_scale")
 
 
 def load_library(path: str = LIB_PATH):
@@ -95,9 +107,26 @@ def load_library(path: str = LIB_PATH):
     lib.eprop_destroy.restype = None
     lib.eprop_last_error.argtypes = [vp]
     lib.eprop_last_error.restype = ctypes.c_char_p
+    u64, f32 = ctypes.c_uint64, ctypes.c_float
+    lib.eprop_predictor_create.argtypes = [i32, i32, i32, i32, vp, u64, vp, ctypes.POINTER(vp)]
+    lib.eprop_predictor_num_params.argtypes = [vp]
+    lib.eprop_predictor_forward.argtypes = [vp, vp, i32, vp, i32]
+    lib.eprop_predictor_train_step.argtypes = [vp, vp, vp, i32, f32, vp, i32]
+    lib.eprop_predictor_read.argtypes = [vp, i32, vp, i64]
+    lib.eprop_predictor_set_params.argtypes = [vp, vp]
+    lib.eprop_predictor_sync.argtypes = [vp]
+    lib.eprop_predictor_destroy.argtypes = [vp]
+    lib.eprop_predictor_last_error.argtypes = [vp]
+    lib.eprop_predictor_last_error.restype = ctypes.c_char_p
+    lib.eprop_attach_predictor.argtypes = [vp, vp, i32]
+    lib.eprop_autotune.argtypes = [vp, ctypes.POINTER(TuneResult)]
+    lib.eprop_predictor_set_input_scale.argtypes = [vp, vp]
+    lib.eprop_read_predictor_inputs.argtypes = [vp, vp, i32]
+    void_ret = ("eprop_destroy", "eprop_last_error", "eprop_predictor_destroy", "eprop_predictor_last_error")
     for name in EXPORTS:
-        if name not in ("eprop_destroy", "eprop_last_error"):
+        if name not in void_ret:
             getattr(lib, name).restype = ctypes.c_int
+    lib.eprop_predictor_num_params.restype = i64
     _lib = lib
     return lib
 
@@ -262,6 +291,27 @@ class Network:
         self._check(self.lib.eprop_readout_raster_static(self.h, r.ctypes.data, 0))
         return r
 
+    def autotune(self) -> dict:
+        """Times the candidate launch shapes on the current inputs, keeps the
+        fastest and leaves the network state as it was (eprop_autotune)."""
+        r = TuneResult()
+        self._check(self.lib.eprop_autotune(self.h, ctypes.byref(r)))
+        cands = [(r.cand_trace_kernel[q], r.cand_blocks_per_sm[q], r.cand_ms[q]) for q in range(r.n_candidates)]
+        return dict(trace_kernel=r.trace_kernel, blocks_per_sm=r.blocks_per_sm, candidates=cands)
+
+    def attach_predictor(self, pred, mode: int = 1):
+        """mode 0 detach; bit 0 predicted E outside the target window; bit 1
+        record the predictor inputs of every step."""
+        self._pred = pred if mode else None
+        self._check(self.lib.eprop_attach_predictor(self.h, pred.h if pred is not None else None, mode))
+
+    def predictor_inputs(self):
+        """x [batch, T, n_out + 64] of the last call (attached with bit 1)."""
+        s = self.spec
+        x = np.zeros((s.batch, self.T, s.n_out + 64), np.float32)
+        self._check(self.lib.eprop_read_predictor_inputs(self.h, x.ctypes.data, 0))
+        return x
+
     def surrogate(self):
         """psi [batch, T, n_rec] of the last call (needs record_psi=1)."""
         s = self.spec
@@ -281,6 +331,101 @@ class Network:
     def close(self):
         if getattr(self, "h", None):
             self.lib.eprop_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ predictor
+
+PRED_BUFFERS = dict(params=0, grads=1, A1=2, H1=3, A2=4, H2=5, Y=6, dY=7, dA2=8, dA1=9,
+                    m=10, v=11, X=12)
+
+
+class Predictor:
+    """Learned learning-signal predictor (BF16 MLP on the GPU); see
+    include/eprop_predictor.h.  Arrays are host numpy float32."""
+
+    def __init__(self, n_in: int, n_out: int, hidden: int = 256, max_rows: int = 4096,
+                 params=None, seed: int = 0, stream=None):
+        self.lib = load_library()
+        self.n_in, self.n_out, self.hidden, self.max_rows = n_in, n_out, hidden, max_rows
+        ptr = None
+        if params is not None:
+            params = np.ascontiguousarray(params, np.float32)
+            ptr = params.ctypes.data
+        st = None if stream is None else ctypes.c_void_p(stream)
+        h = ctypes.c_void_p()
+        rc = self.lib.eprop_predictor_create(n_in, hidden, n_out, max_rows, ptr, seed, st, ctypes.byref(h))
+        if rc != 0:
+            raise EpropError(rc, self.lib.eprop_predictor_last_error(None).decode())
+        self.h = h
+        self.n_params = int(self.lib.eprop_predictor_num_params(self.h))
+        self.rows = 0
+
+    def _check(self, rc):
+        if rc != 0:
+            raise EpropError(rc, self.lib.eprop_predictor_last_error(self.h).decode())
+
+    @staticmethod
+    def pack(p: dict) -> np.ndarray:
+        return np.concatenate([np.asarray(p[k], np.float32).ravel()
+                               for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+    def unpack(self, flat) -> dict:
+        dims = [(self.n_in, self.hidden), (self.hidden, self.hidden), (self.hidden, self.n_out)]
+        out, o = {}, 0
+        for i, (a, b) in enumerate(dims, 1):
+            out[f"W{i}"] = np.asarray(flat[o:o + a * b]).reshape(a, b)
+            o += a * b
+            out[f"b{i}"] = np.asarray(flat[o:o + b])
+            o += b
+        return out
+
+    def forward(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.zeros((x.shape[0], self.n_out), np.float32)
+        self._check(self.lib.eprop_predictor_forward(self.h, x.ctypes.data, x.shape[0], y.ctypes.data, 0))
+        self.rows = x.shape[0]
+        return y
+
+    def train_step(self, x, e, lr: float) -> float:
+        x = np.ascontiguousarray(x, np.float32)
+        e = np.ascontiguousarray(e, np.float32)
+        loss = np.zeros(1, np.float32)
+        self._check(self.lib.eprop_predictor_train_step(self.h, x.ctypes.data, e.ctypes.data, x.shape[0],
+                                                        lr, loss.ctypes.data, 0))
+        self.rows = x.shape[0]
+        return float(loss[0])
+
+    def read(self, name: str) -> np.ndarray:
+        which = PRED_BUFFERS[name]
+        R, H, K, I = self.rows, self.hidden, self.n_out, self.n_in
+        size = {0: self.n_params, 1: self.n_params, 10: self.n_params, 11: self.n_params,
+                6: R * K, 7: R * K, 12: R * I}.get(which, R * H)
+        out = np.zeros(size, np.float32)
+        self._check(self.lib.eprop_predictor_read(self.h, which, out.ctypes.data, size))
+        if which in (0, 1, 10, 11):
+            return out
+        cols = {6: K, 7: K, 12: I}.get(which, H)
+        return out.reshape(R, cols)
+
+    def set_input_scale(self, scale):
+        scale = np.ascontiguousarray(scale, np.float32)
+        assert scale.shape == (self.n_in,)
+        self._check(self.lib.eprop_predictor_set_input_scale(self.h, scale.ctypes.data))
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        self._check(self.lib.eprop_predictor_set_params(self.h, flat.ctypes.data))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.eprop_predictor_destroy(self.h)
             self.h = None
 
     def __del__(self):

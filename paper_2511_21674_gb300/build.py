@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libeprop.so")
-SOURCES = ["eprop_api.cu", "kernels_step.cu", "kernels_window.cu"]
+SOURCES = ["eprop_api.cu", "kernels_step.cu", "kernels_window.cu", "predictor.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +37,8 @@ def _flags():
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "eprop.h")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + \
+        [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     newest = max(os.path.getmtime(p) for p in deps)
     if not force and os.path.exists(SO) and os.path.getmtime(SO) >= newest:
         return SO

@@ -10,8 +10,15 @@
 #include "eprop.h"
 #include "eprop_internal.cuh"
 #include "eprop_launch.h"
+#include "eprop_predictor.h"
+#include "predictor_internal.h"
 
 using eprop::Net;
+
+struct DevAlloc {          // one device allocation of the network and its size
+    void *p;
+    size_t bytes;
+};
 
 struct eprop_net {
     eprop_config cfg;
@@ -20,9 +27,9 @@ struct eprop_net {
     int dev = 0, sm_count = 1;
     std::string err;
     int bad = 0;
-    std::vector<void *> fixed_allocs;   // freed at destroy
-    std::vector<void *> win_allocs;     // window-sized buffers
-    std::vector<void *> in_allocs;      // per-T input buffers
+    std::vector<DevAlloc> fixed_allocs;   // freed at destroy
+    std::vector<DevAlloc> win_allocs;     // window-sized buffers
+    std::vector<DevAlloc> in_allocs;      // per-T input buffers
     long long nnz_in = 0;
     int U_alloc = 0, T_alloc = 0, T_in = 0, U_fixed = 0;
     int trace_mode = 0;                 // 0 window work queue, 1 batched, 2 dense window pass
@@ -40,6 +47,8 @@ struct eprop_net {
     long long launches = 0, trace_launches = 0, windows = 0;
     unsigned char *tmp_raster = nullptr;
     long long tmp_raster_bytes = 0;
+    eprop_predictor *pred = nullptr;    // attached learned learning-signal predictor
+    int *pop_cnt_buf = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -67,17 +76,17 @@ static eprop_status cuda_fail(eprop_net *net, cudaError_t e, const char *what) {
         if (_e != cudaSuccess) return cuda_fail((net), _e, #call); \
     } while (0)
 
-static cudaError_t dalloc(std::vector<void *> &owner, void **p, size_t bytes) {
+static cudaError_t dalloc(std::vector<DevAlloc> &owner, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) return e;
-    owner.push_back(*p);
+    owner.push_back(DevAlloc{*p, bytes});
     return cudaMemset(*p, 0, bytes);
 }
 
-static void free_all(std::vector<void *> &v) {
-    for (void *p : v) cudaFree(p);
+static void free_all(std::vector<DevAlloc> &v) {
+    for (const DevAlloc &a : v) cudaFree(a.p);
     v.clear();
 }
 
@@ -163,7 +172,7 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
         while (rc < 256 && std::exp(-(double)rc * U / tau) > 1e-30) rc <<= 1;
         n.RC = rc;
     }
-    std::vector<void *> &o = net->win_allocs;
+    std::vector<DevAlloc> &o = net->win_allocs;
     void *p;
 #define WA(field, type, count)                                                   \
     do {                                                                         \
@@ -179,7 +188,7 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     WA(E_win, float, B * U * K);
     WA(Ebar_win, float, B * U * K);
     WA(qp, float, B * (long long)U * N * net->qp_stride);
-    WA(win_off, long long, U + D + 2);
+    WA(win_off, long long, U + D + 2 + eprop::kWorkCounters);
     if (n.has_state) WA(coef, float, (long long)n.RC * N * (c.neuron_model == 1 ? 8 : 4));
 #undef WA
     net->U_alloc = U;
@@ -252,6 +261,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     n.alpha = (float)alpha; n.kappa = (float)kappa; n.kappa_e = (float)kappa_e;
     n.rho = n.alif ? (float)std::exp(-(double)c.dt / c.tau_a) : 0.f;
     n.alpha_lo = (float)(alpha - (double)n.alpha);
+    n.kappa_e_lo = (float)(kappa_e - (double)n.kappa_e);
     n.rho_lo = n.alif ? (float)(std::exp(-(double)c.dt / c.tau_a) - (double)n.rho) : 0.f;
     n.beta_a = n.alif ? c.beta_a : 0.f;
     n.v_th = c.v_th; n.gamma = c.gamma; n.beta_sg = c.beta_sg; n.lr = c.lr;
@@ -259,7 +269,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     n.log2_alpha = (float)std::log2(alpha); n.log2_kappa = (float)std::log2(kappa);
     n.inv_B = (float)(1.0 / c.batch);
 
-    std::vector<void *> &o = net->fixed_allocs;
+    std::vector<DevAlloc> &o = net->fixed_allocs;
     void *p;
     eprop_status s;
 #define FA(field, type, count)                                                        \
@@ -298,7 +308,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             const uint8_t *dl = syn->delay;
             const float *wt = syn->weight;
             void *t_tg = nullptr, *t_dl = nullptr, *t_w = nullptr;
-            std::vector<void *> tmp;
+            std::vector<DevAlloc> tmp;
             if (!is_device) {
                 if (dalloc(tmp, &t_tg, nnz * 4) != cudaSuccess || dalloc(tmp, &t_dl, nnz) != cudaSuccess ||
                     dalloc(tmp, &t_w, nnz * 4) != cudaSuccess) {
@@ -437,7 +447,7 @@ extern "C" eprop_status eprop_set_inputs_targets(eprop_net *net, const int64_t *
             net->g_T = -1;
         }
         void *p;
-        std::vector<void *> &o = net->in_allocs;
+        std::vector<DevAlloc> &o = net->in_allocs;
 #define IA(field, type, count)                                                     \
         do {                                                                       \
             cudaError_t _e = dalloc(o, &p, (size_t)(count) * sizeof(type));        \
@@ -453,6 +463,7 @@ extern "C" eprop_status eprop_set_inputs_targets(eprop_net *net, const int64_t *
         IA(y_rec, float, B * T * K);
         if (n.record_raster) IA(rec_raster, uint32_t, B * ((T + 31) / 32) * N);
         if (n.record_psi) IA(rec_psi, float, B * T * N);
+        if (net->pred && (n.pred_mode & 2)) IA(pred_rec, float, B * T * n.pred_in);
 #undef IA
         net->x_cap = cap;
     }
@@ -526,6 +537,10 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         }
     }
     if (n.record_raster) cudaMemsetAsync(n.rec_raster, 0, B * ((T + 31) / 32) * N * 4, st);
+    if (n.pred_mode && !c.continuous) {
+        cudaMemsetAsync(n.pop_rate, 0, B * eprop::kPopGroups * 4, st);
+        cudaMemsetAsync(n.pop_cnt, 0, B * eprop::kPopGroups * 4, st);
+    }
     long long L = 0, LT = 0, nwin = 0;
     if (!c.continuous) L += 1;                       // anchor fill
     eprop::launch_begin_call(n, c.continuous, st);
@@ -546,6 +561,15 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         if (c.n_in > 0) { eprop::launch_inject(n, i, (int)net->max_in_per_step, st); L += 1; }
         eprop::launch_neuron(n, i, st);
         eprop::launch_readout(n, i, net->sm_count, st);
+        if (n.pred_mode) {
+            eprop::launch_pred_input(n, i, st);
+            L += 1;
+            if (n.pred_mode & 1) {
+                n.pred_y = predictor_issue_forward(net->pred, n.pred_x, (int)B, st);
+                eprop::launch_pred_apply(n, i, st);
+                L += 5;
+            }
+        }
         eprop::launch_deliver(n, i, grid_rows, st);
         L += 4;
         if (i % U == 0) {
@@ -694,6 +718,215 @@ extern "C" eprop_status eprop_readout(eprop_net *net, float *y, float *loss_per_
         CK(net, cudaMemcpyAsync(raster, net->tmp_raster, bytes, kind, st));
     }
     CK(net, cudaStreamSynchronize(st));
+    return EPROP_OK;
+}
+
+// ---- autotuner of the launch shapes
+
+static void invalidate_graph(eprop_net *net) {
+    if (net->gexec) {
+        cudaGraphExecDestroy(net->gexec);
+        net->gexec = nullptr;
+        net->g_T = -1;
+    }
+}
+
+static long long alloc_bytes(const std::vector<DevAlloc> &v) {
+    long long b = 0;
+    for (const DevAlloc &a : v) b += (long long)a.bytes;
+    return b;
+}
+
+// copies every allocation of v to (dir 0) or from (dir 1) scratch + offset
+static cudaError_t copy_allocs(const std::vector<DevAlloc> &v, unsigned char *scratch, long long &off, int dir,
+                               cudaStream_t st) {
+    for (const DevAlloc &a : v) {
+        cudaError_t e = dir == 0 ? cudaMemcpyAsync(scratch + off, a.p, a.bytes, cudaMemcpyDeviceToDevice, st)
+                                 : cudaMemcpyAsync(a.p, scratch + off, a.bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        off += (long long)a.bytes;
+    }
+    return cudaSuccess;
+}
+
+static bool same_layout(const std::vector<DevAlloc> &a, const std::vector<size_t> &sizes) {
+    if (a.size() != sizes.size()) return false;
+    for (size_t q = 0; q < a.size(); ++q)
+        if (a[q].bytes != sizes[q]) return false;
+    return true;
+}
+
+extern "C" eprop_status eprop_autotune(eprop_net *net, eprop_tune_result *out) {
+    if (!net || !out) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "eprop_set_inputs_targets must come first");
+    eprop_config &c = net->cfg;
+    const int T = net->T_in;
+    const int U = c.update_interval > 0 ? c.update_interval : T;
+    const bool pristine = net->t_abs == 0;
+    const int tk0 = c.trace_kernel, bps0 = c.blocks_per_sm;
+    // candidates: the trace form (only before the first call, while the
+    // carried state is still zero) and the CTAs per SM of the row kernels
+    std::vector<int> tks;
+    if (pristine && c.batch == 1 && net->n.has_state) tks = {3, 1};
+    else tks = {tk0};
+    const int bps_list[4] = {1, 2, 3, 4};
+    std::memset(out, 0, sizeof(*out));
+    CK(net, cudaStreamSynchronize(net->st));
+    // snapshot of every device allocation and of the host-side clock
+    const long long bytes = alloc_bytes(net->fixed_allocs) + alloc_bytes(net->win_allocs) +
+                            alloc_bytes(net->in_allocs);
+    void *sp = nullptr;
+    cudaError_t e = cudaMalloc(&sp, (size_t)bytes);
+    if (e != cudaSuccess) return cuda_fail(net, e, "autotune snapshot");
+    unsigned char *scratch = static_cast<unsigned char *>(sp);
+    std::vector<size_t> win_sizes;
+    for (const DevAlloc &a : net->win_allocs) win_sizes.push_back(a.bytes);
+    const long long h_t_abs = net->t_abs;
+    const int h_r_base = net->r_base, h_U_fixed = net->U_fixed;
+    long long off = 0;
+    e = copy_allocs(net->fixed_allocs, scratch, off, 0, net->st);
+    if (e == cudaSuccess) e = copy_allocs(net->in_allocs, scratch, off, 0, net->st);
+    const long long win_off0 = off;
+    if (e == cudaSuccess) e = copy_allocs(net->win_allocs, scratch, off, 0, net->st);
+    auto restore = [&]() -> cudaError_t {
+        long long o = 0;
+        cudaError_t r = copy_allocs(net->fixed_allocs, scratch, o, 1, net->st);
+        if (r == cudaSuccess) r = copy_allocs(net->in_allocs, scratch, o, 1, net->st);
+        if (r == cudaSuccess && same_layout(net->win_allocs, win_sizes)) {
+            o = win_off0;
+            r = copy_allocs(net->win_allocs, scratch, o, 1, net->st);
+        }
+        net->t_abs = h_t_abs;
+        net->r_base = h_r_base;
+        net->U_fixed = h_U_fixed;
+        return r == cudaSuccess ? cudaStreamSynchronize(net->st) : r;
+    };
+    auto set_shape = [&](int tk, int bps) -> eprop_status {
+        c.blocks_per_sm = bps;
+        if (tk != c.trace_kernel) {
+            c.trace_kernel = tk;
+            net->U_alloc = 0;                  // the trace form decides the window layout
+            eprop_status st = alloc_window(net, U, T);
+            if (st != EPROP_OK) return st;
+        }
+        invalidate_graph(net);
+        return EPROP_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    eprop_status status = e == cudaSuccess ? EPROP_OK : cuda_fail(net, e, "autotune setup");
+    double best = 1e300;
+    int best_tk = tk0, best_bps = bps0;
+    for (size_t a = 0; a < tks.size() && status == EPROP_OK; ++a) {
+        for (int q = 0; q < 4 && status == EPROP_OK; ++q) {
+            const int tk = tks[a], bps = bps_list[q];
+            status = set_shape(tk, bps);
+            if (status != EPROP_OK) break;
+            status = eprop_simulate(net, T, nullptr);      // warm-up (graph capture)
+            if (status != EPROP_OK) break;
+            if ((e = restore()) != cudaSuccess) { status = cuda_fail(net, e, "autotune restore"); break; }
+            cudaEventRecord(e0, net->st);
+            status = eprop_simulate(net, T, nullptr);
+            if (status != EPROP_OK) break;
+            cudaEventRecord(e1, net->st);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { status = cuda_fail(net, e, "autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const int k = out->n_candidates;
+            if (k < EPROP_TUNE_MAX) {
+                out->cand_trace_kernel[k] = tk;
+                out->cand_blocks_per_sm[k] = bps;
+                out->cand_ms[k] = ms;
+                out->n_candidates = k + 1;
+            }
+            if (ms < best) {
+                best = ms;
+                best_tk = tk;
+                best_bps = bps;
+            }
+            if ((e = restore()) != cudaSuccess) { status = cuda_fail(net, e, "autotune restore"); break; }
+        }
+    }
+    if (status == EPROP_OK) status = set_shape(best_tk, best_bps);
+    if (status == EPROP_OK && (e = restore()) != cudaSuccess) status = cuda_fail(net, e, "autotune restore");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sp);
+    out->trace_kernel = c.trace_kernel;
+    out->blocks_per_sm = c.blocks_per_sm;
+    return status;
+}
+
+// ---- learned learning-signal predictor
+
+extern "C" eprop_status eprop_attach_predictor(eprop_net *net, eprop_predictor *pred, int32_t mode) {
+    if (!net) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    Net &n = net->n;
+    const eprop_config &c = net->cfg;
+    if (mode < 0 || mode > 3) return fail(net, EPROP_EINVAL, "mode must be 0..3");
+    if (mode != 0 && !pred) return fail(net, EPROP_EINVAL, "a predictor is required");
+    CK(net, cudaStreamSynchronize(net->st));
+    if (net->gexec) {                       // the captured call changes
+        cudaGraphExecDestroy(net->gexec);
+        net->gexec = nullptr;
+        net->g_T = -1;
+    }
+    if (mode == 0) {
+        net->pred = nullptr;
+        n.pred_mode = 0;
+        n.pop_cnt = nullptr;
+        return EPROP_OK;
+    }
+    int pin = 0, pout = 0, prows = 0;
+    predictor_dims(pred, &pin, &pout, &prows);
+    if (pout != c.n_out || pin != c.n_out + eprop::kPopGroups)
+        return fail(net, EPROP_EINVAL, "predictor must map n_out + 64 inputs to n_out outputs");
+    if (prows < c.batch) return fail(net, EPROP_EINVAL, "predictor max_rows must be >= batch");
+    const long long B = c.batch, G = eprop::kPopGroups;
+    void *p;
+    std::vector<DevAlloc> &o = net->fixed_allocs;
+    if (!n.pop_rate) {
+        if (dalloc(o, &p, B * G * 4) != cudaSuccess) return fail(net, EPROP_ENOMEM, "predictor buffers");
+        n.pop_rate = (float *)p;
+        if (dalloc(o, &p, B * G * 4) != cudaSuccess) return fail(net, EPROP_ENOMEM, "predictor buffers");
+        net->pop_cnt_buf = (int *)p;
+        if (dalloc(o, &p, B * pin * 4) != cudaSuccess) return fail(net, EPROP_ENOMEM, "predictor buffers");
+        n.pred_x = (float *)p;
+        std::vector<float> inv(G, 0.f);
+        for (int g = 0; g < G; ++g) {
+            const int size = c.n_rec > g ? (c.n_rec - g + (int)G - 1) / (int)G : 0;
+            inv[g] = size > 0 ? 1.0f / (float)size : 0.f;
+        }
+        if (dalloc(o, &p, G * 4) != cudaSuccess) return fail(net, EPROP_ENOMEM, "predictor buffers");
+        CK(net, cudaMemcpy(p, inv.data(), G * 4, cudaMemcpyHostToDevice));
+        n.pop_inv = (const float *)p;
+    }
+    n.pop_cnt = net->pop_cnt_buf;
+    n.pred_in = pin;
+    n.pop_beta = (float)std::exp(-(double)c.dt / 20.0);
+    net->pred = pred;
+    n.pred_mode = mode;
+    if ((mode & 2) && net->have_inputs) {
+        if (dalloc(net->in_allocs, &p, B * (long long)net->T_in * pin * 4) != cudaSuccess)
+            return fail(net, EPROP_ENOMEM, "predictor record buffer");
+        n.pred_rec = (float *)p;
+    }
+    return EPROP_OK;
+}
+
+extern "C" eprop_status eprop_read_predictor_inputs(eprop_net *net, float *x, int32_t is_device) {
+    if (!net || !x) return EPROP_EINVAL;
+    if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
+    if (!(net->n.pred_mode & 2) || !net->n.pred_rec)
+        return fail(net, EPROP_EINVAL, "recording needs a predictor attached with mode bit 1");
+    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    const long long cnt = (long long)net->cfg.batch * net->T_in * net->n.pred_in;
+    CK(net, cudaMemcpyAsync(x, net->n.pred_rec, cnt * 4,
+                            is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, net->st));
+    CK(net, cudaStreamSynchronize(net->st));
     return EPROP_OK;
 }
 

@@ -59,6 +59,7 @@ struct Net {
     // constants (float, computed on the host in double)
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
     float alpha_lo, rho_lo;   // alpha - (float)alpha, rho - (float)rho
+    float kappa_e_lo;         // kappa_e - (float)kappa_e (the FP64 adjoint sweep uses both)
     float log2_alpha, log2_kappa, alphaU, kappaeU, inv_B;
     unsigned long long drive_seed;
     const uint32_t *drive_thr;
@@ -93,7 +94,8 @@ struct Net {
     // window tables
     float *qp;
     float *coef;
-    long long *win_off;       // [U + D + 1] work-item offsets of the window
+    long long *win_off;       // [U + D + 2] work-item offsets of the window, then
+                              // kWorkCounters work counters of the row kernels
     // inputs of the current call
     const long long *x_ptr;
     const int *x_ids;
@@ -103,6 +105,16 @@ struct Net {
     const uint8_t *forced;
     uint32_t *rec_raster;     // [B][T/32+1][N] bits (record_raster)
     float *rec_psi;           // [B][T][N] (record_psi)
+    // learned learning-signal predictor (attached with eprop_attach_predictor)
+    int pred_mode;            // 0 none; bit 0 predict E outside the target window; bit 1 record inputs
+    int pred_in;              // n_out + kPopGroups inputs per row
+    float pop_beta;           // exp(-dt / 20 ms)
+    int *pop_cnt;             // [B][kPopGroups] spikes of the step per group
+    float *pop_rate;          // [B][kPopGroups] filtered group rates
+    const float *pop_inv;     // [kPopGroups] 1 / group size
+    float *pred_x;            // [B][pred_in] inputs of the current step
+    float *pred_rec;          // [B][T][pred_in] recorded inputs (bit 1)
+    const float *pred_y;      // [B][n_out] predictor outputs of the current step
     unsigned long long *events;
     unsigned int *err_flags;  // bit 0: catch-up ring overflow
     Clock *clock;
@@ -180,6 +192,8 @@ struct StageDesc {
 };
 
 constexpr int kBkt = 32;           // spike-list buckets per step
+constexpr int kPopGroups = 64;     // population-rate groups of the predictor inputs (j mod 64)
+constexpr int kWorkCounters = 2;   // row-kernel work counters kept after the window offsets
 
 __device__ __forceinline__ long long list_index(const Net &n, int b, int slot) {
     return (long long)(b * n.RS + slot) * kBkt;

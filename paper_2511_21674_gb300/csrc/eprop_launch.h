@@ -20,6 +20,8 @@ int launch_tables(const Net &n, int i_end, cudaStream_t st);
 void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st);
 void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st);
 void launch_window_pass(const Net &n, int i_end, int grid_x, cudaStream_t st);
+void launch_pred_input(const Net &n, int i, cudaStream_t st);
+void launch_pred_apply(const Net &n, int i, cudaStream_t st);
 void launch_readout_weights(const Net &n, int i_end, cudaStream_t st);
 void launch_rollover(const Net &n, int i_end, cudaStream_t st);
 void launch_flush(const Net &n, int i_end, float *w_dst, float *g_dst, long long q_begin, long long q_end,

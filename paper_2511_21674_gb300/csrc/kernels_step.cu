@@ -123,6 +123,7 @@ __global__ void neuron_kernel(Net n, int i) {
     n.z_prev[nb] = (uint8_t)z;
     if (z) {
         mark_spike(n, b, n.n_in + j, r);
+        if (n.pop_cnt) atomicAdd(&n.pop_cnt[b * kPopGroups + (j & (kPopGroups - 1))], 1);
         if (n.record_raster) {
             const int W32 = (n.T + 31) / 32;
             atomicOr(&n.rec_raster[((long long)b * W32 + ((i - 1) >> 5)) * n.n_rec + j],
@@ -245,6 +246,43 @@ __global__ void readout_error_kernel(Net n, int i) {
     }
     const float tot = block_sum(l, sh);
     if (threadIdx.x == 0) n.loss_acc[b] += tot;
+}
+
+// Predictor inputs of step i (one block per sample): the readout
+// potentials y^t and the group rates r_g = beta r_g + (1 - beta) * (spikes of
+// group g at this step) / |group| (Eq. ema-rate on group means), given in
+// spikes per 1000 steps (the paper's rate unit).
+__global__ void pred_input_kernel(Net n, int i) {
+    const int b = blockIdx.x;
+    const int K = n.n_out;
+    const bool live = i <= n.lengths[b];
+    float *x = n.pred_x + (long long)b * n.pred_in;
+    for (int g = threadIdx.x; g < kPopGroups; g += blockDim.x) {
+        const long long o = (long long)b * kPopGroups + g;
+        const int c = n.pop_cnt[o];
+        n.pop_cnt[o] = 0;
+        const float rr = n.pop_beta * n.pop_rate[o] + (1.0f - n.pop_beta) * ((float)c * n.pop_inv[g]);
+        n.pop_rate[o] = rr;
+        x[K + g] = 1000.0f * rr;         // spikes per 1000 steps
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) x[k] = live ? n.y[(long long)b * K + k] : 0.0f;
+    __syncthreads();
+    if (n.pred_mode & 2) {
+        float *rec = n.pred_rec + ((long long)b * n.T + (i - 1)) * n.pred_in;
+        for (int q = threadIdx.x; q < n.pred_in; q += blockDim.x) rec[q] = x[q];
+    }
+}
+
+// Where the sample's target window is closed, the predicted error signal
+// stands in for E^t (learning signal and readout gradient of the window).
+__global__ void pred_apply_kernel(Net n, int i) {
+    const int b = blockIdx.x;
+    const int k = threadIdx.x;
+    if (k >= n.n_out || i > n.lengths[b]) return;
+    if (n.window && n.window[(long long)b * n.T + (i - 1)]) return;
+    const int r = run_step(n, i);
+    const int a0 = win_start(n, r);
+    n.E_win[((long long)b * n.U + (r - a0 - 1)) * n.n_out + k] = n.pred_y[(long long)b * n.n_out + k];
 }
 
 // Issues the bulk copies of one chunk (cnt records from q0) into a stage
@@ -494,6 +532,12 @@ void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
     readout_accum_kernel<<<dim3(blocks, n.B), th, 0, st>>>(n, i, chunk);
     int th2 = ((n.n_out + 31) / 32) * 32;
     readout_error_kernel<<<n.B, th2, 0, st>>>(n, i);
+}
+
+void launch_pred_input(const Net &n, int i, cudaStream_t st) { pred_input_kernel<<<n.B, 128, 0, st>>>(n, i); }
+
+void launch_pred_apply(const Net &n, int i, cudaStream_t st) {
+    pred_apply_kernel<<<n.B, ((n.n_out + 31) / 32) * 32, 0, st>>>(n, i);
 }
 
 void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st) {

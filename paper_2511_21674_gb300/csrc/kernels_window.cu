@@ -115,7 +115,9 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     const R alpha = (R)n.alpha + (R)n.alpha_lo;
     const R rho = ALIF ? (R)n.rho + (R)n.rho_lo : (R)0;
     const R beta = n.beta_a;
-    const R ke = n.kappa_e;
+    // kappa_e^m over a window of hundreds of steps: in the FP64 sweep the
+    // filter constant keeps its FP64 value (hi + lo), as alpha and rho do
+    const R ke = ALIF ? (R)n.kappa_e + (R)n.kappa_e_lo : (R)n.kappa_e;
     // adjoint of G (mz, ma, me); of ebar^b (ez, ea, ee); of eps_a^b (az, aa, ae)
     R mz = 0, ma = 0, me = 0;
     R ez = 0, ea = 0, ee = 1;
@@ -270,6 +272,8 @@ __global__ void window_offsets_kernel(Net n, int i_end) {
         acc += v;
     }
     if (lane == 0) n.win_off[nsteps > 0 ? nsteps : 0] = acc;
+    // the row kernels' work counters (after the U + D + 2 offsets)
+    if (lane < kWorkCounters) n.win_off[n.U + n.D + 2 + lane] = 0;
 }
 
 __device__ __forceinline__ bool any_spike(const uint32_t *words, int RW, int lo, int hi) {
@@ -410,15 +414,25 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
     const int kW = a0 / U;
     const float step = n.lr * n.inv_B;
     const long long qa = (long long)(-a0 - 1) * N;     // table index = qa + a * N + j
-    // producer cursor (warp-uniform): work item, current row and its range
-    long long pit = gw;
+    // producer cursor (warp-uniform): work item, current row and its range;
+    // items are handed out in order by a counter, so the warps in flight
+    // stay within about one emission step (their table slabs stay in L2)
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(n.win_off + n.U + n.D + 2);
+    long long pit = 0;
     long long pq = 0, pre = 0;
     int psrc = -1, ps = 0, pns = 0;
     RowInfo rinfo;
     unsigned vmask = 0;
+    (void)gw;
+    (void)nw;
     // advances the producer to the next chunk; false when the window is done
     auto next_row = [&]() -> bool {
         while (pq >= pre) {
+            {
+                long long v = 0;
+                if (lane == 0) v = (long long)atomicAdd(ctr, 1ULL);
+                pit = __shfl_sync(0xffffffffu, v, 0);
+            }
             if (pit >= total) return false;
             int lo = 0, hi = nsteps;
             while (hi - lo > 1) {
@@ -429,7 +443,6 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
             const long long li = list_index(n, 0, s % n.RS);
             const BucketScan bs = bucket_scan(n.list_cnt + li);
             const int src = bucket_entry(n, n.list_ids + li * n.list_cap, bs, (int)(pit - off[lo]));
-            pit += nw;
             const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
             if (re <= rb) continue;
             const uint32_t *words = src_words_c(n, 0, src);
@@ -627,7 +640,7 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
 // streams of the next chunks into shared memory while the current chunk is
 // advanced; what stays on the critical path are the targets' window
 // coefficients (L2-resident) and, in the active pass, the table entries.
-template <bool ALIF, bool ACTIVE>
+template <bool ALIF, bool ACTIVE, bool TB>
 __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ uint64_t bars[8][kTStages];
@@ -655,14 +668,24 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     const float step = n.lr * n.inv_B;
     const long long qa = (long long)(-a0 - 1) * N;     // table index = qa + a * N + j
-    // producer cursor (warp-uniform): work item, current row and its range
-    long long pit = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    // producer cursor (warp-uniform): work item, current row and its range;
+    // items are handed out in order by a counter, so the warps in flight
+    // stay within about one emission step (their table slabs stay in L2)
+    unsigned long long *ctr =
+        reinterpret_cast<unsigned long long *>(n.win_off + n.U + n.D + 2) + (ACTIVE ? 0 : 1);
+    long long pit = 0;
     long long pq = 0, pre = 0;
     int psrc = -1, ps = s_lo, pns = 0;
     float pzb = 0.f;            // lane d: zbar at a0 of the row's delay-d synapses
     unsigned vmask = 0;
+    (void)nw;
     auto next_row = [&]() -> bool {
         while (pq >= pre) {
+            {
+                long long v = 0;
+                if (lane == 0) v = (long long)atomicAdd(ctr, 1ULL);
+                pit = __shfl_sync(0xffffffffu, v, 0);
+            }
             if (pit >= total) return false;
             int src, s = s_lo;
             if (ACTIVE) {
@@ -678,7 +701,6 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
             } else {
                 src = (int)pit;
             }
-            pit += nw;
             const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
             if (re <= rb) continue;
             const uint32_t *words = src_words_c(n, 0, src);
@@ -753,6 +775,11 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
         const int ns = ACTIVE ? nspk[warp][k] : 0;
         const bool listed = ns <= kSpikeCap;
         const int *sp = spk[warp][ACTIVE ? k : 0];
+        const float *zrow = zbs[warp][k];
+        // chunk-relative addressing: shared offsets and global bases of the chunk
+        const int o4 = (int)(d.q0 - d.q_al), o2 = (int)(d.q0 - d.q_al2);
+        float *wq = n.w + d.q0;
+        float *gq = n.grad + d.q0;
         constexpr int kB = ALIF ? 4 : 8;       // synapses per lane in flight
 #pragma unroll 1
         for (int h = 0; h < kChunk / 32; h += kB) {
@@ -763,21 +790,22 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
                 const int idx = lane + 32 * (h + u);
-                const long long q = d.q0 + idx;
                 const bool in = idx < d.n;
-                td[u] = in ? sb.td[q - d.q_al] : 0u;
-                zr[u] = zbs[warp][k][td[u] >> 24];
-                wv[u] = in ? sb.w[q - d.q_al] : 0.f;
-                eb[u] = in ? stage_trace_w(n, sb, d, q) : 0.f;
-                ep[u] = (ALIF && in) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+                td[u] = in ? sb.td[o4 + idx] : 0u;
+                zr[u] = zrow[td[u] >> 24];
+                wv[u] = in ? sb.w[o4 + idx] : 0.f;
+                if (TB) eb[u] = in ? __bfloat162float(__ushort_as_bfloat16(
+                                         reinterpret_cast<const uint16_t *>(sb.tr)[o2 + idx])) : 0.f;
+                else eb[u] = in ? reinterpret_cast<const float *>(sb.tr)[o4 + idx] : 0.f;
+                ep[u] = (ALIF && in) ? load_trace(n.epsa, d.q0 + idx, TB) : 0.f;
                 live[u] = in && (ACTIVE || zr[u] != 0.f || eb[u] != 0.f || ep[u] != 0.f);
                 if (live[u]) cf[u] = load_coef<ALIF>(n, td[u] & 0xFFFFFFu, 0);
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
                 if (!live[u]) continue;
-                const long long q = d.q0 + lane + 32 * (h + u);
-                const long long j = td[u] & 0xFFFFFFu;
+                const int idx = lane + 32 * (h + u);
+                const int j = (int)(td[u] & 0xFFFFFFu);
                 const int dl = (int)(td[u] >> 24);
                 float G = 0.f, zbar = zr[u], ebar = eb[u], epsa = ep[u];
                 apply_coef<ALIF>(n, cf[u], zbar, epsa, ebar, G);
@@ -787,11 +815,12 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                             const int a = sp[cc] + dl;
                             if (a <= a0) continue;
                             if (a > r_end) break;
+                            const long long qi = qa + (long long)a * N + j;
                             if (ALIF) {
-                                const float4 t = __ldg(reinterpret_cast<const float4 *>(n.qp) + qa + (long long)a * N + j);
+                                const float4 t = __ldg(reinterpret_cast<const float4 *>(n.qp) + qi);
                                 G += t.x; ebar += t.y; epsa += t.z;
                             } else {
-                                const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qa + (long long)a * N + j);
+                                const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qi);
                                 G += t.x; ebar += t.y;
                             }
                         }
@@ -800,10 +829,12 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                                                  r_end - dl, dl, qa + j, ebar, epsa);
                     }
                 }
-                if (G != 0.f) __stcs(n.w + q, wv[u] - step * G);
-                store_trace(n.ebar, q, ebar, n.trace_bf16);
-                if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
-                if (n.record_grad) n.grad[q] += n.inv_B * G;
+                if (G != 0.f) __stcs(wq + idx, wv[u] - step * G);
+                if (TB) __stcs(reinterpret_cast<uint16_t *>(n.ebar) + d.q0 + idx,
+                               __bfloat16_as_ushort(__float2bfloat16_rn(ebar)));
+                else __stcs(reinterpret_cast<float *>(n.ebar) + d.q0 + idx, ebar);
+                if (ALIF) store_trace(n.epsa, d.q0 + idx, epsa, TB);
+                if (n.record_grad) gq[idx] += n.inv_B * G;
             }
         }
         __syncwarp();
@@ -1022,10 +1053,13 @@ __global__ void unpack_raster_kernel(Net n, unsigned char *dst) {
 
 void prepare_kernel_attributes() {
     const int tl = 200 * 1024;
-    cudaFuncSetAttribute(window_pass_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
-    cudaFuncSetAttribute(window_pass_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
-    cudaFuncSetAttribute(window_pass_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
-    cudaFuncSetAttribute(window_pass_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
+#define EPROP_PASS_ATTR(A, P, T) \
+    cudaFuncSetAttribute(window_pass_kernel<A, P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl)
+    EPROP_PASS_ATTR(true, true, true); EPROP_PASS_ATTR(true, true, false);
+    EPROP_PASS_ATTR(true, false, true); EPROP_PASS_ATTR(true, false, false);
+    EPROP_PASS_ATTR(false, true, true); EPROP_PASS_ATTR(false, true, false);
+    EPROP_PASS_ATTR(false, false, true); EPROP_PASS_ATTR(false, false, false);
+#undef EPROP_PASS_ATTR
     cudaFuncSetAttribute(trace_window_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
@@ -1068,13 +1102,17 @@ void launch_window_pass(const Net &n, int i_end, int grid_x, cudaStream_t st) {
     window_offsets_kernel<<<1, 32, 0, st>>>(n, i_end);
     const size_t sb = sizeof(StageBuf) * 8 * kTStages;
     const size_t sm = sb + (size_t)(n.U + n.D + 2) * sizeof(long long);
+#define EPROP_PASS(A, T)                                                  \
+    do {                                                                  \
+        window_pass_kernel<A, true, T><<<grid_x, 256, sm, st>>>(n, i_end);  \
+        window_pass_kernel<A, false, T><<<grid_x, 256, sb, st>>>(n, i_end); \
+    } while (0)
     if (n.alif) {
-        window_pass_kernel<true, true><<<grid_x, 256, sm, st>>>(n, i_end);
-        window_pass_kernel<true, false><<<grid_x, 256, sb, st>>>(n, i_end);
+        if (n.trace_bf16) EPROP_PASS(true, true); else EPROP_PASS(true, false);
     } else {
-        window_pass_kernel<false, true><<<grid_x, 256, sm, st>>>(n, i_end);
-        window_pass_kernel<false, false><<<grid_x, 256, sb, st>>>(n, i_end);
+        if (n.trace_bf16) EPROP_PASS(false, true); else EPROP_PASS(false, false);
     }
+#undef EPROP_PASS
 }
 
 void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st) {

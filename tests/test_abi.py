@@ -115,3 +115,9 @@ def test_null_network_calls(lib):
     assert lib.eprop_simulate(None, 10, None) == 1
     assert lib.eprop_sync(None) == 1
     lib.eprop_destroy(None)
+
+
+def test_autotune_needs_a_network(lib):
+    import paper_2511_21674_gb300 as ep
+    r = ep.TuneResult()
+    assert lib.eprop_autotune(None, ctypes.byref(r)) == 1

@@ -411,6 +411,35 @@ def test_arrival_contributions_sum_to_the_gradient(model):
     assert np.all(mag >= np.abs(g) * (1 - 1e-12))
 
 
+@pytest.mark.parametrize("model", [0, 1])
+def test_error_override_with_the_true_signal_is_the_full_window_run(model):
+    # the override replaces E only where the window is closed: feeding it the
+    # error signal of a run with the window open everywhere, and closing the
+    # window, must reproduce that run's gradients and readout gradients
+    net, x, tg, window, lengths = _random_small(model, 1, seed=60 + model)
+    s = net["spec"]
+    x_ptr, x_ids = raster_to_lists(x)
+    args = (net["ptr"], net["col"], net["w"], net["delay"], net["w_out"], net["out_mask"])
+    o1 = oracle.Oracle(s, *args)
+    ones = np.ones_like(window)
+    r1 = o1.simulate(s.T, x_ptr, x_ids, tg, ones, lengths)
+    g1, go1 = o1.take_grads()
+    y = r1["y"]
+    E = np.exp(y - y.max(axis=2, keepdims=True))
+    E = E / E.sum(axis=2, keepdims=True) - tg
+    o2 = oracle.Oracle(s, *args)
+    o2.simulate(s.T, x_ptr, x_ids, tg, np.zeros_like(window), lengths, E_override=E)
+    g2, go2 = o2.take_grads()
+    assert np.abs(g1).max() > 0
+    np.testing.assert_allclose(g2, g1, rtol=1e-12, atol=1e-13 * np.abs(g1).max())
+    np.testing.assert_allclose(go2, go1, rtol=1e-12, atol=1e-13 * np.abs(go1).max())
+    # with the window open the override is ignored
+    o3 = oracle.Oracle(s, *args)
+    o3.simulate(s.T, x_ptr, x_ids, tg, ones, lengths, E_override=np.full_like(E, 7.0))
+    g3, _ = o3.take_grads()
+    np.testing.assert_array_equal(g3, g1)
+
+
 def test_index_flip_future_facing_form():
     # Eq. summation-future: sum_{t'} dL/dz^{t'} e^{t'}, with dL/dz^{t'} =
     # sum_k B_jk sum_{t >= t'} kappa^{t - t'} E_k^t, equals the oracle's causal

@@ -1,0 +1,181 @@
+"""The learned learning-signal predictor inside e-prop (GPU only).
+
+* its per-step inputs (readout potentials, group rates) against their
+  definition on the recorded readout and raster;
+* e-prop driven by the predicted error signal against the FP64 oracle fed
+  the same predictions (teacher-forced spikes and surrogate values);
+* the gain: a predictor trained on the network's own (state, error) pairs
+  brings the gradient of a sample whose target arrives only in its last 25
+  steps closer to the gradient with the target known at every step than
+  plain e-prop (which has no learning signal before the window).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import predictor as P
+from tests import parity as PT
+from workloads import configs as C
+
+pytestmark = pytest.mark.gpu
+
+
+def _net(W, **kw):
+    import paper_2511_21674_gb300 as ep
+    kw.setdefault("launch_mode", 0)
+    return ep.Network(W["spec"], W["ptr"], W["col"], W["w"], W["delay"], W["w_out"],
+                      W["out_mask"], W["feedback"], **kw)
+
+
+def _small(batch=4, sample_seed=None):
+    return C.event_classification(batch=batch, T=120, len_lo=80, len_hi=120, n_rec=60, side=8,
+                                  events_per_300=2000.0, sample_seed=sample_seed)
+
+
+def test_predictor_inputs_follow_their_definition():
+    import paper_2511_21674_gb300 as ep
+    W = _small()
+    s = W["spec"]
+    net = _net(W, record_raster=1)
+    pred = ep.Predictor(s.n_out + 64, s.n_out, seed=1, max_rows=64)
+    net.attach_predictor(pred, mode=2)
+    for _ in range(2):                        # the record buffer survives repeated calls
+        net.set_inputs(W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"], s.T)
+        net.simulate(s.T)
+    y, _, raster = net.readout(raster=True)
+    x = net.predictor_inputs()
+    assert raster.sum() > 0
+    np.testing.assert_array_equal(x[..., :s.n_out], y)
+    r = 1000.0 * P.population_rates(raster, math.exp(-s.dt / 20.0))   # spikes per 1000 steps
+    np.testing.assert_allclose(x[..., s.n_out:], r, rtol=5e-6, atol=1e-9)   # FP32 filter
+    net.close()
+    pred.close()
+
+
+def test_eprop_with_predicted_error_matches_oracle():
+    # the predictor's outputs stand in for E where the target window is
+    # closed; the oracle takes the same outputs as its error signal there
+    import paper_2511_21674_gb300 as ep
+    W = _small()
+    s = W["spec"]
+    B, T, K = s.batch, s.T, s.n_out
+    net = _net(W, record_raster=1, record_psi=1, record_grad=1)
+    pred = ep.Predictor(K + 64, K, seed=3, max_rows=B * T)
+    net.attach_predictor(pred, mode=3)
+    net.set_inputs(W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"], T)
+    net.simulate(T)
+    _, _, raster = net.readout(raster=True)
+    psi = net.surrogate()
+    x = net.predictor_inputs()
+    E_hat = pred.forward(x.reshape(B * T, K + 64)).reshape(B, T, K)
+    nnz_in = int(W["ptr"][s.n_in])
+    _, g_in = net.weights(ep.PROJ_IN, with_grad=True)
+    _, g_rec = net.weights(ep.PROJ_REC, with_grad=True)
+    _, g_out = net.weights(ep.PROJ_OUT, with_grad=True)
+    net.close()
+    pred.close()
+    o = oracle.Oracle(s, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["out_mask"], W["feedback"])
+    r = o.simulate(T, W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"],
+                   forced=raster, forced_psi=psi, record=True, E_override=E_hat)
+    g, go = o.take_grads()
+    m, mo = o.take_grad_magnitudes()
+    se, seo = o.take_grad_sensitivities()
+    arr = oracle.arrival_magnitude(s, W["ptr"], W["col"], W["delay"], W["x_ptr"], W["x_ids"],
+                                   W["lengths"], raster, r["psi"], r["L"])
+    tol = m + 0.1 * se + arr
+    assert np.abs(g).max() > 0
+    PT.assert_close(g_in, g[:nnz_in], "g_in (predicted E)", mag=tol[:nnz_in])
+    PT.assert_close(g_rec, g[nnz_in:], "g_rec (predicted E)", mag=tol[nnz_in:])
+    PT.assert_close(g_out, go, "g_out (predicted E)", mag=mo + 0.1 * seo)
+
+
+def _run_grads(W, samples, window_mode, pred=None):
+    """Summed input+recurrent gradients over the given sample batches with
+    frozen weights: window_mode 'full' (target at every step), 'plain' (last
+    25 steps) or 'pred' (last 25 steps, predicted error before)."""
+    import paper_2511_21674_gb300 as ep
+    net = _net(W, record_grad=1)
+    if window_mode == "pred":
+        net.attach_predictor(pred, mode=1)
+    for Ws in samples:
+        win = np.ones_like(Ws["window"]) if window_mode == "full" else Ws["window"]
+        net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], win, Ws["lengths"], W["spec"].T)
+        net.simulate(W["spec"].T)
+    g = np.concatenate([net.weights(ep.PROJ_IN, with_grad=True)[1],
+                        net.weights(ep.PROJ_REC, with_grad=True)[1]])
+    net.close()
+    return g
+
+
+def _cos(a, b):
+    return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def test_trained_predictor_brings_the_gradient_closer_to_the_full_signal():
+    import paper_2511_21674_gb300 as ep
+    B = 16
+    W = C.event_classification(batch=B)
+    s = W["spec"]
+    s.lr = 0.0                                  # frozen network: data and evaluation
+    K, T = s.n_out, s.T
+    # training pairs (x^t, E^t) with the target known at every step
+    net = _net(W)
+    pred = ep.Predictor(K + 64, K, seed=7, max_rows=256)
+    net.attach_predictor(pred, mode=2)
+    X, E = [], []
+    for k in range(24):
+        Ws = C.event_classification(batch=B, sample_seed=5000 + k)
+        net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], np.ones_like(Ws["window"]),
+                       Ws["lengths"], T)
+        net.simulate(T)
+        y, _ = net.readout()
+        x = net.predictor_inputs()
+        e = P.softmax_error(y, Ws["targets"])
+        live = np.arange(T)[None, :] < Ws["lengths"][:, None]
+        X.append(x[live])
+        E.append(e[live])
+    net.close()
+    X = np.concatenate(X).astype(np.float32)
+    E = np.concatenate(E).astype(np.float32)
+    # input scale: unit spread per input over the training pairs
+    pred.set_input_scale((1.0 / np.maximum(X.std(axis=0), 1e-3)).astype(np.float32))
+    rng = np.random.default_rng(0)
+    first = None
+    for epoch in range(6):
+        order = rng.permutation(len(X))
+        for lo in range(0, len(X) - 255, 256):
+            idx = order[lo:lo + 256]
+            l = pred.train_step(X[idx], E[idx], 1e-3)
+            first = l if first is None else first
+    # held-out samples
+    held = [C.event_classification(batch=B, sample_seed=9000 + k) for k in range(2)]
+    mse_pred = mse_zero = 0.0
+    net = _net(W)
+    net.attach_predictor(pred, mode=2)
+    for Ws in held:
+        net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], np.ones_like(Ws["window"]),
+                       Ws["lengths"], T)
+        net.simulate(T)
+        y, _ = net.readout()
+        x = net.predictor_inputs()
+        live = np.arange(T)[None, :] < Ws["lengths"][:, None]
+        e = P.softmax_error(y, Ws["targets"])[live]
+        xl = x[live]
+        eh = np.concatenate([pred.forward(xl[lo:lo + 256]) for lo in range(0, len(xl), 256)])
+        mse_pred += float(((eh - e) ** 2).sum())
+        mse_zero += float((e ** 2).sum())
+    net.close()
+    g_full = _run_grads(W, held, "full")
+    g_plain = _run_grads(W, held, "plain")
+    g_pred = _run_grads(W, held, "pred", pred)
+    c_plain, c_pred = _cos(g_plain, g_full), _cos(g_pred, g_full)
+    print(f"predictor: train loss {first:.4g} -> {l:.4g}; held-out error MSE ratio "
+          f"{mse_pred / mse_zero:.3f}; gradient cosine to the full-signal gradient: "
+          f"plain {c_plain:.3f}, with predictor {c_pred:.3f}")
+    pred.close()
+    assert mse_pred < 0.9 * mse_zero
+    assert c_pred > c_plain + 0.05

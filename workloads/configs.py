@@ -251,7 +251,10 @@ def event_classification(seed: int = 1235, batch: int = 64, T: int = 350,
                          len_lo: int = 250, len_hi: int = 350, side: int = 34,
                          n_rec: int = 200, n_out: int = 10, p_rec: float = 0.1,
                          events_per_300: float = 4000.0, w_in_scale: float = 3.0,
-                         **over) -> dict:
+                         sample_seed: int | None = None, **over) -> dict:
+    # seed fixes the network and the class rate maps; sample_seed (default:
+    # seed) draws the samples (classes, lengths, events) of the batch
+    ss = seed if sample_seed is None else sample_seed
     n_in = 2 * side * side
     spec = Spec(name="event_classification", n_in=n_in, n_rec=n_rec,
                 n_out=n_out, batch=batch, T=T, neuron_model=1, tau_a=200.0,
@@ -274,8 +277,8 @@ def event_classification(seed: int = 1235, batch: int = 64, T: int = 350,
                      axis=1)
     # per-sample class, length and event raster
     bidx = np.arange(batch, dtype=np.uint64)
-    cls = (_u64(seed, _TAG_CLS, bidx, 0) % np.uint64(n_out)).astype(np.int64)
-    lengths = (len_lo + (_u64(seed, _TAG_LEN, bidx, 0) %
+    cls = (_u64(ss, _TAG_CLS, bidx, 0) % np.uint64(n_out)).astype(np.int64)
+    lengths = (len_lo + (_u64(ss, _TAG_LEN, bidx, 0) %
                          np.uint64(len_hi - len_lo + 1)).astype(np.int64)).astype(np.int32)
     kk = np.arange(n_out, dtype=np.uint64)
     centre = side * (0.25 + 0.5 * np.stack([_uniform(seed, _TAG_CLS, kk, 1),
@@ -302,7 +305,7 @@ def event_classification(seed: int = 1235, batch: int = 64, T: int = 350,
         rate_off = np.exp(-(np.sqrt(dist2) - 2.0 * sigma[c]) ** 2 / (2.0 * sigma[c] ** 2))
         rates = np.concatenate([rate_on.reshape(T, -1), rate_off.reshape(T, -1)], 1)
         rates *= (events_per_300 / 300.0) / rates.sum(axis=1, keepdims=True)
-        u = _uniform(seed, _TAG_X, np.uint64(b) * np.uint64(n_in) +
+        u = _uniform(ss, _TAG_X, np.uint64(b) * np.uint64(n_in) +
                      np.arange(n_in, dtype=np.uint64)[None, :],
                      np.arange(1, T + 1, dtype=np.uint64)[:, None])
         rb = u < np.minimum(rates, 1.0)
