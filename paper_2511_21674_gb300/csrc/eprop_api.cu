@@ -548,6 +548,9 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     // the delivery and trace kernels hold two 256-thread blocks per SM (launch
     // bounds); their work queues are drained by whichever blocks are resident
     const int grid_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 2) * net->sm_count;
+    // delivery without carried state holds four blocks per SM
+    const int deliver_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : (n.has_state && !n.dense ? 2 : 4)) *
+                             net->sm_count;
     const int pass_rows = 2 * net->sm_count;         // window pass: two blocks per SM
     const int nw = T / U;
     if (c.profile && (int)net->ev.size() < 2 * nw) {
@@ -570,7 +573,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
                 L += 5;
             }
         }
-        eprop::launch_deliver(n, i, grid_rows, st);
+        eprop::launch_deliver(n, i, deliver_rows, st);
         L += 4;
         if (i % U == 0) {
             eprop::launch_filter_error(n, i, st);

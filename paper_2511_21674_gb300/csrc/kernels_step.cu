@@ -1,5 +1,8 @@
 // Per-step kernels: input injection, neuron update, readout and error
 // signal, spike transmission through the delayed synapses.
+#include <cstddef>
+
+#include "eprop.h"
 #include "eprop_internal.cuh"
 #include "eprop_launch.h"
 
@@ -42,92 +45,126 @@ __global__ void inject_kernel(Net n, int i) {
 
 // K1: LIF / ALIF neuron update (Eq. lif_update, Eq. binary-spike-state-
 // variable, Eq. spike-threshold-adaptation, Eq. piecewise-linear-surrogate-
-// gradient), one thread per (sample, neuron).
-__global__ void neuron_kernel(Net n, int i) {
+// gradient).  Each thread updates kNPT neurons of one sample (strided by the
+// block size, so every access stays coalesced): the clock and the drive
+// table are read once per block, then the state of all kNPT neurons is
+// loaded in one batch (one memory round trip for the batch), updated, and
+// stored.
+constexpr int kNPT = 4;
+constexpr int kNeuronThreads = 256;
+
+__global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
+    __shared__ uint32_t thr_s[EPROP_MAX_DRIVE_THR];
+    __shared__ Clock ck_s;
+    __shared__ int len_s;
     const int b = blockIdx.y;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n.n_rec) return;
-    const long long nb = (long long)b * n.n_rec + j;
-    // every load that does not depend on the clock is issued together with
-    // the clock and sample-length loads (one memory round trip)
-    const Clock ck = *n.clock;
-    const int len = n.lengths[b];
-    const uint8_t zp8 = n.z_prev[nb];
-    float v_hi = n.v[nb], v_lo = n.v_lo[nb];
-    float a_hi = 0.f, a_lo = 0.f;
-    if (n.alif) {
-        a_hi = n.a[nb];
-        a_lo = n.a_lo[nb];
+    if (threadIdx.x == 0) {
+        ck_s = *n.clock;
+        len_s = n.lengths[b];
     }
-    int ref = n.ref[nb];
+    for (int m = threadIdx.x; m < n.n_thr; m += blockDim.x) thr_s[m] = n.drive_thr[m];
+    __syncthreads();
+    const Clock ck = ck_s;
+    const int len = len_s;
     const int r = ck.r_base + i;
     const int a0 = ((r - 1) / n.U) * n.U;
-    float *psi_slot = n.psi_hist + ((long long)b * (n.U + 1) + (r - a0)) * n.n_rec + j;
-    if (i > len) {               // sample already finished: frozen, silent
-        *psi_slot = 0.0f;
-        if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
-        return;
-    }
     const long long t_abs = ck.t_abs_base + i;
     const int slot = (ck.ring0 + i) % (n.D + 1);
-    long long *ring = n.ring + ((long long)b * (n.D + 1) + slot) * n.n_rec + j;
-    const long long acc = *ring;
-    *ring = 0;
-    // exact fixed-point input split into an FP32 pair
-    const float acc_hi = (float)acc;
-    float u_hi = acc_hi * kFixInv;
-    float u_lo = (float)(acc - (long long)acc_hi) * kFixInv;
-    if (n.n_thr > 0) {
-        const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
-        const uint32_t u = (uint32_t)(h >> 32);
-        // thresholds are non-decreasing (checked at creation): the count of
-        // thresholds <= u is the index of the first one above u
-        int cnt = 0;
-        while (cnt < n.n_thr && u >= __ldg(n.drive_thr + cnt)) ++cnt;
-        const float dv = n.drive_weight * (float)cnt;
-        const float de = fmaf(n.drive_weight, (float)cnt, -dv);
-        float e;
-        two_sum(u_hi, dv, u_hi, e);
-        u_lo += e + de;
+    const int jb = blockIdx.x * (kNeuronThreads * kNPT) + threadIdx.x;
+    float *psi_row = n.psi_hist + ((long long)b * (n.U + 1) + (r - a0)) * n.n_rec;
+    long long *ring_row = n.ring + ((long long)b * (n.D + 1) + slot) * n.n_rec;
+    const long long nb0 = (long long)b * n.n_rec;
+    if (i > len) {               // sample already finished: frozen, silent
+#pragma unroll
+        for (int q = 0; q < kNPT; ++q) {
+            const int j = jb + q * kNeuronThreads;
+            if (j >= n.n_rec) break;
+            psi_row[j] = 0.0f;
+            if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
+        }
+        return;
     }
-    const float zp = (float)zp8;
-    float vth = n.v_th, vth_lo = 0.0f;
-    if (n.alif) {
-        comp_step(n.rho, n.rho_lo, zp, 0.0f, a_hi, a_lo);
-        n.a[nb] = a_hi;
-        n.a_lo[nb] = a_lo;
-        vth = fmaf(n.beta_a, a_hi, n.v_th);
-        vth_lo = fmaf(n.beta_a, a_hi, n.v_th - vth) + n.beta_a * a_lo;
+    // batch of loads
+    float v_hi[kNPT], v_lo[kNPT], a_hi[kNPT], a_lo[kNPT];
+    int ref[kNPT];
+    uint8_t zp8[kNPT];
+    long long acc[kNPT];
+#pragma unroll
+    for (int q = 0; q < kNPT; ++q) {
+        const int j = jb + q * kNeuronThreads;
+        const bool in = j < n.n_rec;
+        const long long nb = nb0 + (in ? j : 0);
+        v_hi[q] = in ? n.v[nb] : 0.f;
+        v_lo[q] = in ? n.v_lo[nb] : 0.f;
+        a_hi[q] = (in && n.alif) ? n.a[nb] : 0.f;
+        a_lo[q] = (in && n.alif) ? n.a_lo[nb] : 0.f;
+        ref[q] = in ? n.ref[nb] : 0;
+        zp8[q] = in ? n.z_prev[nb] : 0;
+        acc[q] = in ? ring_row[j] : 0;
     }
-    // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
-    {
-        float e;
-        two_sum(u_hi, -zp * vth, u_hi, e);
-        u_lo += e - zp * vth_lo;
-    }
-    comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi, v_lo);
-    n.v[nb] = v_hi;
-    n.v_lo[nb] = v_lo;
-    const float m = (v_hi - vth) + (v_lo - vth_lo);
-    const bool refractory = ref > 0;
-    int z;
-    if (n.forced) z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
-    else z = (!refractory && m > 0.0f) ? 1 : 0;
-    const float h = 1.0f - n.beta_sg * fabsf(m);
-    const float psi = refractory ? 0.0f : n.gamma * fmaxf(h, 0.0f);
-    *psi_slot = psi;
-    if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = psi;
-    if (refractory) ref -= 1;
-    if (z) ref = n.t_ref;
-    n.ref[nb] = ref;
-    n.z_prev[nb] = (uint8_t)z;
-    if (z) {
-        mark_spike(n, b, n.n_in + j, r);
-        if (n.pop_cnt) atomicAdd(&n.pop_cnt[b * kPopGroups + (j & (kPopGroups - 1))], 1);
-        if (n.record_raster) {
-            const int W32 = (n.T + 31) / 32;
-            atomicOr(&n.rec_raster[((long long)b * W32 + ((i - 1) >> 5)) * n.n_rec + j],
-                     1u << ((i - 1) & 31));
+#pragma unroll
+    for (int q = 0; q < kNPT; ++q) {
+        const int j = jb + q * kNeuronThreads;
+        if (j >= n.n_rec) break;
+        const long long nb = nb0 + j;
+        ring_row[j] = 0;
+        // exact fixed-point input split into an FP32 pair
+        const float acc_hi = (float)acc[q];
+        float u_hi = acc_hi * kFixInv;
+        float u_lo = (float)(acc[q] - (long long)acc_hi) * kFixInv;
+        if (n.n_thr > 0) {
+            const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
+            const uint32_t u = (uint32_t)(h >> 32);
+            // thresholds are non-decreasing (checked at creation): the count of
+            // thresholds <= u is the index of the first one above u
+            int cnt = 0;
+            while (cnt < n.n_thr && u >= thr_s[cnt]) ++cnt;
+            const float dv = n.drive_weight * (float)cnt;
+            const float de = fmaf(n.drive_weight, (float)cnt, -dv);
+            float e;
+            two_sum(u_hi, dv, u_hi, e);
+            u_lo += e + de;
+        }
+        const float zp = (float)zp8[q];
+        float vth = n.v_th, vth_lo = 0.0f;
+        if (n.alif) {
+            comp_step(n.rho, n.rho_lo, zp, 0.0f, a_hi[q], a_lo[q]);
+            n.a[nb] = a_hi[q];
+            n.a_lo[nb] = a_lo[q];
+            vth = fmaf(n.beta_a, a_hi[q], n.v_th);
+            vth_lo = fmaf(n.beta_a, a_hi[q], n.v_th - vth) + n.beta_a * a_lo[q];
+        }
+        // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
+        {
+            float e;
+            two_sum(u_hi, -zp * vth, u_hi, e);
+            u_lo += e - zp * vth_lo;
+        }
+        comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi[q], v_lo[q]);
+        n.v[nb] = v_hi[q];
+        n.v_lo[nb] = v_lo[q];
+        const float m = (v_hi[q] - vth) + (v_lo[q] - vth_lo);
+        const bool refractory = ref[q] > 0;
+        int z;
+        if (n.forced) z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
+        else z = (!refractory && m > 0.0f) ? 1 : 0;
+        const float hh = 1.0f - n.beta_sg * fabsf(m);
+        const float psi = refractory ? 0.0f : n.gamma * fmaxf(hh, 0.0f);
+        psi_row[j] = psi;
+        if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = psi;
+        int rf = ref[q];
+        if (refractory) rf -= 1;
+        if (z) rf = n.t_ref;
+        n.ref[nb] = rf;
+        n.z_prev[nb] = (uint8_t)z;
+        if (z) {
+            mark_spike(n, b, n.n_in + j, r);
+            if (n.pop_cnt) atomicAdd(&n.pop_cnt[b * kPopGroups + (j & (kPopGroups - 1))], 1);
+            if (n.record_raster) {
+                const int W32 = (n.T + 31) / 32;
+                atomicOr(&n.rec_raster[((long long)b * W32 + ((i - 1) >> 5)) * n.n_rec + j],
+                         1u << ((i - 1) & 31));
+            }
         }
     }
 }
@@ -324,6 +361,9 @@ __device__ __forceinline__ float stage_trace(const Net &n, const StageBuf &sb, c
 }
 
 constexpr int kDStages = 3;
+__host__ __device__ constexpr size_t deliver_stage_bytes(bool state) {
+    return state ? sizeof(StageBuf) : offsetof(StageBuf, tr);
+}
 
 // K2: transmission of the spikes of call step i.  Each warp walks its share
 // of the step's spiking rows as a sequence of chunks of kChunk synapse
@@ -334,17 +374,22 @@ constexpr int kDStages = 3;
 // last arrival is added on the fly (read-only).  Arrivals are summed in
 // exact int64 fixed point.
 template <bool ALIF, bool STATE>
-__global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
+__global__ void __launch_bounds__(256, STATE ? 2 : 4) deliver_kernel(Net n, int i) {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ uint64_t bars[8][kDStages];
     __shared__ StageDesc desc[8][kDStages];
-    __shared__ RowInfo info[8][kDStages][kMaxDelay + 1];
+    __shared__ RowInfo info[8][STATE ? kDStages : 1][kMaxDelay + 1];
     __shared__ unsigned long long ev_block;
     __shared__ long long ring_off[kMaxDelay + 1];
     const int b = blockIdx.y;
     if (i > n.lengths[b]) return;            // whole block: same sample
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kDStages;
+    // without carried state the trace stream is not staged: stages are the
+    // (j|d, w) part of a StageBuf only
+    constexpr size_t kStride = deliver_stage_bytes(STATE);
+    auto buf = [&](int k) -> StageBuf & {
+        return *reinterpret_cast<StageBuf *>(dsm + (size_t)(warp * kDStages + k) * kStride);
+    };
     if (threadIdx.x == 0) ev_block = 0ULL;
     if (threadIdx.x <= n.D)                  // ring slot of an arrival d steps ahead
         ring_off[threadIdx.x] = (long long)((n.clock->ring0 + i + (int)threadIdx.x) % (n.D + 1)) * n.n_rec;
@@ -385,7 +430,7 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
         const int cnt = (int)min((long long)kChunk, pre - pq);
         if (STATE && lane >= 1 && lane <= n.D) info[warp][k][lane] = rinfo;
         if (lane == 0) {
-            issue_chunk(n, buf[k], &bars[warp][k], pq, cnt, STATE, desc[warp][k]);
+            issue_chunk(n, buf(k), &bars[warp][k], pq, cnt, STATE, desc[warp][k]);
             desc[warp][k].first = pfirst;
             desc[warp][k].row = (int)(pre - pq);
         }
@@ -404,7 +449,7 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
         }
         const StageDesc d = desc[warp][k];
         if (d.first && lane == 0) ev_warp += (unsigned long long)d.row;
-        const StageBuf &sb = buf[k];
+        const StageBuf &sb = buf(k);
 #pragma unroll 2
         for (int h = 0; h < kChunk / 32; h += 4) {
             uint32_t td[4];
@@ -487,7 +532,7 @@ __global__ void __launch_bounds__(256, 2) deliver_kernel(Net n, int i) {
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async();
-                issue_chunk(n, buf[k], &bars[warp][k], pq, cnt, STATE, desc[warp][k]);
+                issue_chunk(n, buf(k), &bars[warp][k], pq, cnt, STATE, desc[warp][k]);
                 desc[warp][k].first = pfirst;
                 desc[warp][k].row = (int)(pre - pq);
             }
@@ -518,7 +563,8 @@ void launch_inject(const Net &n, int i, int max_events_per_step, cudaStream_t st
 }
 
 void launch_neuron(const Net &n, int i, cudaStream_t st) {
-    neuron_kernel<<<dim3((n.n_rec + 255) / 256, n.B), 256, 0, st>>>(n, i);
+    const int per_block = kNeuronThreads * kNPT;
+    neuron_kernel<<<dim3((n.n_rec + per_block - 1) / per_block, n.B), kNeuronThreads, 0, st>>>(n, i);
 }
 
 void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
@@ -542,20 +588,22 @@ void launch_pred_apply(const Net &n, int i, cudaStream_t st) {
 
 void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st) {
     const dim3 grid(grid_x, n.B);
-    const size_t sm = sizeof(StageBuf) * 8 * kDStages;
     if (n.has_state && !n.dense) {
+        const size_t sm = deliver_stage_bytes(true) * 8 * kDStages;
         if (n.alif) deliver_kernel<true, true><<<grid, 256, sm, st>>>(n, i);
         else deliver_kernel<false, true><<<grid, 256, sm, st>>>(n, i);
     } else {
+        const size_t sm = deliver_stage_bytes(false) * 8 * kDStages;
         deliver_kernel<false, false><<<grid, 256, sm, st>>>(n, i);
     }
 }
 
 void prepare_step_kernel_attributes() {
-    const int sm = (int)(sizeof(StageBuf) * 8 * kDStages);
+    const int sm = (int)(deliver_stage_bytes(true) * 8 * kDStages);
+    const int sm0 = (int)(deliver_stage_bytes(false) * 8 * kDStages);
     cudaFuncSetAttribute(deliver_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(deliver_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(deliver_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(deliver_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm0);
 }
 
 }  // namespace eprop

@@ -85,16 +85,18 @@ __global__ void filter_error_kernel(Net n) {
     n.Cwin[idx] = n.kappa * acc;
 }
 
-// learning-signal tables: one thread per (sample, neuron); the window's
-// errors E[U][K] are staged in shared memory (when they fit), the learning
-// signal L^t = sum_k B_jk E_k^t of the window is formed k-chunk by k-chunk in
-// a per-thread shared-memory column, then a backward adjoint sweep writes
-// the per-step tables and the window coefficients.
+// learning-signal tables: one thread per (sample, neuron), 128 neurons per
+// block.  The window is swept backwards in chunks of steps: the chunk's
+// learning signals L^t = sum_k B_jk E_k^t (Eq. final-gradient) are formed in
+// registers from shared tiles of the block's feedback rows and of the
+// chunk's errors, then the adjoint recursion writes the per-step tables and,
+// at the window start, the window coefficients.
 template <bool ALIF>
 __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     constexpr int kTC = ALIF ? 16 : 32;     // window steps per chunk
     constexpr int kKT = 32;                 // feedback columns per shared tile
-    __shared__ float Bs[128][kKT + 1];
+    __shared__ __align__(16) float Bs[128][kKT + 4];     // rows 16-byte aligned, conflict-free float4
+    __shared__ __align__(16) float Es[kTC][kKT];         // the chunk's errors (zero outside it)
     const int b = blockIdx.y;
     const int U = n.U, K = n.n_out, N = n.n_rec;
     const int r_end = run_step_w(n, i_end);
@@ -105,7 +107,6 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     const int j = j0 + tid;
     const bool act = j < N;
     const float *psi_g = n.psi_hist + (long long)b * (U + 1) * N + (act ? j : 0);
-    const bool vec4 = (K & 3) == 0;
     // The adjoint sweep is the per-window reduction of the gradient.  For
     // ALIF the eligibility psi (zbar - beta eps_a) is a near-cancellation of
     // two long-memory traces, so the sweep runs in FP64 there (FP32 loses up
@@ -148,30 +149,24 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
                 const int jr = j0 + r;
                 Bs[r][cc] = (jr < N && cc < kt) ? n.fb[(long long)jr * K + k0 + cc] : 0.f;
             }
-            __syncthreads();
-            int kk = 0;
-            if (vec4) {
-                for (; kk + 4 <= kt; kk += 4) {
-                    const float b0 = Bs[tid][kk], b1 = Bs[tid][kk + 1], b2 = Bs[tid][kk + 2], b3 = Bs[tid][kk + 3];
-#pragma unroll
-                    for (int c = 0; c < kTC; ++c) {
-                        const int u = u1 - c;
-                        if (u >= u0) {
-                            const float4 e = __ldg(reinterpret_cast<const float4 *>(E + (long long)(u - 1) * K + k0 + kk));
-                            Lc[c] = fmaf(b0, e.x, Lc[c]);
-                            Lc[c] = fmaf(b1, e.y, Lc[c]);
-                            Lc[c] = fmaf(b2, e.z, Lc[c]);
-                            Lc[c] = fmaf(b3, e.w, Lc[c]);
-                        }
-                    }
-                }
+            for (int q = tid; q < kTC * kKT; q += 128) {
+                const int c = q / kKT, cc = q % kKT;
+                const int u = u1 - c;
+                Es[c][cc] = (u >= u0 && cc < kt) ? E[(long long)(u - 1) * K + k0 + cc] : 0.f;
             }
-            for (; kk < kt; ++kk) {
-                const float b0 = Bs[tid][kk];
+            __syncthreads();
+            // L^t for the chunk's steps: one float4 of the neuron's feedback
+            // row against one broadcast float4 of each step's errors
+#pragma unroll 2
+            for (int kk = 0; kk < kKT; kk += 4) {
+                const float4 bq = *reinterpret_cast<const float4 *>(&Bs[tid][kk]);
 #pragma unroll
                 for (int c = 0; c < kTC; ++c) {
-                    const int u = u1 - c;
-                    if (u >= u0) Lc[c] = fmaf(b0, __ldg(E + (long long)(u - 1) * K + k0 + kk), Lc[c]);
+                    const float4 e = *reinterpret_cast<const float4 *>(&Es[c][kk]);
+                    Lc[c] = fmaf(bq.x, e.x, Lc[c]);
+                    Lc[c] = fmaf(bq.y, e.y, Lc[c]);
+                    Lc[c] = fmaf(bq.z, e.z, Lc[c]);
+                    Lc[c] = fmaf(bq.w, e.w, Lc[c]);
                 }
             }
         }
