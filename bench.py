@@ -36,7 +36,7 @@ METRIC = "synapse-events/s and sim-time/wall-time vs HBM roofline at stated grad
 UNIT = "synapse-events/s"
 FALLBACK_HBM_GBS = 6800.0
 TRACE_KERNEL_SRC = os.path.join(ROOT, "paper_2511_21674_gb300", "csrc", "kernels_window.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_million_sparse.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "window_pass_million_sparse.md")
 
 
 def parse():
@@ -71,18 +71,18 @@ def measured_peaks():
 
 
 def recorded_traffic():
-    """DRAM bytes per trace launch from the committed ncu summary, if it was
-    taken on the current kernel source (sha256 recorded in the summary)."""
+    """DRAM bytes of one window pass (active + idle launches) at full size,
+    from the committed ncu summary, if it was taken on the current kernel
+    source (sha256 recorded in the summary); else None."""
     try:
         text = open(TRAFFIC_FILE).read()
         src = hashlib.sha256(open(TRACE_KERNEL_SRC, "rb").read()).hexdigest()
         fields = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[0] != " ")
         if fields.get("kernel_source_sha256", "").strip() != src:
-            return None, None
-        return (float(fields["dram_bytes_per_event"].strip()),
-                float(fields["dram_bytes_per_launch_at_full_size"].strip()))
+            return None
+        return float(fields["dram_bytes_per_window_at_full_size"].strip())
     except Exception:
-        return None, None
+        return None
 
 
 class ClockSampler:
@@ -319,10 +319,9 @@ def _run_ours(args, rank, world, local):
     bytes_per_event = 16.0 if trace_dtype == 1 else 20.0     # j|d 4 r, w 4 r/w, trace 2|4 r/w
     peak, peak_src = measured_peaks()
     achieved = events * bytes_per_event / (trace_ms / 1000.0) / 1e9 if trace_ms > 0 else None
-    traffic_per_event, traffic_launch = recorded_traffic()
-    traffic = None
-    if traffic_per_event is not None and trace_launches:
-        traffic = traffic_per_event * events / trace_launches
+    # per window pass (the unit `achieved` averages over): DRAM bytes from
+    # the committed ncu capture, scaled to full size (see profiles/)
+    traffic = recorded_traffic()
     net.close()
     if rank != 0:
         return
@@ -341,6 +340,8 @@ def _run_ours(args, rank, world, local):
                      "kernel": "window_pass_kernel (active + idle rows, one pair per update window)",
                      "bytes_per_event": bytes_per_event,
                      "stream_bytes_per_window": nnz * bytes_per_event,
+                     "algorithmic_bytes_per_window": (events * bytes_per_event / windows) if windows else None,
+                     "traffic_unit": "DRAM bytes per window pass (active + idle launches)",
                      "peak_source": f"{peak_src} (hbm_gbs)",
                      "trace_ms_per_step": trace_ms / K, "trace_launches_per_step": trace_launches / K},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -374,6 +374,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         FA(Cwin, float, B * K);
         FA(zk, float, 2 * B * N);
         FA(loss_acc, float, B);
+        FA(ro_done, int, B);
         FA(events, unsigned long long, 1);
         FA(err_flags, unsigned int, 1);
         FA(clock, eprop::Clock, 1);
@@ -551,7 +552,9 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     // delivery without carried state holds four blocks per SM
     const int deliver_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : (n.has_state && !n.dense ? 2 : 4)) *
                              net->sm_count;
-    const int pass_rows = 2 * net->sm_count;         // window pass: two blocks per SM
+    // window pass: two blocks per SM by default (a third fits, but the
+    // smaller L1 that leaves for the table lookups measured slower)
+    const int pass_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 2) * net->sm_count;
     const int nw = T / U;
     if (c.profile && (int)net->ev.size() < 2 * nw) {
         for (int q = (int)net->ev.size(); q < 2 * nw; ++q) {
@@ -574,7 +577,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             }
         }
         eprop::launch_deliver(n, i, deliver_rows, st);
-        L += 4;
+        L += 3;
         if (i % U == 0) {
             eprop::launch_filter_error(n, i, st);
             eprop::launch_tables(n, i, st);

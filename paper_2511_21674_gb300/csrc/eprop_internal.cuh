@@ -115,6 +115,7 @@ struct Net {
     float *pred_x;            // [B][pred_in] inputs of the current step
     float *pred_rec;          // [B][T][pred_in] recorded inputs (bit 1)
     const float *pred_y;      // [B][n_out] predictor outputs of the current step
+    int *ro_done;             // [B] readout blocks finished in the current step
     unsigned long long *events;
     unsigned int *err_flags;  // bit 0: catch-up ring overflow
     Clock *clock;

@@ -171,13 +171,89 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
 
 constexpr int kReadoutChunk = 16;    // spikes per readout block and round
 
+__device__ float block_sum(float x, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = x;
+    __syncthreads();
+    float t = 0.0f;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int q = 0; q < nw; ++q) t += sh[q];
+    return t;
+}
+
+__device__ float block_max(float x, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = x;
+    __syncthreads();
+    float t = -INFINITY;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int q = 0; q < nw; ++q) t = fmaxf(t, sh[q]);
+    return t;
+}
+
+// K3b: leaky readout (Eq. leaky_integrator), error signal and loss
+// (Eq. mean-squared-error / Eq. softmax, Eq. cross-entropy-loss) of sample b,
+// by one whole CTA, thread = readout k (blockDim multiple of 32, >= n_out).
+__device__ void readout_finish(const Net &n, int i, int b) {
+    __shared__ float sh[32];
+    const int k = threadIdx.x;
+    const bool has_k = k < n.n_out;
+    const int r = run_step(n, i);
+    const int a0 = win_start(n, r);
+    const long long bk = (long long)b * n.n_out + k;
+    float *E = n.E_win + ((long long)b * n.U + (r - a0 - 1)) * n.n_out;
+    // the list slot of step r + 1 was last used RS steps ago; every reader of
+    // it has finished (RS = U + D + 1 covers the window's trace launches)
+    if (threadIdx.x < kBkt) n.list_cnt[list_index(n, b, (r + 1) % n.RS) + threadIdx.x] = 0;
+    if (i > n.lengths[b]) {      // after the sample's end: no error, no output
+        if (has_k) {
+            E[k] = 0.0f;
+            n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = 0.0f;
+        }
+        return;
+    }
+    float y = 0.0f;
+    if (has_k) {
+        const long long acc = __ldcg(n.y_acc + bk);     // summed by atomics in L2
+        n.y_acc[bk] = 0;
+        y = n.kappa * n.y[bk] + (float)acc * kFixInv;
+        n.y[bk] = y;
+        n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = y;
+    }
+    const float win = n.window ? (float)n.window[(long long)b * n.T + (i - 1)] : 1.0f;
+    const float tgt = has_k ? n.targets[((long long)b * n.T + (i - 1)) * n.n_out + k] : 0.0f;
+    float l;
+    if (n.loss == 0) {
+        const float diff = y - tgt;
+        if (has_k) E[k] = win * diff;
+        l = has_k ? 0.5f * win * diff * diff : 0.0f;
+    } else {
+        const float mx = block_max(has_k ? y : -INFINITY, sh);
+        const float ex = has_k ? expf(y - mx) : 0.0f;
+        const float den = block_sum(ex, sh);
+        if (has_k) E[k] = win * (ex / den - tgt);
+        l = has_k ? -win * tgt * ((y - mx) - logf(den)) : 0.0f;
+    }
+    const float tot = block_sum(l, sh);
+    if (threadIdx.x == 0) n.loss_acc[b] += tot;
+}
+
 // K3a: readout input sum_j W_out[j][k] z_j^t in exact fixed point; one CTA per
-// (chunk of the step's spike list, sample); thread = readout k.
+// (chunk of the step's spike list, sample); thread = readout k; the last CTA
+// of a sample then runs K3b for it.
 __global__ void readout_accum_kernel(Net n, int i, int chunk) {
     __shared__ int srcs[kReadoutChunk];
     __shared__ int incl[kBkt];
+    __shared__ int last;
     const int b = blockIdx.y;
-    if (i > n.lengths[b]) return;
+    if (i > n.lengths[b]) {                  // finished sample: block 0 writes the zeros
+        if (blockIdx.x == 0) readout_finish(n, i, b);
+        return;
+    }
     const int r = run_step(n, i);
     const long long li = list_index(n, b, r % n.RS);
     const int *cnt = n.list_cnt + li;
@@ -211,78 +287,16 @@ __global__ void readout_accum_kernel(Net n, int i, int chunk) {
         }
         __syncthreads();
     }
-}
-
-__device__ float block_sum(float x, float *sh) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = x;
-    __syncthreads();
-    float t = 0.0f;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int q = 0; q < nw; ++q) t += sh[q];
-    return t;
-}
-
-__device__ float block_max(float x, float *sh) {
-    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = x;
-    __syncthreads();
-    float t = -INFINITY;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int q = 0; q < nw; ++q) t = fmaxf(t, sh[q]);
-    return t;
-}
-
-// K3b: leaky readout (Eq. leaky_integrator), error signal and loss
-// (Eq. mean-squared-error / Eq. softmax, Eq. cross-entropy-loss), one CTA per
-// sample, thread = readout k (blockDim multiple of 32, >= n_out).
-__global__ void readout_error_kernel(Net n, int i) {
-    __shared__ float sh[32];
-    const int b = blockIdx.x;
-    const int k = threadIdx.x;
-    const bool has_k = k < n.n_out;
-    const int r = run_step(n, i);
-    const int a0 = win_start(n, r);
-    const long long bk = (long long)b * n.n_out + k;
-    float *E = n.E_win + ((long long)b * n.U + (r - a0 - 1)) * n.n_out;
-    // the list slot of step r + 1 was last used RS steps ago; every reader of
-    // it has finished (RS = U + D + 1 covers the window's trace launches)
-    if (threadIdx.x < kBkt) n.list_cnt[list_index(n, b, (r + 1) % n.RS) + threadIdx.x] = 0;
-    if (i > n.lengths[b]) {      // after the sample's end: no error, no output
-        if (has_k) {
-            E[k] = 0.0f;
-            n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = 0.0f;
-        }
-        return;
+    // the sample's last block to finish forms y, E and the loss
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&n.ro_done[b], 1) == (int)gridDim.x - 1;
     }
-    float y = 0.0f;
-    if (has_k) {
-        const long long acc = n.y_acc[bk];
-        n.y_acc[bk] = 0;
-        y = n.kappa * n.y[bk] + (float)acc * kFixInv;
-        n.y[bk] = y;
-        n.y_rec[((long long)b * n.T + (i - 1)) * n.n_out + k] = y;
-    }
-    const float win = n.window ? (float)n.window[(long long)b * n.T + (i - 1)] : 1.0f;
-    const float tgt = has_k ? n.targets[((long long)b * n.T + (i - 1)) * n.n_out + k] : 0.0f;
-    float l;
-    if (n.loss == 0) {
-        const float diff = y - tgt;
-        if (has_k) E[k] = win * diff;
-        l = has_k ? 0.5f * win * diff * diff : 0.0f;
-    } else {
-        const float mx = block_max(has_k ? y : -INFINITY, sh);
-        const float ex = has_k ? expf(y - mx) : 0.0f;
-        const float den = block_sum(ex, sh);
-        if (has_k) E[k] = win * (ex / den - tgt);
-        l = has_k ? -win * tgt * ((y - mx) - logf(den)) : 0.0f;
-    }
-    const float tot = block_sum(l, sh);
-    if (threadIdx.x == 0) n.loss_acc[b] += tot;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) n.ro_done[b] = 0;
+    readout_finish(n, i, b);
 }
 
 // Predictor inputs of step i (one block per sample): the readout
@@ -572,12 +586,8 @@ void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
     int blocks = (n.n_src + chunk - 1) / chunk;
     const int cap = n.B > 1 ? 4 : 2 * sm_count;
     if (blocks > cap) blocks = cap;
-    int th = ((n.n_out + 31) / 32) * 32;
-    if (th > 256) th = 256;
-    if (th < 32) th = 32;
+    const int th = ((n.n_out + 31) / 32) * 32;     // >= n_out: one thread per readout
     readout_accum_kernel<<<dim3(blocks, n.B), th, 0, st>>>(n, i, chunk);
-    int th2 = ((n.n_out + 31) / 32) * 32;
-    readout_error_kernel<<<n.B, th2, 0, st>>>(n, i);
 }
 
 void launch_pred_input(const Net &n, int i, cudaStream_t st) { pred_input_kernel<<<n.B, 128, 0, st>>>(n, i); }

