@@ -158,9 +158,16 @@ def barrier_max(value, world):
     if world == 1:
         return value
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    # NCCL reduces device tensors; the gloo backend (CPU tests) host tensors
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Each replica builds its own network and drive (independent problems)."""
+    return 1237 + rank
 
 
 def barrier(world):
@@ -247,7 +254,7 @@ def _run_ours(args, rank, world, local):
     from workloads import gpu_build as G
     torch.manual_seed(0)
     W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
-                               seed=1237 + rank)
+                               seed=replica_seed(rank))
     spec = W["spec"]
     trace_dtype = 1 if args.trace_dtype == "bf16" else 0
     net = ep.Network(spec, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], None, W["feedback"],

@@ -565,7 +565,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     }
     for (int i = 1; i <= T; ++i) {
         if (c.n_in > 0) { eprop::launch_inject(n, i, (int)net->max_in_per_step, st); L += 1; }
-        eprop::launch_neuron(n, i, st);
+        eprop::launch_neuron(n, i, net->sm_count, st);
         eprop::launch_readout(n, i, net->sm_count, st);
         if (n.pred_mode) {
             eprop::launch_pred_input(n, i, st);

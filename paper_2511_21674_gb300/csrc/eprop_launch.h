@@ -7,7 +7,7 @@ namespace eprop {
 struct Net;
 
 void launch_inject(const Net &n, int i, int max_events_per_step, cudaStream_t st);
-void launch_neuron(const Net &n, int i, cudaStream_t st);
+void launch_neuron(const Net &n, int i, int sm_count, cudaStream_t st);
 void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st);
 void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st);
 

@@ -70,10 +70,13 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
     const int a0 = ((r - 1) / n.U) * n.U;
     const long long t_abs = ck.t_abs_base + i;
     const int slot = (ck.ring0 + i) % (n.D + 1);
-    const int jb = blockIdx.x * (kNeuronThreads * kNPT) + threadIdx.x;
     float *psi_row = n.psi_hist + ((long long)b * (n.U + 1) + (r - a0)) * n.n_rec;
     long long *ring_row = n.ring + ((long long)b * (n.D + 1) + slot) * n.n_rec;
     const long long nb0 = (long long)b * n.n_rec;
+    // the grid holds as many blocks as are resident at once; each block
+    // walks groups of kNeuronThreads * kNPT neurons
+    for (int jg = blockIdx.x * (kNeuronThreads * kNPT); jg < n.n_rec; jg += gridDim.x * (kNeuronThreads * kNPT)) {
+    const int jb = jg + threadIdx.x;
     if (i > len) {               // sample already finished: frozen, silent
 #pragma unroll
         for (int q = 0; q < kNPT; ++q) {
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
             psi_row[j] = 0.0f;
             if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
         }
-        return;
+        continue;
     }
     // batch of loads
     float v_hi[kNPT], v_lo[kNPT], a_hi[kNPT], a_lo[kNPT];
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
                          1u << ((i - 1) & 31));
             }
         }
+    }
     }
 }
 
@@ -576,9 +580,13 @@ void launch_inject(const Net &n, int i, int max_events_per_step, cudaStream_t st
     inject_kernel<<<dim3(blocks, n.B), 256, 0, st>>>(n, i);
 }
 
-void launch_neuron(const Net &n, int i, cudaStream_t st) {
+void launch_neuron(const Net &n, int i, int sm_count, cudaStream_t st) {
     const int per_block = kNeuronThreads * kNPT;
-    neuron_kernel<<<dim3((n.n_rec + per_block - 1) / per_block, n.B), kNeuronThreads, 0, st>>>(n, i);
+    // one group of kNeuronThreads * kNPT neurons per block (a grid capped at
+    // the resident blocks, walking several groups per block, measured slower)
+    (void)sm_count;
+    const int blocks = (n.n_rec + per_block - 1) / per_block;
+    neuron_kernel<<<dim3(blocks, n.B), kNeuronThreads, 0, st>>>(n, i);
 }
 
 void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {

@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
 constexpr int kPStages = 2;
 
 template <bool ALIF, bool ACTIVE, bool TB>
-__global__ void __launch_bounds__(256, 3) window_pass_kernel(Net n, int i_end) {
+__global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ uint64_t bars[8][kPStages];
     __shared__ StageDesc desc[8][kPStages];
@@ -786,7 +786,10 @@ __global__ void __launch_bounds__(256, 3) window_pass_kernel(Net n, int i_end) {
             uint32_t td[kB];
             float wv[kB], zr[kB], eb[kB], ep[kB];
             Coef cf[kB];
+            float4 t0[kB];                     // table entry of the first arrival
+            int c0[kB];                        // its index in the row's spike list (-1: none)
             bool live[kB];
+            // phase 1: every load the synapses need is issued before any is used
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
                 const int idx = lane + 32 * (h + u);
@@ -800,6 +803,23 @@ __global__ void __launch_bounds__(256, 3) window_pass_kernel(Net n, int i_end) {
                 ep[u] = (ALIF && in) ? load_trace(n.epsa, d.q0 + idx, TB) : 0.f;
                 live[u] = in && (ACTIVE || zr[u] != 0.f || eb[u] != 0.f || ep[u] != 0.f);
                 if (live[u]) cf[u] = load_coef<ALIF>(n, td[u] & 0xFFFFFFu, 0);
+                c0[u] = -1;
+                t0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ACTIVE && listed && in) {
+                    const int dl = (int)(td[u] >> 24);
+                    int cc = 0;
+                    while (cc < ns && sp[cc] + dl <= a0) ++cc;
+                    if (cc < ns && sp[cc] + dl <= r_end) {
+                        c0[u] = cc;
+                        const long long qi = qa + (long long)(sp[cc] + dl) * N + (td[u] & 0xFFFFFFu);
+                        if (ALIF) {
+                            t0[u] = __ldg(reinterpret_cast<const float4 *>(n.qp) + qi);
+                        } else {
+                            const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qi);
+                            t0[u] = make_float4(t.x, t.y, 0.f, 0.f);
+                        }
+                    }
+                }
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
@@ -811,9 +831,14 @@ __global__ void __launch_bounds__(256, 3) window_pass_kernel(Net n, int i_end) {
                 apply_coef<ALIF>(n, cf[u], zbar, epsa, ebar, G);
                 if (ACTIVE) {
                     if (listed) {
-                        for (int cc = 0; cc < ns; ++cc) {
+                        if (c0[u] >= 0) {
+                            G += t0[u].x;
+                            ebar += t0[u].y;
+                            if (ALIF) epsa += t0[u].z;
+                        }
+                        // further arrivals (rows with more than one spike)
+                        for (int cc = (c0[u] >= 0 ? c0[u] + 1 : ns); cc < ns; ++cc) {
                             const int a = sp[cc] + dl;
-                            if (a <= a0) continue;
                             if (a > r_end) break;
                             const long long qi = qa + (long long)a * N + j;
                             if (ALIF) {
@@ -924,6 +949,48 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
     float *zk_nxt = n.zk + (long long)(par ^ 1) * n.B * N;
     const float kU = exp2f(n.log2_kappa * (float)U);
     const bool upd = n.out_mask[j] != 0;
+    if ((K & 3) == 0) {
+        // four readouts per lane (float4 rows; K % 4 == 0 keeps every row
+        // 16-byte aligned), the neuron's spikes scanned once per 128 readouts
+        for (int k0 = 0; k0 < K; k0 += 128) {
+            const int k = k0 + 4 * lane;
+            const bool has_k = k < K;
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int b = 0; b < n.B; ++b) {
+                const float z0 = zk_cur[(long long)b * N + j];
+                const float *Eb = n.Ebar_win + (long long)b * U * K + k;
+                float4 gb = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (has_k) {
+                    const float4 cw = *reinterpret_cast<const float4 *>(n.Cwin + b * K + k);
+                    gb = make_float4(z0 * cw.x, z0 * cw.y, z0 * cw.z, z0 * cw.w);
+                }
+                float zn = kU * z0;
+                for_each_spike(src_words_c(n, b, n.n_in + (int)j), n.RW, a0 + 1, r_end, [&](int st) {
+                    if (has_k) {
+                        const float4 e = *reinterpret_cast<const float4 *>(Eb + (long long)(st - a0 - 1) * K);
+                        gb.x += e.x; gb.y += e.y; gb.z += e.z; gb.w += e.w;
+                    }
+                    zn += exp2f(n.log2_kappa * (float)(r_end - st));
+                });
+                g.x += gb.x; g.y += gb.y; g.z += gb.z; g.w += gb.w;
+                if (k0 == 0 && lane == 0) zk_nxt[(long long)b * N + j] = zn;
+            }
+            if (upd && has_k) {
+                const float s = n.lr * n.inv_B;
+                float4 *wp = reinterpret_cast<float4 *>(n.w_out + j * K + k);
+                float4 w = *wp;
+                w.x -= s * g.x; w.y -= s * g.y; w.z -= s * g.z; w.w -= s * g.w;
+                *wp = w;
+                if (n.record_grad) {
+                    float4 *gp = reinterpret_cast<float4 *>(n.grad_out + j * K + k);
+                    float4 gg = *gp;
+                    gg.x += n.inv_B * g.x; gg.y += n.inv_B * g.y; gg.z += n.inv_B * g.z; gg.w += n.inv_B * g.w;
+                    *gp = gg;
+                }
+            }
+        }
+        return;
+    }
     for (int k0 = 0; k0 < K; k0 += 32) {
         const int k = k0 + lane;
         const bool has_k = k < K;
