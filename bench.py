@@ -71,7 +71,7 @@ def measured_peaks():
 
 
 def recorded_traffic():
-    """DRAM bytes of one window pass (active + idle launches) at full size,
+    """DRAM bytes of one window pass (its two launches) at full size,
     from the committed ncu summary, if it was taken on the current kernel
     source (sha256 recorded in the summary); else None."""
     try:
@@ -344,11 +344,11 @@ def _run_ours(args, rank, world, local):
                       "BF16 traces: reported in DESIGN.md",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "window_pass_kernel (active + idle rows, one pair per update window)",
+                     "kernel": "window_pass_kernel (spiking-row and idle-row launches per update window)",
                      "bytes_per_event": bytes_per_event,
                      "stream_bytes_per_window": nnz * bytes_per_event,
                      "algorithmic_bytes_per_window": (events * bytes_per_event / windows) if windows else None,
-                     "traffic_unit": "DRAM bytes per window pass (active + idle launches)",
+                     "traffic_unit": "DRAM bytes per window pass (both launches)",
                      "peak_source": f"{peak_src} (hbm_gbs)",
                      "trace_ms_per_step": trace_ms / K, "trace_launches_per_step": trace_launches / K},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -42,6 +42,10 @@ struct eprop_net {
     int g_T = -1;
     int have_inputs = 0;
     int own_stream = 0;
+    // the readout work of a call runs on a second stream, forked from and
+    // joined back into st by events (also inside a captured graph)
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float *tmp_w = nullptr, *tmp_g = nullptr;
     std::vector<cudaEvent_t> ev;        // [2 * windows] trace timing events
     long long launches = 0, trace_launches = 0, windows = 0;
@@ -243,6 +247,15 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             return fail(nullptr, EPROP_ECUDA, "cannot create a stream for graph capture");
         }
         net->own_stream = 1;
+    }
+    if (cudaStreamCreateWithFlags(&net->st2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (net->ev_fork) cudaEventDestroy(net->ev_fork);
+        if (net->st2) cudaStreamDestroy(net->st2);
+        if (net->own_stream) cudaStreamDestroy(net->st);
+        delete net;
+        return fail(nullptr, EPROP_ECUDA, "cannot create the readout stream");
     }
     Net &n = net->n;
     memset(&n, 0, sizeof(n));
@@ -563,10 +576,36 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             net->ev.push_back(e);
         }
     }
+    // Readout work (the per-step readout sum and error, the window's readout
+    // weight update) reads the step's spike list and W_out and feeds only the
+    // window-end kernels, so it runs on the second stream beside delivery and
+    // the next neuron updates; the weight update is forked after the tables
+    // kernel, which reads W_out as the feedback matrix when B is symmetric,
+    // and overlaps the window pass.  Joins: before the error filter and tables
+    // of a window (they read its errors), before the rollover (it clears the
+    // spike bits the weight update reads), and at the end of the call.  With
+    // a predictor attached everything stays on one stream (the prediction
+    // feeds the step's learning signal), and so it does when the spike-list
+    // ring is not longer than the update window (batched form, RS = 2): a
+    // readout may then trail the neuron updates by at most U - 1 steps
+    // without its list slot being reused.
+    const bool fork = n.pred_mode == 0 && n.RS > n.U;
+    cudaStream_t sr = fork ? net->st2 : st;
+    auto fork_readout = [&]() {
+        if (!fork) return;
+        cudaEventRecord(net->ev_fork, st);
+        cudaStreamWaitEvent(net->st2, net->ev_fork, 0);
+    };
+    auto join_readout = [&]() {
+        if (!fork) return;
+        cudaEventRecord(net->ev_join, net->st2);
+        cudaStreamWaitEvent(st, net->ev_join, 0);
+    };
     for (int i = 1; i <= T; ++i) {
         if (c.n_in > 0) { eprop::launch_inject(n, i, (int)net->max_in_per_step, st); L += 1; }
         eprop::launch_neuron(n, i, net->sm_count, st);
-        eprop::launch_readout(n, i, net->sm_count, st);
+        fork_readout();
+        eprop::launch_readout(n, i, net->sm_count, sr);
         if (n.pred_mode) {
             eprop::launch_pred_input(n, i, st);
             L += 1;
@@ -579,9 +618,13 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         eprop::launch_deliver(n, i, deliver_rows, st);
         L += 3;
         if (i % U == 0) {
+            join_readout();
             eprop::launch_filter_error(n, i, st);
             eprop::launch_tables(n, i, st);
-            L += 2;
+            // after the tables: with symmetric feedback B is W_out itself
+            fork_readout();
+            eprop::launch_readout_weights(n, i, sr);
+            L += 3;
             if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin], st, cudaEventRecordExternal);
             if (net->trace_mode == 1) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
@@ -594,12 +637,12 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
                 LT += 2;
             }
             if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin + 1], st, cudaEventRecordExternal);
-            eprop::launch_readout_weights(n, i, st);
-            L += 1;
+            join_readout();
             if (i < T || n.has_state) { eprop::launch_rollover(n, i, st); L += 1; }
             nwin += 1;
         }
     }
+    join_readout();
     if (!c.continuous && n.has_state && !n.dense) {
         eprop::launch_flush(n, T, nullptr, nullptr, 0, n.nnz, 1, net->sm_count, st);
         L += 1;
@@ -802,6 +845,14 @@ extern "C" eprop_status eprop_autotune(eprop_net *net, eprop_tune_result *out) {
         if (r == cudaSuccess && same_layout(net->win_allocs, win_sizes)) {
             o = win_off0;
             r = copy_allocs(net->win_allocs, scratch, o, 1, net->st);
+        } else {
+            // another trace form's layout: the form only changes before the
+            // first call, when the window buffers still hold their initial
+            // zeros, so that is the state to put back
+            for (const DevAlloc &a : net->win_allocs) {
+                if (r != cudaSuccess) break;
+                r = cudaMemsetAsync(a.p, 0, a.bytes, net->st);
+            }
         }
         net->t_abs = h_t_abs;
         net->r_base = h_r_base;
@@ -1043,6 +1094,9 @@ extern "C" void eprop_destroy(eprop_net *net) {
     free_all(net->in_allocs);
     free_all(net->win_allocs);
     free_all(net->fixed_allocs);
+    if (net->ev_fork) cudaEventDestroy(net->ev_fork);
+    if (net->ev_join) cudaEventDestroy(net->ev_join);
+    if (net->st2) cudaStreamDestroy(net->st2);
     if (net->own_stream) cudaStreamDestroy(net->st);
     delete net;
 }

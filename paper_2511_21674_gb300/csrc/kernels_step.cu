@@ -210,9 +210,6 @@ __device__ void readout_finish(const Net &n, int i, int b) {
     const int a0 = win_start(n, r);
     const long long bk = (long long)b * n.n_out + k;
     float *E = n.E_win + ((long long)b * n.U + (r - a0 - 1)) * n.n_out;
-    // the list slot of step r + 1 was last used RS steps ago; every reader of
-    // it has finished (RS = U + D + 1 covers the window's trace launches)
-    if (threadIdx.x < kBkt) n.list_cnt[list_index(n, b, (r + 1) % n.RS) + threadIdx.x] = 0;
     if (i > n.lengths[b]) {      // after the sample's end: no error, no output
         if (has_k) {
             E[k] = 0.0f;
@@ -400,6 +397,13 @@ __global__ void __launch_bounds__(256, STATE ? 2 : 4) deliver_kernel(Net n, int 
     __shared__ unsigned long long ev_block;
     __shared__ long long ring_off[kMaxDelay + 1];
     const int b = blockIdx.y;
+    // the list slot of step r + 1 (filled by the next neuron update) was last
+    // used RS steps ago; every reader of it has finished: the delivery and
+    // window kernels of that step come earlier on this stream, its readout
+    // before the last window end (RS = U + D + 1 > U), and with RS = 2 the
+    // readout runs on this stream
+    if (blockIdx.x == 0 && threadIdx.x < kBkt)
+        n.list_cnt[list_index(n, b, (run_step(n, i) + 1) % n.RS) + threadIdx.x] = 0;
     if (i > n.lengths[b]) return;            // whole block: same sample
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // without carried state the trace stream is not staged: stages are the
@@ -426,25 +430,34 @@ __global__ void __launch_bounds__(256, STATE ? 2 : 4) deliver_kernel(Net n, int 
     const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
     const int nw = gridDim.x * (blockDim.x >> 5);
     // producer cursor (warp-uniform)
+    // work items: (spiking row, one of kDParts equal parts of its synapses),
+    // dealt round-robin to the warps; a step has about as many spiking rows
+    // as there are warps, and whole rows would leave most warps idle while
+    // a few finish a second row
+    constexpr int kDParts = 4;
     int prow = gw;
     long long pq = 0, pre = 0;
     int psrc = -1, pfirst = 0;
     RowInfo rinfo;
     unsigned vmask = 0;
-    for (int k = 0; k < kDStages; ++k) {
-        bool ok = true;
+    auto next_item = [&]() -> bool {
         while (pq >= pre) {
-            if (prow >= bs.total) { ok = false; break; }
-            psrc = bucket_entry(n, ids, bs, prow);
-            pq = n.row_ptr[psrc];
-            pre = n.row_ptr[psrc + 1];
+            if (prow >= bs.total * kDParts) return false;
+            const int row = prow / kDParts, part = prow % kDParts;
+            psrc = bucket_entry(n, ids, bs, row);
+            const long long rb = n.row_ptr[psrc], len = n.row_ptr[psrc + 1] - rb;
+            pq = rb + len * part / kDParts;
+            pre = rb + len * (part + 1) / kDParts;
             prow += nw;
             pfirst = 1;
             if (STATE && pre > pq && lane >= 1 && lane <= n.D)
                 rinfo = row_info(n, src_words(n, b, psrc), n.anchor_t[(long long)b * n.n_src + psrc],
                                  n.anchor_z[(long long)b * n.n_src + psrc], a0, lane, false);
         }
-        if (!ok) break;
+        return true;
+    };
+    for (int k = 0; k < kDStages; ++k) {
+        if (!next_item()) break;
         const int cnt = (int)min((long long)kChunk, pre - pq);
         if (STATE && lane >= 1 && lane <= n.D) info[warp][k][lane] = rinfo;
         if (lane == 0) {
@@ -532,19 +545,7 @@ __global__ void __launch_bounds__(256, STATE ? 2 : 4) deliver_kernel(Net n, int 
         __syncwarp();
         // refill stage k with the next chunk
         vmask &= ~(1u << k);
-        bool ok = true;
-        while (pq >= pre) {
-            if (prow >= bs.total) { ok = false; break; }
-            psrc = bucket_entry(n, ids, bs, prow);
-            pq = n.row_ptr[psrc];
-            pre = n.row_ptr[psrc + 1];
-            prow += nw;
-            pfirst = 1;
-            if (STATE && pre > pq && lane >= 1 && lane <= n.D)
-                rinfo = row_info(n, src_words(n, b, psrc), n.anchor_t[(long long)b * n.n_src + psrc],
-                                 n.anchor_z[(long long)b * n.n_src + psrc], a0, lane, false);
-        }
-        if (ok) {
+        if (next_item()) {
             const int cnt = (int)min((long long)kChunk, pre - pq);
             if (STATE && lane >= 1 && lane <= n.D) info[warp][k][lane] = rinfo;
             __syncwarp();

@@ -626,27 +626,46 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
 // coefficients (G += c . x, x <- Phi x); each arrival a in the window adds
 // Q(a) to G and Pe(a), Pa(a) to the traces (event-driven weight update from
 // the archived postsynaptic history, Sec. "From time-driven to event-driven
-// e-prop"; the per-window tables stand for that history).
-// ACTIVE = true: rows with a spike whose arrival can fall in the window,
-// taken from the per-step spike lists in ascending emission step (the row
-// belongs to its first such spike), so the table slabs in use stay in L2;
-// ACTIVE = false: all other rows, in index order (state advance only).
-// Per warp a kTStages-deep pipeline of bulk copies brings the (j|d, w, ebar)
-// streams of the next chunks into shared memory while the current chunk is
-// advanced; what stays on the critical path are the targets' window
-// coefficients (L2-resident) and, in the active pass, the table entries.
+// e-prop"; the per-window tables stand for that history).  Two launches:
+//   kPassFirst: rows with a spike whose arrival can fall in the window,
+//     taken from the per-step spike lists in ascending emission step (the
+//     row belongs to its first such spike), so the table slabs in use stay
+//     in L2: the coefficient step and every arrival of the window (the
+//     first one's table entry loaded with the rest of the synapse batch);
+//   kPassIdle: all other rows, in index order (coefficient step only).
+// Warps take work items in batches (one atomic per batch; the lanes resolve
+// and filter the items in parallel) and advance the accepted rows in item
+// order: 32 rows per batch in the idle launch, one spike-list item per
+// batch in the spiking-row launch, whose warps in flight must stay within
+// about one emission step (larger batches spread them over many steps,
+// whose table slabs then no longer fit in L2: measured slower).  Per warp a kPStages-deep pipeline of bulk copies brings
+// the (j|d, w, ebar) streams of the next chunks into shared memory while
+// the current chunk is advanced; what stays on the critical path are the
+// targets' window coefficients and the table entries (L2).
 // two stages per warp: enough copies in flight for the streams, and the
 // smaller shared-memory carve-out leaves more L1 for the coefficient and
 // table lookups (measured faster than three or four stages)
 constexpr int kPStages = 2;
+constexpr int kPassIdle = 0, kPassFirst = 1;
 
-template <bool ALIF, bool ACTIVE, bool TB>
+// table entry (Q, Pe, Pa) of one arrival (Pa = 0 for LIF)
+template <bool ALIF>
+__device__ __forceinline__ float4 load_table(const Net &n, long long qi) {
+    if (ALIF) return __ldg(reinterpret_cast<const float4 *>(n.qp) + qi);
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qi);
+    return make_float4(t.x, t.y, 0.f, 0.f);
+}
+
+template <bool ALIF, int MODE, bool TB>
 __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
+    constexpr bool LISTS = MODE != kPassIdle;        // work items from the spike lists
+    constexpr int kBatch = LISTS ? 1 : 32;           // work items per fetch
+    constexpr unsigned kFull = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ uint64_t bars[8][kPStages];
     __shared__ StageDesc desc[8][kPStages];
     __shared__ float zbs[8][kPStages][kMaxDelay + 1];
-    __shared__ int spk[8][ACTIVE ? kPStages : 1][kSpikeCap];
+    __shared__ int spk[8][LISTS ? kPStages : 1][kSpikeCap];
     __shared__ int nspk[8][kPStages];
     __shared__ int rspk[8][kSpikeCap];          // the producer's current row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -658,92 +677,136 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
     const int s_lo = max(a0 + 1 - n.D, 1);
     const int s_hi = r_end - 1;
     const int nsteps = s_hi - s_lo + 1;
-    if (ACTIVE && nsteps <= 0) return;
-    if (ACTIVE)
+    if (LISTS && nsteps <= 0) return;
+    if (LISTS)
         for (int k = threadIdx.x; k <= nsteps; k += blockDim.x) off[k] = n.win_off[k];
     if (lane < kPStages) mbar_init(&bars[warp][lane], 1);
     fence_mbar_init();
     __syncthreads();
-    const long long total = ACTIVE ? off[nsteps] : (long long)n.n_src;
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long total = LISTS ? off[nsteps] : (long long)n.n_src;
     const float step = n.lr * n.inv_B;
     const long long qa = (long long)(-a0 - 1) * N;     // table index = qa + a * N + j
-    // producer cursor (warp-uniform): work item, current row and its range;
-    // items are handed out in order by a counter, so the warps in flight
-    // stay within about one emission step (their table slabs stay in L2)
+    // work items are handed out in order by a counter, so the warps in
+    // flight stay within about one emission step (their table slabs stay
+    // in L2)
     unsigned long long *ctr =
-        reinterpret_cast<unsigned long long *>(n.win_off + n.U + n.D + 2) + (ACTIVE ? 0 : 1);
-    long long pit = 0;
+        reinterpret_cast<unsigned long long *>(n.win_off + n.U + n.D + 2) + (MODE == kPassFirst ? 0 : 1);
+    // candidates of the current batch: lane l < kBatch holds item base + l
+    // (its row, emission step and synapse range); amask = accepted rows not
+    // yet taken
+    int csrc = 0, cstep = s_lo;
+    long long crb = 0, cre = 0;
+    unsigned amask = 0;
+    bool drained = false;
+    // producer cursor (warp-uniform): current row and its remaining range
     long long pq = 0, pre = 0;
     int psrc = -1, ps = s_lo, pns = 0;
     float pzb = 0.f;            // lane d: zbar at a0 of the row's delay-d synapses
     unsigned vmask = 0;
-    (void)nw;
-    auto next_row = [&]() -> bool {
-        while (pq >= pre) {
-            {
-                long long v = 0;
-                if (lane == 0) v = (long long)atomicAdd(ctr, 1ULL);
-                pit = __shfl_sync(0xffffffffu, v, 0);
-            }
-            if (pit >= total) return false;
-            int src, s = s_lo;
-            if (ACTIVE) {
-                int lo = 0, hi = nsteps;
+    auto refill = [&]() -> bool {
+        long long base = 0;
+        if (lane == 0) base = (long long)atomicAdd(ctr, (unsigned long long)kBatch);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= total) {
+            drained = true;
+            return false;
+        }
+        const long long it = base + lane;
+        const bool valid = lane < kBatch && it < total;
+        int src = 0, s = s_lo;
+        if (LISTS) {
+            int lo = 0;
+            if (valid) {
+                int hi = nsteps;
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
-                    if (off[mid] <= pit) lo = mid; else hi = mid;
+                    if (off[mid] <= it) lo = mid; else hi = mid;
                 }
-                s = s_lo + lo;
-                const long long li = list_index(n, 0, s % n.RS);
+            }
+            s = s_lo + lo;
+            // list entries, one emission step at a time (a batch spans few)
+            const int s_first = __shfl_sync(kFull, s, 0);
+            const int s_last = __reduce_max_sync(kFull, valid ? s : s_first);
+            for (int ss = s_first; ss <= s_last; ++ss) {
+                const long long li = list_index(n, 0, ss % n.RS);
                 const BucketScan bs = bucket_scan(n.list_cnt + li);
-                src = bucket_entry(n, n.list_ids + li * n.list_cap, bs, (int)(pit - off[lo]));
-            } else {
-                src = (int)pit;
+                const long long r = it - off[ss - s_lo];      // entry index (lanes of step ss)
+                int bk = 0;                                   // buckets with incl <= r
+#pragma unroll
+                for (int w = 16; w > 0; w >>= 1)
+                    if ((long long)__shfl_sync(kFull, bs.incl, bk + w - 1) <= r) bk += w;
+                const int prev = __shfl_sync(kFull, bs.incl, bk > 0 ? bk - 1 : 0);
+                if (valid && s == ss)
+                    src = n.list_ids[(li + bk) * n.list_cap + (r - (bk > 0 ? prev : 0))];
             }
-            const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
-            if (re <= rb) continue;
-            const uint32_t *words = src_words_c(n, 0, src);
-            if (ACTIVE) {
-                if (any_spike(words, n.RW, s_lo, s - 1)) continue;     // another item owns the row
-            } else {
-                if (nsteps > 0 && any_spike(words, n.RW, s_lo, s_hi)) continue;   // active pass
-            }
-            if (ACTIVE) {
-                int ns = 0;
-                if (lane == 0) {         // the row's spikes in [s, s_hi], ascending
-                    const int mask = n.RW * 32 - 1;
-                    int r = s;
-                    while (r <= s_hi) {
-                        const int p = r & mask;
-                        const int bit = p & 31;
-                        const int span = min(31 - bit, s_hi - r);
-                        uint32_t m = words[p >> 5] >> bit;
-                        if (span < 31) m &= (2u << span) - 1u;
-                        while (m) {
-                            if (ns < kSpikeCap) rspk[warp][ns] = r + __ffs(m) - 1;
-                            ++ns;
-                            m &= m - 1;
-                        }
-                        r += span + 1;
-                    }
-                }
-                pns = __shfl_sync(0xffffffffu, ns, 0);
-            }
-            pzb = (lane >= 1 && lane <= n.D)
-                      ? row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false).zbar_a0
-                      : 0.f;
-            psrc = src;
-            ps = s;
-            pq = rb;
-            pre = re;
+        } else {
+            src = valid ? (int)it : 0;
         }
+        bool ok = false;
+        long long rb = 0, re = 0;
+        if (valid) {
+            rb = n.row_ptr[src];
+            re = n.row_ptr[src + 1];
+            if (re > rb) {
+                const uint32_t *words = src_words_c(n, 0, src);
+                if (MODE == kPassIdle)        // rows of the list launch excluded
+                    ok = !(nsteps > 0 && any_spike(words, n.RW, s_lo, s_hi));
+                else                          // the row's first spike of the window
+                    ok = !any_spike(words, n.RW, s_lo, s - 1);
+            }
+        }
+        csrc = src;
+        cstep = s;
+        crb = rb;
+        cre = re;
+        amask = __ballot_sync(kFull, ok);
+        return true;
+    };
+    auto next_row = [&]() -> bool {
+        if (pq < pre) return true;
+        while (amask == 0)
+            if (drained || !refill()) return false;
+        const int l = __ffs(amask) - 1;
+        amask &= amask - 1;
+        const int src = __shfl_sync(kFull, csrc, l);
+        const int s = __shfl_sync(kFull, cstep, l);
+        const long long rb = __shfl_sync(kFull, crb, l), re = __shfl_sync(kFull, cre, l);
+        const uint32_t *words = src_words_c(n, 0, src);
+        if (LISTS) {
+            int ns = 0;
+            if (lane == 0) {         // the row's spikes of the window, ascending
+                const int mask = n.RW * 32 - 1;
+                int r = s;
+                while (r <= s_hi) {
+                    const int p = r & mask;
+                    const int bit = p & 31;
+                    const int span = min(31 - bit, s_hi - r);
+                    uint32_t m = words[p >> 5] >> bit;
+                    if (span < 31) m &= (2u << span) - 1u;
+                    while (m) {
+                        if (ns < kSpikeCap) rspk[warp][ns] = r + __ffs(m) - 1;
+                        ++ns;
+                        m &= m - 1;
+                    }
+                    r += span + 1;
+                }
+            }
+            __syncwarp();
+            pns = __shfl_sync(kFull, ns, 0);
+        }
+        pzb = (lane >= 1 && lane <= n.D)
+                  ? row_info(n, words, n.anchor_t[src], n.anchor_z[src], a0, lane, false).zbar_a0
+                  : 0.f;
+        psrc = src;
+        ps = s;
+        pq = rb;
+        pre = re;
         return true;
     };
     auto produce = [&](int k) {
         const int cnt = (int)min((long long)kChunk, pre - pq);
         if (lane <= n.D) zbs[warp][k][lane] = pzb;
-        if (ACTIVE) {
+        if (LISTS) {
             for (int c = lane; c < min(pns, kSpikeCap); c += 32) spk[warp][k][c] = rspk[warp][c];
             if (lane == 0) nspk[warp][k] = pns;
         }
@@ -772,9 +835,9 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
         }
         const StageDesc d = desc[warp][k];
         const StageBuf &sb = buf[k];
-        const int ns = ACTIVE ? nspk[warp][k] : 0;
+        const int ns = LISTS ? nspk[warp][k] : 0;
         const bool listed = ns <= kSpikeCap;
-        const int *sp = spk[warp][ACTIVE ? k : 0];
+        const int *sp = spk[warp][LISTS ? k : 0];
         const float *zrow = zbs[warp][k];
         // chunk-relative addressing: shared offsets and global bases of the chunk
         const int o4 = (int)(d.q0 - d.q_al), o2 = (int)(d.q0 - d.q_al2);
@@ -795,31 +858,23 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                 const int idx = lane + 32 * (h + u);
                 const bool in = idx < d.n;
                 td[u] = in ? sb.td[o4 + idx] : 0u;
-                zr[u] = zrow[td[u] >> 24];
+                const int dl = (int)(td[u] >> 24);
                 wv[u] = in ? sb.w[o4 + idx] : 0.f;
                 if (TB) eb[u] = in ? __bfloat162float(__ushort_as_bfloat16(
                                          reinterpret_cast<const uint16_t *>(sb.tr)[o2 + idx])) : 0.f;
                 else eb[u] = in ? reinterpret_cast<const float *>(sb.tr)[o4 + idx] : 0.f;
-                ep[u] = (ALIF && in) ? load_trace(n.epsa, d.q0 + idx, TB) : 0.f;
-                live[u] = in && (ACTIVE || zr[u] != 0.f || eb[u] != 0.f || ep[u] != 0.f);
-                if (live[u]) cf[u] = load_coef<ALIF>(n, td[u] & 0xFFFFFFu, 0);
                 c0[u] = -1;
                 t0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ACTIVE && listed && in) {
-                    const int dl = (int)(td[u] >> 24);
-                    int cc = 0;
-                    while (cc < ns && sp[cc] + dl <= a0) ++cc;
-                    if (cc < ns && sp[cc] + dl <= r_end) {
-                        c0[u] = cc;
-                        const long long qi = qa + (long long)(sp[cc] + dl) * N + (td[u] & 0xFFFFFFu);
-                        if (ALIF) {
-                            t0[u] = __ldg(reinterpret_cast<const float4 *>(n.qp) + qi);
-                        } else {
-                            const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qi);
-                            t0[u] = make_float4(t.x, t.y, 0.f, 0.f);
-                        }
-                    }
+                int cc = 0;
+                if (LISTS && listed && in) {
+                    while (cc < ns && sp[cc] + dl <= a0) ++cc;   // first arrival in the window
+                    if (cc < ns && sp[cc] + dl <= r_end) c0[u] = cc;
                 }
+                zr[u] = zrow[dl];
+                ep[u] = (ALIF && in) ? load_trace(n.epsa, d.q0 + idx, TB) : 0.f;
+                live[u] = in && (LISTS || zr[u] != 0.f || eb[u] != 0.f || ep[u] != 0.f);
+                if (live[u]) cf[u] = load_coef<ALIF>(n, td[u] & 0xFFFFFFu, 0);
+                if (c0[u] >= 0) t0[u] = load_table<ALIF>(n, qa + (long long)(sp[cc] + dl) * N + (td[u] & 0xFFFFFFu));
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
@@ -829,7 +884,7 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                 const int dl = (int)(td[u] >> 24);
                 float G = 0.f, zbar = zr[u], ebar = eb[u], epsa = ep[u];
                 apply_coef<ALIF>(n, cf[u], zbar, epsa, ebar, G);
-                if (ACTIVE) {
+                if (LISTS) {
                     if (listed) {
                         if (c0[u] >= 0) {
                             G += t0[u].x;
@@ -840,16 +895,13 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                         for (int cc = (c0[u] >= 0 ? c0[u] + 1 : ns); cc < ns; ++cc) {
                             const int a = sp[cc] + dl;
                             if (a > r_end) break;
-                            const long long qi = qa + (long long)a * N + j;
-                            if (ALIF) {
-                                const float4 t = __ldg(reinterpret_cast<const float4 *>(n.qp) + qi);
-                                G += t.x; ebar += t.y; epsa += t.z;
-                            } else {
-                                const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qi);
-                                G += t.x; ebar += t.y;
-                            }
+                            const float4 t = load_table<ALIF>(n, qa + (long long)a * N + j);
+                            G += t.x;
+                            ebar += t.y;
+                            if (ALIF) epsa += t.z;
                         }
-                    } else {            // rows with more spikes than the cache holds
+                    } else {
+                        // rows with more spikes than the cache holds
                         G += scan_arrivals<ALIF>(n, src_words_c(n, 0, d.src), max(d.row, a0 + 1 - dl),
                                                  r_end - dl, dl, qa + j, ebar, epsa);
                     }
@@ -951,13 +1003,27 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
     const bool upd = n.out_mask[j] != 0;
     if ((K & 3) == 0) {
         // four readouts per lane (float4 rows; K % 4 == 0 keeps every row
-        // 16-byte aligned), the neuron's spikes scanned once per 128 readouts
+        // 16-byte aligned).  The weight row is requested first and the
+        // window's spike words one per lane, so the neuron's memory round
+        // trips overlap instead of following one another.
+        const int mask = n.RW * 32 - 1;
+        const int base = (a0 + 1) & ~31;                 // step of the first word's bit 0
+        const int nwd = (r_end - base) / 32 + 1;         // words covering a0+1 .. r_end
+        const float s = n.lr * n.inv_B;
         for (int k0 = 0; k0 < K; k0 += 128) {
             const int k = k0 + 4 * lane;
             const bool has_k = k < K;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f), gg = w;
+            float4 *wp = reinterpret_cast<float4 *>(n.w_out + j * K + k);
+            float4 *gp = reinterpret_cast<float4 *>(n.grad_out + j * K + k);
+            if (upd && has_k) {
+                w = *wp;
+                if (n.record_grad) gg = *gp;
+            }
             float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int b = 0; b < n.B; ++b) {
                 const float z0 = zk_cur[(long long)b * N + j];
+                const uint32_t *words = src_words_c(n, b, n.n_in + (int)j);
                 const float *Eb = n.Ebar_win + (long long)b * U * K + k;
                 float4 gb = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (has_k) {
@@ -965,25 +1031,33 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
                     gb = make_float4(z0 * cw.x, z0 * cw.y, z0 * cw.z, z0 * cw.w);
                 }
                 float zn = kU * z0;
-                for_each_spike(src_words_c(n, b, n.n_in + (int)j), n.RW, a0 + 1, r_end, [&](int st) {
-                    if (has_k) {
-                        const float4 e = *reinterpret_cast<const float4 *>(Eb + (long long)(st - a0 - 1) * K);
-                        gb.x += e.x; gb.y += e.y; gb.z += e.z; gb.w += e.w;
+                for (int g0 = 0; g0 < nwd; g0 += 32) {
+                    const int st0 = base + 32 * (g0 + lane);     // this lane's word
+                    const uint32_t wd = g0 + lane < nwd ? words[(st0 & mask) >> 5] : 0u;
+                    for (int l = 0; l < min(32, nwd - g0); ++l) {
+                        const int sb = base + 32 * (g0 + l);
+                        uint32_t m = __shfl_sync(0xffffffffu, wd, l);
+                        const int lo = max(a0 + 1 - sb, 0), hi = min(r_end - sb, 31);
+                        m = (m >> lo) << lo;
+                        if (hi < 31) m &= (2u << hi) - 1u;
+                        while (m) {
+                            const int st = sb + __ffs(m) - 1;
+                            m &= m - 1;
+                            if (has_k) {
+                                const float4 e = *reinterpret_cast<const float4 *>(Eb + (long long)(st - a0 - 1) * K);
+                                gb.x += e.x; gb.y += e.y; gb.z += e.z; gb.w += e.w;
+                            }
+                            zn += exp2f(n.log2_kappa * (float)(r_end - st));
+                        }
                     }
-                    zn += exp2f(n.log2_kappa * (float)(r_end - st));
-                });
+                }
                 g.x += gb.x; g.y += gb.y; g.z += gb.z; g.w += gb.w;
                 if (k0 == 0 && lane == 0) zk_nxt[(long long)b * N + j] = zn;
             }
             if (upd && has_k) {
-                const float s = n.lr * n.inv_B;
-                float4 *wp = reinterpret_cast<float4 *>(n.w_out + j * K + k);
-                float4 w = *wp;
                 w.x -= s * g.x; w.y -= s * g.y; w.z -= s * g.z; w.w -= s * g.w;
                 *wp = w;
                 if (n.record_grad) {
-                    float4 *gp = reinterpret_cast<float4 *>(n.grad_out + j * K + k);
-                    float4 gg = *gp;
                     gg.x += n.inv_B * g.x; gg.y += n.inv_B * g.y; gg.z += n.inv_B * g.z; gg.w += n.inv_B * g.w;
                     *gp = gg;
                 }
@@ -1122,10 +1196,10 @@ void prepare_kernel_attributes() {
     const int tl = 200 * 1024;
 #define EPROP_PASS_ATTR(A, P, T) \
     cudaFuncSetAttribute(window_pass_kernel<A, P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl)
-    EPROP_PASS_ATTR(true, true, true); EPROP_PASS_ATTR(true, true, false);
-    EPROP_PASS_ATTR(true, false, true); EPROP_PASS_ATTR(true, false, false);
-    EPROP_PASS_ATTR(false, true, true); EPROP_PASS_ATTR(false, true, false);
-    EPROP_PASS_ATTR(false, false, true); EPROP_PASS_ATTR(false, false, false);
+#define EPROP_PASS_ATTR3(A, T) EPROP_PASS_ATTR(A, kPassIdle, T); EPROP_PASS_ATTR(A, kPassFirst, T)
+    EPROP_PASS_ATTR3(true, true); EPROP_PASS_ATTR3(true, false);
+    EPROP_PASS_ATTR3(false, true); EPROP_PASS_ATTR3(false, false);
+#undef EPROP_PASS_ATTR3
 #undef EPROP_PASS_ATTR
     cudaFuncSetAttribute(trace_window_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
@@ -1171,8 +1245,8 @@ void launch_window_pass(const Net &n, int i_end, int grid_x, cudaStream_t st) {
     const size_t sm = sb + (size_t)(n.U + n.D + 2) * sizeof(long long);
 #define EPROP_PASS(A, T)                                                  \
     do {                                                                  \
-        window_pass_kernel<A, true, T><<<grid_x, 256, sm, st>>>(n, i_end);  \
-        window_pass_kernel<A, false, T><<<grid_x, 256, sb, st>>>(n, i_end); \
+        window_pass_kernel<A, kPassFirst, T><<<grid_x, 256, sm, st>>>(n, i_end); \
+        window_pass_kernel<A, kPassIdle, T><<<grid_x, 256, sb, st>>>(n, i_end);  \
     } while (0)
     if (n.alif) {
         if (n.trace_bf16) EPROP_PASS(true, true); else EPROP_PASS(true, false);

@@ -89,6 +89,13 @@ def run_parity(W, calls=1, gpu_kw=None, check=True):
         rep["mismatches"] += mm
         rep["ambiguous"] += amb
         rep["spikes"] += int(raster.sum())
+        if s.update_interval > 0 and s.T >= s.update_interval:
+            # recurrent rows with two / three or more spikes inside one update
+            # window (arrivals after a synapse's first are summed one by one)
+            U = s.update_interval
+            cnt = raster[:, :s.T // U * U].reshape(raster.shape[0], s.T // U, U, -1).sum(axis=2)
+            rep["rows_2plus"] = rep.get("rows_2plus", 0) + int((cnt >= 2).sum())
+            rep["rows_3plus"] = rep.get("rows_3plus", 0) + int((cnt >= 3).sum())
         rep.setdefault("psi_err", 0.0)
         rep["psi_err"] = max(rep["psi_err"], P.psi_error(psi, rA, s))
         if check:
@@ -211,6 +218,7 @@ def test_million_replica_continuous_windows(tk):
     W = _replica(True, 200)
     rep = run_parity(W, calls=3, gpu_kw=dict(trace_kernel=tk))
     assert rep["events"] > 0
+    assert rep["rows_3plus"] > 0
 
 
 @pytest.mark.parametrize("tk", STATE_KERNELS)
