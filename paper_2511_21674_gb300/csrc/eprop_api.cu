@@ -586,9 +586,10 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     // spike bits the weight update reads), and at the end of the call.  With
     // a predictor attached everything stays on one stream (the prediction
     // feeds the step's learning signal), and so it does when the spike-list
-    // ring is not longer than the update window (batched form, RS = 2): a
-    // readout may then trail the neuron updates by at most U - 1 steps
-    // without its list slot being reused.
+    // ring is not longer than the update window (batched form, RS = 2).
+    // Otherwise a readout trails the neuron updates by fewer than U steps
+    // (the joins at window ends), and the ring's RS > U slots keep its
+    // step's list until it has run.
     const bool fork = n.pred_mode == 0 && n.RS > n.U;
     cudaStream_t sr = fork ? net->st2 : st;
     auto fork_readout = [&]() {
