@@ -638,10 +638,11 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
 // order: 32 rows per batch in the idle launch, one spike-list item per
 // batch in the spiking-row launch, whose warps in flight must stay within
 // about one emission step (larger batches spread them over many steps,
-// whose table slabs then no longer fit in L2: measured slower).  Per warp a kPStages-deep pipeline of bulk copies brings
-// the (j|d, w, ebar) streams of the next chunks into shared memory while
-// the current chunk is advanced; what stays on the critical path are the
-// targets' window coefficients and the table entries (L2).
+// whose table slabs then no longer fit in L2: measured slower).  Per warp
+// a kPStages-deep pipeline of bulk copies brings the (j|d, w, ebar) streams
+// of the next chunks into shared memory while the current chunk is
+// advanced; what stays on the critical path are the targets' window
+// coefficients and the table entries (L2).
 // two stages per warp: enough copies in flight for the streams, and the
 // smaller shared-memory carve-out leaves more L1 for the coefficient and
 // table lookups (measured faster than three or four stages)
