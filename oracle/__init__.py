@@ -17,6 +17,10 @@ Contents
   the arrivals of its presynaptic spikes and integrates its trace over the
   left-open interval since the previous arrival; used to check that the
   event-driven and the time-driven organisations give the same gradient.
+* ``sampled_gradients``: the gradient of a sample of synapses over a run
+  whose postsynaptic history (spikes, surrogate values, readout) is given,
+  with ``error_signal`` and ``readout_magnitude``: the oracle side of the
+  sampled parity check at sizes the full simulation cannot reach.
 * ``build()``: compiles the C oracle with gcc into ``oracle/_lib``.
 
 Parity status per function: all functions are pinned by the CPU tests in
@@ -89,6 +93,9 @@ def _load():
                                             ctypes.c_int32] + [ctypes.c_void_p] * 15
             lib.oracle_eligibility_step.restype = ctypes.c_double
             lib.oracle_eligibility_step.argtypes = [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3
+            lib.oracle_synapse_sample.restype = None
+            lib.oracle_synapse_sample.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int64, ctypes.c_int32] + \
+                [ctypes.c_void_p] * 7
             lib.oracle_arrival_contrib.restype = None
             lib.oracle_arrival_contrib.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int32, ctypes.c_int32,
                                                                            ctypes.c_int64] + [ctypes.c_void_p] * 3
@@ -129,6 +136,80 @@ def arrival_contrib(spec, psi, L, U=None):
     beta = spec.beta_a if spec.neuron_model == 1 else 0.0
     lib.oracle_arrival_contrib(alpha, rho, beta, kappa_e, T, U or T, N, _p(psi), _p(L), _p(Q))
     return Q
+
+
+def error_signal(spec, y, targets, window, y_abs):
+    """Error signal E [T, K] of one sample and its sensitivity Esens [T, K]
+    from a readout y and its magnitude y_abs ([T, K]), as the C oracle forms
+    them: MSE E_k = win (y_k - y*_k) (Eq. mean-squared-error), softmax CE
+    E_k = win (pi_k - pi*_k) (Eq. softmax, Eq. cross-entropy-loss);
+    Esens = win (y_abs + |y*|) for MSE and win (pi (y_abs + sum_l pi_l
+    y_abs_l) + pi + |pi*|) for CE."""
+    y = np.asarray(y, np.float64)
+    tg = np.asarray(targets, np.float64)
+    win = np.asarray(window, np.float64)[:, None]
+    ya = np.asarray(y_abs, np.float64)
+    if spec.loss == 0:
+        return win * (y - tg), win * (ya + np.abs(tg))
+    e = np.exp(y - y.max(axis=1, keepdims=True))
+    pi = e / e.sum(axis=1, keepdims=True)
+    pya = (pi * ya).sum(axis=1, keepdims=True)
+    return win * (pi - tg), win * (pi * (ya + pya) + pi + np.abs(tg))
+
+
+def readout_magnitude(raster, w_out, kappa):
+    """y_abs [T, K] = kappa-filtered sum over the spiking neurons of |W_out|
+    (raster [T, N] of one sample; the magnitude companion of the leaky
+    readout, Eq. leaky_integrator, for the parity tolerance)."""
+    raster = np.asarray(raster)
+    wa = np.abs(np.asarray(w_out, np.float64))
+    T, K = raster.shape[0], wa.shape[1]
+    out = np.zeros((T, K))
+    acc = np.zeros(K)
+    for t in range(T):
+        idx = np.nonzero(raster[t])[0]
+        acc = kappa * acc + (wa[idx].sum(axis=0) if idx.size else 0.0)
+        out[t] = acc
+    return out
+
+
+def sampled_gradients(spec, src_spikes, delay, psi, y, targets, window, fb_rows, y_abs):
+    """Gradients of a sample of synapses over a run whose postsynaptic
+    history is given (teacher forcing), batch of one, fixed feedback B.
+
+    src_spikes [S, T]: spike of each synapse's source at emission steps 1..T
+    delay      [S]   : the synapse's delay d (arrival at emission + d)
+    psi        [S, T]: surrogate psi_j^t of each synapse's target
+    y, targets [T, K], window [T], y_abs [T, K]: readout, target, target
+               window and readout magnitude of the run
+    fb_rows    [S, K]: B_jk of each synapse's target j
+    Returns (G, mag, sens) [S]: sum_t L_j^t ebar^t over the run with
+    L_j = sum_k B_jk E_k (Eq. final-gradient) and the recursion of
+    `eligibility_step` (Eq. eligibility-vector-substituted, Eq. filtered-
+    eligibility-trace), sum_t |g^t| and sum_t Lsens_j^t |ebar^t|."""
+    lib = _load()
+    src = np.asarray(src_spikes, np.uint8)
+    S, T = src.shape
+    d = np.asarray(delay, np.int64).reshape(S)
+    E, Es = error_signal(spec, y, targets, window, y_abs)
+    fb = np.asarray(fb_rows, np.float64)
+    L = np.ascontiguousarray(fb @ E.T)
+    Ls = np.ascontiguousarray(np.abs(fb) @ Es.T)
+    arrive = np.zeros((S, T), np.uint8)
+    for s in range(S):
+        if d[s] < T:
+            arrive[s, d[s]:] = src[s, :T - d[s]]
+    psi = np.ascontiguousarray(psi, np.float64)
+    assert psi.shape == (S, T)
+    alpha = math.exp(-spec.dt / spec.tau_m)
+    rho = math.exp(-spec.dt / spec.tau_a)
+    kappa = math.exp(-spec.dt / spec.tau_out)
+    kappa_e = kappa if spec.kappa_e is None else float(spec.kappa_e)
+    beta = spec.beta_a if spec.neuron_model == 1 else 0.0
+    G, mag, sens = np.zeros(S), np.zeros(S), np.zeros(S)
+    lib.oracle_synapse_sample(alpha, rho, beta, kappa_e, S, T, _p(arrive), _p(psi), _p(L), _p(Ls),
+                              _p(G), _p(mag), _p(sens))
+    return G, mag, sens
 
 
 def arrival_magnitude(spec, ptr, col, delay, x_ptr, x_ids, lengths, raster, psi, L):

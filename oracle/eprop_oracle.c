@@ -169,6 +169,38 @@ void oracle_arrival_contrib(double alpha, double rho, double beta_a, double kapp
     }
 }
 
+/* Sampled synapses of a run whose postsynaptic history is given (teacher
+   forcing with the surrogate values and readout of another implementation):
+   each synapse s runs the recursion above over steps t = 1..T of the run
+   from a zero state (psi^0 = 0), with its arrivals arrive[s][t-1] (its
+   source's spike d steps before t), its target's psi[s][t-1] and learning
+   signal L[s][t-1], and the learning signal's sensitivity Ls[s][t-1].
+   Returns per synapse G = sum_t g^t (the gradient summed over every update
+   window of the run, batch of one), mag = sum_t |g^t| and
+   sens = sum_t Ls^t |ebar^t|, the parity condition of the sum as
+   oracle_simulate keeps it. */
+void oracle_synapse_sample(double alpha, double rho, double beta_a, double kappa_e,
+                           int64_t S, int32_t T, const uint8_t *arrive, const double *psi,
+                           const double *L, const double *Ls, double *G, double *mag,
+                           double *sens) {
+    for (int64_t s = 0; s < S; ++s) {
+        const int64_t o = s * (int64_t)T;
+        double zbar = 0.0, epsa = 0.0, ebar = 0.0, g = 0.0, m = 0.0, se = 0.0;
+        for (int32_t t = 1; t <= T; ++t) {
+            const double pp = t > 1 ? psi[o + t - 2] : 0.0;
+            const double gt = oracle_eligibility_step(alpha, rho, beta_a, kappa_e, pp, psi[o + t - 1],
+                                                      L[o + t - 1], (double)arrive[o + t - 1],
+                                                      &zbar, &epsa, &ebar);
+            g += gt;
+            m += fabs(gt);
+            se += Ls[o + t - 1] * fabs(ebar);
+        }
+        G[s] = g;
+        mag[s] = m;
+        sens[s] = se;
+    }
+}
+
 static void reset_state(const oracle_cfg *c, oracle_state *s) {
     int64_t B = c->batch, N = c->n_rec, K = c->n_out, D1 = c->max_delay + 1;
     memset(s->v, 0, sizeof(double) * B * N);
