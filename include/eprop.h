@@ -20,7 +20,11 @@
  *     stay owned by the caller.
  *   - All state is owned by the library; eprop_destroy frees it.
  *   - Work is issued asynchronously on the CUDA stream given at creation.
- *     eprop_sync waits for it and surfaces device errors.
+ *     Inside a simulate call part of it (the readout kernels) runs on a
+ *     second stream the network owns, forked from and joined back into
+ *     that stream with events, so that work the caller orders after the
+ *     call on the given stream sees all of it.  eprop_sync waits for it and
+ *     surfaces device errors.
  *   - After EPROP_ETIMEOUT or EPROP_ECUDA the network is in an error state
  *     and every further call except eprop_destroy / eprop_last_error
  *     returns EPROP_ESTATE.
@@ -148,7 +152,9 @@ typedef struct eprop_synapses {
  *   out_mask  [n_rec] 1 if neuron j projects to the readouts, else its row of
  *             W_out is held at its value and gets no gradient; NULL = all 1
  *   feedback  [n_rec][n_out] fixed random B (required iff cfg->feedback == 1)
- *   cuda_stream  cudaStream_t to issue all work on (NULL: legacy stream)
+ *   cuda_stream  cudaStream_t to issue all work on (NULL: legacy stream);
+ *             the network also creates one stream and two events of its own
+ *             (readout work, see above), freed by eprop_destroy
  * Errors: EPROP_EINVAL (inconsistent sizes, delays out of range, unsupported
  * combination), EPROP_ENOMEM, EPROP_ECUDA.  On error *out is NULL.
  * Unsupported: batch > 1 together with continuous = 1 or update_interval > 0
