@@ -340,8 +340,9 @@ def _run_ours(args, rank, world, local):
         "sim_time_per_wall_time": (T * spec.dt / 1000.0) / (ms_max / K / 1000.0),
         "events_per_step": events / K,
         "mean_rate_hz": events / K / nnz / (T * spec.dt / 1000.0),
-        "grad_error": "FP32 traces: <=1e-5 relative vs FP64 oracle (scaled replica); "
-                      "BF16 traces: reported in DESIGN.md",
+        "grad_error": "FP32 traces: within 1e-5 of each gradient's magnitude sum vs the FP64 oracle "
+                      "(scaled replicas on every synapse, this workload on 256 sampled synapses); "
+                      "BF16 traces: ~5e-4 relative L2 vs the oracle (gated at 1e-2)",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "window_pass_kernel (spiking-row and idle-row launches per update window)",
