@@ -60,7 +60,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = SO + f".tmp{os.getpid()}"
-    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    # cuBLAS serves the window's learning-signal product (a plain GEMM); the
+    # toolkit's library directory is recorded as the run path
+    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nv))), "lib64")
+    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcublas", "-Xlinker", "-rpath",
+                                                          "-Xlinker", libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -1,5 +1,6 @@
 // C ABI of libeprop (see include/eprop.h): argument checks, device memory,
 // and the launch schedule of one simulate call.
+#include <cublas_v2.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -46,6 +47,10 @@ struct eprop_net {
     // joined back into st by events (also inside a captured graph)
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the window's learning signals L = B E as one strided-batched SGEMM
+    // (FP32, no TF32), with a fixed workspace so that it can be captured
+    cublasHandle_t blas = nullptr;
+    int blas_err = 0;
     float *tmp_w = nullptr, *tmp_g = nullptr;
     std::vector<cudaEvent_t> ev;        // [2 * windows] trace timing events
     long long launches = 0, trace_launches = 0, windows = 0;
@@ -72,6 +77,14 @@ static eprop_status cuda_fail(eprop_net *net, cudaError_t e, const char *what) {
         g_create_err = m;
     }
     return e == cudaErrorMemoryAllocation ? EPROP_ENOMEM : EPROP_ECUDA;
+}
+
+static eprop_status blas_fail(eprop_net *net) {
+    const int st = net->blas_err;
+    net->blas_err = 0;
+    net->bad = 1;
+    net->err = "cuBLAS learning-signal product failed (status " + std::to_string(st) + ")";
+    return EPROP_ECUDA;
 }
 
 #define CK(net, call)                                              \
@@ -190,6 +203,7 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     WA(list_cnt, int, B * n.RS * eprop::kBkt);
     WA(psi_hist, float, B * (U + 1) * N);
     WA(E_win, float, B * U * K);
+    WA(L_win, float, B * (long long)U * N);
     WA(Ebar_win, float, B * U * K);
     WA(qp, float, B * (long long)U * N * net->qp_stride);
     WA(win_off, long long, U + D + 2 + eprop::kWorkCounters);
@@ -256,6 +270,26 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         if (net->own_stream) cudaStreamDestroy(net->st);
         delete net;
         return fail(nullptr, EPROP_ECUDA, "cannot create the readout stream");
+    }
+    {
+        // cuBLAS for the learning-signal product: plain FP32 (no TF32) and a
+        // fixed workspace, so that the product allocates nothing when a call
+        // is captured into a graph
+        void *ws = nullptr;
+        const size_t ws_bytes = (size_t)32 << 20;
+        if (cublasCreate(&net->blas) != CUBLAS_STATUS_SUCCESS ||
+            cublasSetMathMode(net->blas, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS ||
+            dalloc(net->fixed_allocs, &ws, ws_bytes) != cudaSuccess ||
+            cublasSetWorkspace(net->blas, ws, ws_bytes) != CUBLAS_STATUS_SUCCESS) {
+            if (net->blas) cublasDestroy(net->blas);
+            free_all(net->fixed_allocs);
+            cudaEventDestroy(net->ev_fork);
+            cudaEventDestroy(net->ev_join);
+            cudaStreamDestroy(net->st2);
+            if (net->own_stream) cudaStreamDestroy(net->st);
+            delete net;
+            return fail(nullptr, EPROP_ECUDA, "cannot set up cuBLAS for the learning-signal product");
+        }
     }
     Net &n = net->n;
     memset(&n, 0, sizeof(n));
@@ -621,6 +655,19 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         if (i % U == 0) {
             join_readout();
             eprop::launch_filter_error(n, i, st);
+            {
+                // L[b][u][j] = sum_k B[j][k] E[b][u][k] (Eq. final-gradient); in
+                // column-major terms C (N x U, ld N) = A^T B with A = B^T (K x N,
+                // ld K) and B = E_b (K x U, ld K), one product per sample
+                const float one = 1.0f, zero = 0.0f;
+                const int Nn = c.n_rec, Kk = c.n_out;
+                cublasStatus_t bs = cublasSetStream(net->blas, st);
+                if (bs == CUBLAS_STATUS_SUCCESS)
+                    bs = cublasSgemmStridedBatched(net->blas, CUBLAS_OP_T, CUBLAS_OP_N, Nn, U, Kk, &one, n.fb, Kk,
+                                                   0LL, n.E_win, Kk, (long long)U * Kk, &zero, n.L_win, Nn,
+                                                   (long long)U * Nn, (int)B);
+                if (bs != CUBLAS_STATUS_SUCCESS) net->blas_err = (int)bs;
+            }
             eprop::launch_tables(n, i, st);
             // after the tables: with symmetric feedback B is W_out itself
             fork_readout();
@@ -678,6 +725,10 @@ extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t 
             CK(net, cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal));
             issue_call(net, T, nullptr);
             CK(net, cudaStreamEndCapture(net->st, &g));
+            if (net->blas_err) {
+                cudaGraphDestroy(g);
+                return blas_fail(net);
+            }
             e = cudaGraphInstantiate(&net->gexec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(net, e, "cudaGraphInstantiate");
@@ -686,6 +737,7 @@ extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t 
         CK(net, cudaGraphLaunch(net->gexec, net->st));
     } else {
         issue_call(net, T, forced_raster);
+        if (net->blas_err) return blas_fail(net);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(net, e, "kernel launch");
@@ -1095,6 +1147,7 @@ extern "C" void eprop_destroy(eprop_net *net) {
     free_all(net->in_allocs);
     free_all(net->win_allocs);
     free_all(net->fixed_allocs);
+    if (net->blas) cublasDestroy(net->blas);
     if (net->ev_fork) cudaEventDestroy(net->ev_fork);
     if (net->ev_join) cudaEventDestroy(net->ev_join);
     if (net->st2) cudaStreamDestroy(net->st2);

@@ -87,26 +87,21 @@ __global__ void filter_error_kernel(Net n) {
 
 // learning-signal tables: one thread per (sample, neuron), 128 neurons per
 // block.  The window is swept backwards in chunks of steps: the chunk's
-// learning signals L^t = sum_k B_jk E_k^t (Eq. final-gradient) are formed in
-// registers from shared tiles of the block's feedback rows and of the
-// chunk's errors, then the adjoint recursion writes the per-step tables and,
-// at the window start, the window coefficients.
+// learning signals L^t = sum_k B_jk E_k^t (Eq. final-gradient; formed for
+// the whole window beforehand by one strided-batched SGEMM, L_win) are
+// loaded into registers, then the adjoint recursion writes the per-step
+// tables and, at the window start, the window coefficients.
 template <bool ALIF>
 __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     constexpr int kTC = ALIF ? 16 : 32;     // window steps per chunk
-    constexpr int kKT = 32;                 // feedback columns per shared tile
-    __shared__ __align__(16) float Bs[128][kKT + 4];     // rows 16-byte aligned, conflict-free float4
-    __shared__ __align__(16) float Es[kTC][kKT];         // the chunk's errors (zero outside it)
     const int b = blockIdx.y;
-    const int U = n.U, K = n.n_out, N = n.n_rec;
+    const int U = n.U, N = n.n_rec;
     const int r_end = run_step_w(n, i_end);
     const int a0 = r_end - U;
-    const float *E = n.E_win + (long long)b * U * K;
-    const int tid = threadIdx.x;
-    const int j0 = blockIdx.x * 128;
-    const int j = j0 + tid;
+    const int j = blockIdx.x * 128 + threadIdx.x;
     const bool act = j < N;
     const float *psi_g = n.psi_hist + (long long)b * (U + 1) * N + (act ? j : 0);
+    const float *L_g = n.L_win + (long long)b * U * N + (act ? j : 0);    // [U][N], row u - 1 = step u
     // The adjoint sweep is the per-window reduction of the gradient.  For
     // ALIF the eligibility psi (zbar - beta eps_a) is a near-cancellation of
     // two long-memory traces, so the sweep runs in FP64 there (FP32 loses up
@@ -126,50 +121,20 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     R pn = 0;
     const float psi_b = act ? psi_g[(long long)U * N] : 0.f;
     const long long qbase = ((long long)b * U) * N + j;
-    // Steps are taken backwards in chunks of kTC.  A chunk's learning
-    // signals L^t = sum_k B_jk E_k^t are formed in registers from feedback
-    // tiles staged in shared memory (coalesced rows of the block's neurons)
-    // and the window errors E (the same address for every thread); then the
-    // recursion runs over the chunk in registers.
+    // Steps are taken backwards in chunks of kTC: the chunk's psi and
+    // learning signals are loaded in one batch, then the recursion runs over
+    // the chunk in registers.
     for (int u1 = U; u1 >= 1; u1 -= kTC) {
         const int u0 = max(1, u1 - kTC + 1);            // chunk = steps u0..u1
         float Lc[kTC], Pc[kTC + 1];
 #pragma unroll
         for (int c = 0; c < kTC; ++c) {
             const int u = u1 - c;
-            Lc[c] = 0.f;
-            Pc[c] = (act && u >= u0) ? psi_g[(long long)u * N] : 0.f;
+            const bool in = act && u >= u0;
+            Lc[c] = in ? L_g[(long long)(u - 1) * N] : 0.f;
+            Pc[c] = in ? psi_g[(long long)u * N] : 0.f;
         }
         Pc[kTC] = act ? psi_g[(long long)(u0 - 1) * N] : 0.f;   // psi of the step before the chunk
-        for (int k0 = 0; k0 < K; k0 += kKT) {
-            const int kt = min(kKT, K - k0);
-            __syncthreads();
-            for (int q = tid; q < 128 * kKT; q += 128) {
-                const int r = q / kKT, cc = q % kKT;
-                const int jr = j0 + r;
-                Bs[r][cc] = (jr < N && cc < kt) ? n.fb[(long long)jr * K + k0 + cc] : 0.f;
-            }
-            for (int q = tid; q < kTC * kKT; q += 128) {
-                const int c = q / kKT, cc = q % kKT;
-                const int u = u1 - c;
-                Es[c][cc] = (u >= u0 && cc < kt) ? E[(long long)(u - 1) * K + k0 + cc] : 0.f;
-            }
-            __syncthreads();
-            // L^t for the chunk's steps: one float4 of the neuron's feedback
-            // row against one broadcast float4 of each step's errors
-#pragma unroll 2
-            for (int kk = 0; kk < kKT; kk += 4) {
-                const float4 bq = *reinterpret_cast<const float4 *>(&Bs[tid][kk]);
-#pragma unroll
-                for (int c = 0; c < kTC; ++c) {
-                    const float4 e = *reinterpret_cast<const float4 *>(&Es[c][kk]);
-                    Lc[c] = fmaf(bq.x, e.x, Lc[c]);
-                    Lc[c] = fmaf(bq.y, e.y, Lc[c]);
-                    Lc[c] = fmaf(bq.z, e.z, Lc[c]);
-                    Lc[c] = fmaf(bq.w, e.w, Lc[c]);
-                }
-            }
-        }
         if (!act) continue;
 #pragma unroll
         for (int c = 0; c < kTC; ++c) {
