@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--n-out", type=int, default=100)
     p.add_argument("--trace-dtype", default="bf16", choices=["bf16", "fp32"])
     p.add_argument("--blocks-per-sm", type=int, default=0)
+    p.add_argument("--trace-kernel", default="dense", choices=["dense", "lazy"],
+                   help="synapse-trace form: dense window pass or lazy catch-up at arrivals")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-n", type=int, default=10_000)
     p.add_argument("--cpu-sample-T", type=int, default=100)
@@ -184,7 +186,8 @@ def workload_config(args, nnz, world=1):
     return {"workload": f"million_sparse: {args.n_rec} LIF, in-degree {args.k_in} ({nnz} synapses), "
                         f"delays 1-5, ~5 Hz, {args.n_out} readouts, update window 100, continuous",
             "n_rec": args.n_rec, "k_in": args.k_in, "synapses": nnz, "T_per_step": args.T,
-            "trace_storage": args.trace_dtype, "parallelism": f"replicas{world}",
+            "trace_storage": args.trace_dtype, "trace_form": args.trace_kernel,
+            "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (synapse records ~10 GB per step)"}
 
 
@@ -259,7 +262,8 @@ def _run_ours(args, rank, world, local):
     trace_dtype = 1 if args.trace_dtype == "bf16" else 0
     net = ep.Network(spec, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], None, W["feedback"],
                      launch_mode=1, trace_dtype=trace_dtype, record_grad=0, record_raster=0,
-                     profile=1, blocks_per_sm=args.blocks_per_sm)
+                     profile=1, blocks_per_sm=args.blocks_per_sm,
+                     trace_kernel=3 if args.trace_kernel == "dense" else 1)
     nnz = int(W["col"].shape[0])
     del W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["feedback"]
     torch.cuda.empty_cache()
@@ -328,7 +332,7 @@ def _run_ours(args, rank, world, local):
     achieved = events * bytes_per_event / (trace_ms / 1000.0) / 1e9 if trace_ms > 0 else None
     # per window pass (the unit `achieved` averages over): DRAM bytes from
     # the committed ncu capture, scaled to full size (see profiles/)
-    traffic = recorded_traffic()
+    traffic = recorded_traffic() if args.trace_kernel == "dense" else None
     net.close()
     if rank != 0:
         return
@@ -345,7 +349,9 @@ def _run_ours(args, rank, world, local):
                       "BF16 traces: ~5e-4 relative L2 vs the oracle (gated at 1e-2)",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "window_pass_kernel (spiking-row and idle-row launches per update window)",
+                     "kernel": ("window_pass_kernel (spiking-row and idle-row launches per update window)"
+                                if args.trace_kernel == "dense" else
+                                "trace_window_kernel (lazy: rows with an arrival in the window)"),
                      "bytes_per_event": bytes_per_event,
                      "stream_bytes_per_window": nnz * bytes_per_event,
                      "algorithmic_bytes_per_window": (events * bytes_per_event / windows) if windows else None,

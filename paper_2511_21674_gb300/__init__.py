@@ -80,7 +80,7 @@ EXPORTS = ("eprop_create_network", "eprop_set_inputs_targets", "eprop_simulate",
            "eprop_predictor_train_step", "eprop_predictor_read", "eprop_predictor_set_params",
            "eprop_predictor_sync", "eprop_predictor_destroy", "eprop_predictor_last_error",
            "eprop_attach_predictor", "eprop_read_predictor_inputs", "eprop_autotune",
-           "eprop_predictor_set_input_scale")
+           "eprop_predictor_set_input_scale", "eprop_learning_signals")
 
 
 def load_library(path: str = LIB_PATH):
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
     lib.eprop_autotune.argtypes = [vp, ctypes.POINTER(TuneResult)]
     lib.eprop_predictor_set_input_scale.argtypes = [vp, vp]
     lib.eprop_read_predictor_inputs.argtypes = [vp, vp, i32]
+    lib.eprop_learning_signals.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp]
     void_ret = ("eprop_destroy", "eprop_last_error", "eprop_predictor_destroy", "eprop_predictor_last_error")
     for name in EXPORTS:
         if name not in void_ret:
@@ -129,6 +130,30 @@ def load_library(path: str = LIB_PATH):
     lib.eprop_predictor_num_params.restype = i64
     _lib = lib
     return lib
+
+
+def learning_signals(feedback, E, stream=None):
+    """L [batch, U, n_rec] = sum_k feedback[j, k] E[b, u, k] on the tensor
+    cores (eprop_learning_signals); feedback [n_rec, n_out] and E [batch, U,
+    n_out] are CUDA float32 tensors."""
+    import torch
+    lib = load_library()
+    if not (feedback.is_cuda and E.is_cuda):
+        raise ValueError("feedback and E must be CUDA tensors")
+    feedback = feedback.contiguous().float()
+    E = E.contiguous().float()
+    n_rec, n_out = feedback.shape
+    batch, U, k2 = E.shape
+    if k2 != n_out:
+        raise ValueError("E's last dimension must equal feedback's second")
+    L = torch.empty((batch, U, n_rec), dtype=torch.float32, device=E.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.eprop_learning_signals(feedback.data_ptr(), E.data_ptr(), L.data_ptr(), n_rec, U, n_out,
+                                    batch, stream)
+    if st != 0:
+        raise EpropError(st, lib.eprop_last_error(None).decode())
+    return L
 
 
 def make_config(spec, launch_mode: int = 1, trace_dtype: int = 0, record_grad: int = 1,

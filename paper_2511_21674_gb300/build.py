@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libeprop.so")
-SOURCES = ["eprop_api.cu", "kernels_step.cu", "kernels_window.cu", "predictor.cu"]
+SOURCES = ["eprop_api.cu", "kernels_step.cu", "kernels_window.cu", "kernels_lsig.cu", "predictor.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -60,11 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = SO + f".tmp{os.getpid()}"
-    # cuBLAS serves the window's learning-signal product (a plain GEMM); the
-    # toolkit's library directory is recorded as the run path
-    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nv))), "lib64")
-    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcublas", "-Xlinker", "-rpath",
-                                                          "-Xlinker", libdir]
+    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -1,10 +1,10 @@
 // C ABI of libeprop (see include/eprop.h): argument checks, device memory,
 // and the launch schedule of one simulate call.
-#include <cublas_v2.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -42,15 +42,12 @@ struct eprop_net {
     cudaGraphExec_t gexec = nullptr;
     int g_T = -1;
     int have_inputs = 0;
+    int have_sim = 0;                   // a simulate call ran since the last set_inputs
     int own_stream = 0;
     // the readout work of a call runs on a second stream, forked from and
     // joined back into st by events (also inside a captured graph)
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // the window's learning signals L = B E as one strided-batched SGEMM
-    // (FP32, no TF32), with a fixed workspace so that it can be captured
-    cublasHandle_t blas = nullptr;
-    int blas_err = 0;
     float *tmp_w = nullptr, *tmp_g = nullptr;
     std::vector<cudaEvent_t> ev;        // [2 * windows] trace timing events
     long long launches = 0, trace_launches = 0, windows = 0;
@@ -77,14 +74,6 @@ static eprop_status cuda_fail(eprop_net *net, cudaError_t e, const char *what) {
         g_create_err = m;
     }
     return e == cudaErrorMemoryAllocation ? EPROP_ENOMEM : EPROP_ECUDA;
-}
-
-static eprop_status blas_fail(eprop_net *net) {
-    const int st = net->blas_err;
-    net->blas_err = 0;
-    net->bad = 1;
-    net->err = "cuBLAS learning-signal product failed (status " + std::to_string(st) + ")";
-    return EPROP_ECUDA;
 }
 
 #define CK(net, call)                                              \
@@ -271,26 +260,6 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         delete net;
         return fail(nullptr, EPROP_ECUDA, "cannot create the readout stream");
     }
-    {
-        // cuBLAS for the learning-signal product: plain FP32 (no TF32) and a
-        // fixed workspace, so that the product allocates nothing when a call
-        // is captured into a graph
-        void *ws = nullptr;
-        const size_t ws_bytes = (size_t)32 << 20;
-        if (cublasCreate(&net->blas) != CUBLAS_STATUS_SUCCESS ||
-            cublasSetMathMode(net->blas, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS ||
-            dalloc(net->fixed_allocs, &ws, ws_bytes) != cudaSuccess ||
-            cublasSetWorkspace(net->blas, ws, ws_bytes) != CUBLAS_STATUS_SUCCESS) {
-            if (net->blas) cublasDestroy(net->blas);
-            free_all(net->fixed_allocs);
-            cudaEventDestroy(net->ev_fork);
-            cudaEventDestroy(net->ev_join);
-            cudaStreamDestroy(net->st2);
-            if (net->own_stream) cudaStreamDestroy(net->st);
-            delete net;
-            return fail(nullptr, EPROP_ECUDA, "cannot set up cuBLAS for the learning-signal product");
-        }
-    }
     Net &n = net->n;
     memset(&n, 0, sizeof(n));
     cudaGetDevice(&net->dev);
@@ -433,6 +402,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         }
         eprop::prepare_kernel_attributes();
         eprop::prepare_step_kernel_attributes();
+        eprop::prepare_learning_signal_attributes();
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "network set-up"); goto fail_out; }
         if (c.update_interval > 0) {
@@ -446,6 +416,10 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
 fail_out:
     free_all(net->fixed_allocs);
     free_all(net->win_allocs);
+    cudaEventDestroy(net->ev_fork);
+    cudaEventDestroy(net->ev_join);
+    cudaStreamDestroy(net->st2);
+    if (net->own_stream) cudaStreamDestroy(net->st);
     delete net;
     return s;
 }
@@ -549,6 +523,7 @@ extern "C" eprop_status eprop_set_inputs_targets(eprop_net *net, const int64_t *
     if (s != EPROP_OK) return s;
     net->T_in = T;
     net->have_inputs = 1;
+    net->have_sim = 0;                  // the recorded outputs no longer match these inputs
     return EPROP_OK;
 }
 
@@ -655,24 +630,14 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         if (i % U == 0) {
             join_readout();
             eprop::launch_filter_error(n, i, st);
-            {
-                // L[b][u][j] = sum_k B[j][k] E[b][u][k] (Eq. final-gradient); in
-                // column-major terms C (N x U, ld N) = A^T B with A = B^T (K x N,
-                // ld K) and B = E_b (K x U, ld K), one product per sample
-                const float one = 1.0f, zero = 0.0f;
-                const int Nn = c.n_rec, Kk = c.n_out;
-                cublasStatus_t bs = cublasSetStream(net->blas, st);
-                if (bs == CUBLAS_STATUS_SUCCESS)
-                    bs = cublasSgemmStridedBatched(net->blas, CUBLAS_OP_T, CUBLAS_OP_N, Nn, U, Kk, &one, n.fb, Kk,
-                                                   0LL, n.E_win, Kk, (long long)U * Kk, &zero, n.L_win, Nn,
-                                                   (long long)U * Nn, (int)B);
-                if (bs != CUBLAS_STATUS_SUCCESS) net->blas_err = (int)bs;
-            }
+            // L[b][u][j] = sum_k B[j][k] E[b][u][k] of the whole window
+            // (Eq. final-gradient), tensor cores with split TF32 operands
+            eprop::launch_learning_signals(n.fb, n.E_win, n.L_win, c.n_rec, U, c.n_out, (int)B, n.err_flags, st);
             eprop::launch_tables(n, i, st);
             // after the tables: with symmetric feedback B is W_out itself
             fork_readout();
             eprop::launch_readout_weights(n, i, sr);
-            L += 3;
+            L += 4;
             if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin], st, cudaEventRecordExternal);
             if (net->trace_mode == 1) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
@@ -725,10 +690,6 @@ extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t 
             CK(net, cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal));
             issue_call(net, T, nullptr);
             CK(net, cudaStreamEndCapture(net->st, &g));
-            if (net->blas_err) {
-                cudaGraphDestroy(g);
-                return blas_fail(net);
-            }
             e = cudaGraphInstantiate(&net->gexec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(net, e, "cudaGraphInstantiate");
@@ -737,12 +698,12 @@ extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t 
         CK(net, cudaGraphLaunch(net->gexec, net->st));
     } else {
         issue_call(net, T, forced_raster);
-        if (net->blas_err) return blas_fail(net);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(net, e, "kernel launch");
     net->t_abs += T;
     net->r_base = c.continuous ? net->r_base + T : T;
+    net->have_sim = 1;
     return EPROP_OK;
 }
 
@@ -797,7 +758,7 @@ extern "C" eprop_status eprop_readout(eprop_net *net, float *y, float *loss_per_
                                       int32_t is_device) {
     if (!net) return EPROP_EINVAL;
     if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
-    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    if (!net->have_sim) return fail(net, EPROP_ESTATE, "no simulate call since the last set_inputs");
     Net &n = net->n;
     const eprop_config &c = net->cfg;
     const long long B = c.batch, T = net->T_in, K = c.n_out, N = c.n_rec;
@@ -1032,7 +993,7 @@ extern "C" eprop_status eprop_read_predictor_inputs(eprop_net *net, float *x, in
     if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
     if (!(net->n.pred_mode & 2) || !net->n.pred_rec)
         return fail(net, EPROP_EINVAL, "recording needs a predictor attached with mode bit 1");
-    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    if (!net->have_sim) return fail(net, EPROP_ESTATE, "no simulate call since the last set_inputs");
     const long long cnt = (long long)net->cfg.batch * net->T_in * net->n.pred_in;
     CK(net, cudaMemcpyAsync(x, net->n.pred_rec, cnt * 4,
                             is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, net->st));
@@ -1057,28 +1018,37 @@ static __device__ __align__(256) unsigned char g_raster_scratch[EPROP_STATIC_RAS
 
 static constexpr int kMaxScratchDevices = 64;
 static void *g_raster_scratch_addr[kMaxScratchDevices];
+static std::mutex g_raster_scratch_mu;    // guards the address table
 
 extern "C" eprop_status eprop_readout_raster_static(eprop_net *net, uint8_t *raster, int32_t is_device) {
     if (!net || !raster) return EPROP_EINVAL;
     if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
-    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "eprop_set_inputs_targets must come first");
     if (!net->n.record_raster) return fail(net, EPROP_EINVAL, "raster needs record_raster = 1");
     const long long bytes = (long long)net->cfg.batch * net->T_in * net->cfg.n_rec;
     if (bytes > (long long)EPROP_STATIC_RASTER_BYTES)
         return fail(net, EPROP_EINVAL,
                     "raster (batch * T * n_rec bytes) exceeds EPROP_STATIC_RASTER_BYTES of static scratch");
+    if (!net->have_sim) return fail(net, EPROP_ESTATE, "no simulate call since the last set_inputs");
     int cur = -1;
     CK(net, cudaGetDevice(&cur));
     if (cur != net->dev) return fail(net, EPROP_EINVAL, "the network's device must be the current device");
     if (cur < 0 || cur >= kMaxScratchDevices) return fail(net, EPROP_EINVAL, "device ordinal out of range");
     // the scratch address of this device, resolved once with the device
-    // current (the first call may load the module: a one-time setup)
-    if (!g_raster_scratch_addr[cur]) {
-        void *a = nullptr;
-        CK(net, cudaGetSymbolAddress(&a, g_raster_scratch));
-        g_raster_scratch_addr[cur] = a;
+    // current (the first call may load the module: a one-time setup); the
+    // table is shared by every host thread, so it is read and filled under
+    // a lock.  A device reset (cudaDeviceReset) invalidates every network
+    // of that device and this address with them.
+    unsigned char *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_raster_scratch_mu);
+        if (!g_raster_scratch_addr[cur]) {
+            void *a = nullptr;
+            CK(net, cudaGetSymbolAddress(&a, g_raster_scratch));
+            g_raster_scratch_addr[cur] = a;
+        }
+        scratch = static_cast<unsigned char *>(g_raster_scratch_addr[cur]);
     }
-    unsigned char *scratch = static_cast<unsigned char *>(g_raster_scratch_addr[cur]);
     Net nn = net->n;
     nn.T = net->T_in;
     eprop::launch_unpack_raster(nn, scratch, net->st);
@@ -1089,11 +1059,46 @@ extern "C" eprop_status eprop_readout_raster_static(eprop_net *net, uint8_t *ras
     return EPROP_OK;
 }
 
+// ---- the window's learning-signal product on its own (tensor cores)
+
+// status word of the stand-alone product (bit 1: a bounded wait gave up)
+static __device__ unsigned int g_lsig_status;
+
+extern "C" eprop_status eprop_learning_signals(const float *feedback, const float *E, float *L, int32_t n_rec,
+                                               int32_t U, int32_t n_out, int32_t batch, void *cuda_stream) {
+    if (!feedback || !E || !L) return fail(nullptr, EPROP_EINVAL, "feedback, E and L are required");
+    if (n_rec < 1 || U < 1 || n_out < 1 || batch < 1 || n_out > eprop::kMaxOut || batch >= 65536)
+        return fail(nullptr, EPROP_EINVAL, "sizes out of range (1 <= n_out <= 1024, 1 <= batch < 65536)");
+    cudaPointerAttributes pa[3];
+    const void *ptrs[3] = {feedback, E, L};
+    for (int q = 0; q < 3; ++q)
+        if (cudaPointerGetAttributes(&pa[q], ptrs[q]) != cudaSuccess || pa[q].type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(nullptr, EPROP_EINVAL, "feedback, E and L must be device pointers");
+        }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const unsigned int zero = 0;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_lsig_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    unsigned int *flag = nullptr;
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&flag, g_lsig_status);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "learning-signal status");
+    eprop::prepare_learning_signal_attributes();
+    eprop::launch_learning_signals(feedback, E, L, n_rec, U, n_out, batch, flag, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "learning-signal kernel launch");
+    unsigned int h = 0;
+    e = cudaMemcpyFromSymbolAsync(&h, g_lsig_status, sizeof(h), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "learning-signal kernel");
+    if (h & 2u) return fail(nullptr, EPROP_ETIMEOUT, "a bounded wait for the tensor-core products gave up");
+    return EPROP_OK;
+}
+
 extern "C" eprop_status eprop_read_surrogate(eprop_net *net, float *psi, int32_t is_device) {
     if (!net || !psi) return EPROP_EINVAL;
     if (net->bad) return fail(net, EPROP_ESTATE, "network is in an error state");
     if (!net->n.record_psi) return fail(net, EPROP_EINVAL, "surrogate values need record_psi = 1");
-    if (!net->have_inputs) return fail(net, EPROP_ESTATE, "no simulate call yet");
+    if (!net->have_sim) return fail(net, EPROP_ESTATE, "no simulate call since the last set_inputs");
     const long long cnt = (long long)net->cfg.batch * net->T_in * net->cfg.n_rec;
     CK(net, cudaMemcpyAsync(psi, net->n.rec_psi, cnt * 4,
                             is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, net->st));
@@ -1147,7 +1152,6 @@ extern "C" void eprop_destroy(eprop_net *net) {
     free_all(net->in_allocs);
     free_all(net->win_allocs);
     free_all(net->fixed_allocs);
-    if (net->blas) cublasDestroy(net->blas);
     if (net->ev_fork) cudaEventDestroy(net->ev_fork);
     if (net->ev_join) cudaEventDestroy(net->ev_join);
     if (net->st2) cudaStreamDestroy(net->st2);

@@ -23,6 +23,9 @@ Agreement rules (written out here and in each test):
 """
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 RTOL = 1e-5
@@ -113,3 +116,98 @@ def rel_l2(gpu, ref):
     ref = np.asarray(ref, np.float64).ravel()
     den = np.linalg.norm(ref)
     return float(np.linalg.norm(gpu - ref) / den) if den > 0 else float(np.linalg.norm(gpu))
+
+
+def survey_ratio(gpu, ref, rtol=RTOL, floor=FLOOR):
+    """Worst |gpu - ref| / (rtol * max(|ref|, floor * max|ref|)) over the
+    elements: the plain relative rule (1e-5 relative with a floor at 1e-3
+    of the largest element), reported beside the magnitude-sum gate."""
+    gpu = np.asarray(gpu, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    if ref.size == 0:
+        return 0.0
+    tol = rtol * np.maximum(np.abs(ref), floor * np.abs(ref).max()) + 1e-30
+    return float((np.abs(gpu - ref) / tol).max())
+
+
+def gate_ratio(gpu, ref, mag, rtol=RTOL):
+    """Worst |gpu - ref| / (rtol * max(mag, |ref|)) (<= 1 passes)."""
+    gpu = np.asarray(gpu, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    if ref.size == 0:
+        return 0.0
+    mag = np.asarray(mag, dtype=np.float64).ravel()
+    tol = rtol * np.maximum(mag, np.abs(ref)) + 1e-30
+    return float((np.abs(gpu - ref) / tol).max())
+
+
+def report(rep: dict):
+    """Appends the report of one parity case as a JSON line to the file
+    named by EPROP_PARITY_REPORT (if set), tagged with the running test."""
+    path = os.environ.get("EPROP_PARITY_REPORT")
+    if not path:
+        return
+    keep = {k: v for k, v in rep.items() if k != "res"}
+    keep["test"] = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    with open(path, "a") as f:
+        f.write(json.dumps(keep, default=float) + "\n")
+
+
+# ------------------------------------------------------------------
+# per-sample oracle runs (a batch split over worker processes)
+
+
+def sample_slice(W, b):
+    """The one-sample workload of sample b of a batched workload (same
+    network, the sample's inputs, targets, window and length)."""
+    import copy
+    s = copy.copy(W["spec"])
+    B, T = s.batch, s.T
+    s.batch = 1
+    p0, p1 = int(W["x_ptr"][b * T]), int(W["x_ptr"][(b + 1) * T])
+    Wb = {k: W[k] for k in ("ptr", "col", "w", "delay", "w_out", "out_mask", "feedback")}
+    Wb.update(spec=s, x_ptr=np.asarray(W["x_ptr"][b * T:(b + 1) * T + 1]) - p0,
+              x_ids=np.asarray(W["x_ids"][p0:p1]),
+              targets=np.asarray(W["targets"][b:b + 1]), window=np.asarray(W["window"][b:b + 1]),
+              lengths=np.asarray(W["lengths"][b:b + 1]))
+    return Wb
+
+
+def sample_oracle_job(job):
+    """Oracles A (teacher-forced spikes) and B (spikes and surrogate values)
+    of one sample of a single-window batched call; returns everything the
+    parity check aggregates over the batch."""
+    import oracle
+    Wb, raster, psi = job
+    s = Wb["spec"]
+    mk = lambda: oracle.Oracle(s, Wb["ptr"], Wb["col"], Wb["w"], Wb["delay"], Wb["w_out"],
+                               Wb["out_mask"], Wb["feedback"])
+    orA, orB = mk(), mk()
+    args = (s.T, Wb["x_ptr"], Wb["x_ids"], Wb["targets"], Wb["window"], Wb["lengths"])
+    rA = orA.simulate(*args, forced=raster, record=True)
+    rB = orB.simulate(*args, forced=raster, forced_psi=psi, record=True)
+    out = {}
+    out["gA"], out["goA"] = orA.take_grads()
+    out["gB"], out["goB"] = orB.take_grads()
+    out["magB"], out["gomB"] = orB.take_grad_magnitudes()
+    out["sensB"], out["gosB"] = orB.take_grad_sensitivities()
+    out["arrB"] = oracle.arrival_magnitude(s, Wb["ptr"], Wb["col"], Wb["delay"], Wb["x_ptr"],
+                                           Wb["x_ids"], Wb["lengths"], raster, rB["psi"], rB["L"])
+    out["wB"], out["woB"] = orB.w, orB.w_out
+    out["mm"], out["amb"] = check_decisions(raster, rA["margin"], s.v_th, s.t_ref, Wb["lengths"])
+    out["psi_err"] = psi_error(psi, rA, s)
+    out["yA"], out["y_absA"], out["lossA"] = rA["y"], rA["y_abs"], rA["loss"]
+    out["loss_magA"] = loss_magnitude(s, Wb, rA)
+    return out
+
+
+def pooled_sample_oracles(W, raster, psi, processes=None):
+    """sample_oracle_job for every sample of the batch, in a pool of worker
+    processes started with 'spawn' (safe beside an initialised CUDA
+    context)."""
+    import multiprocessing as mp
+    B = W["spec"].batch
+    jobs = [(sample_slice(W, b), raster[b:b + 1], psi[b:b + 1]) for b in range(B)]
+    n = processes or min(B, max(1, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(sample_oracle_job, jobs)

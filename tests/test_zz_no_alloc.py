@@ -1,9 +1,13 @@
 """Raster readout through the library's fixed device scratch (GPU only).
 
-eprop_readout_raster_static allocates no device memory; it must return the
-same raster as eprop_readout (which allocates its scratch on first use), on
-consecutive calls, and reject a raster larger than its scratch.  Collected
-last so that it also runs after every other GPU test in the session.
+eprop_readout_raster_static serves callers that cannot allocate device
+memory when they read a raster (a monitor beside a simulation that holds
+the device's memory, a loop that must not trigger an allocation's implicit
+synchronisation).  It must return the same raster as eprop_readout (which
+allocates its scratch on first use), on consecutive calls; called first on
+a fresh network it must leave the device's free memory unchanged; it
+rejects a raster larger than its scratch.  Collected last so that it also
+runs after every other GPU test in the session.
 """
 from __future__ import annotations
 
@@ -37,6 +41,31 @@ def test_static_raster_matches_allocating_readout_on_consecutive_calls():
         spikes += int(r_alloc.sum())
     net.close()
     assert spikes > 0
+
+
+def test_static_raster_allocates_nothing_on_a_fresh_network():
+    # a network that has never read a raster: eprop_readout would allocate
+    # its scratch now; the static variant must not change the free memory
+    import torch
+    W = C.event_classification(batch=2, T=100, len_lo=100, len_hi=100, n_rec=50, side=8,
+                               events_per_300=2000.0)
+    s = W["spec"]
+    net = _net(W)
+    net.set_inputs(W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"], s.T)
+    net.simulate(s.T)
+    net.sync()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    r_static = net.raster_static()
+    r_again = net.raster_static()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
+    _, _, r_alloc = net.readout(raster=True)
+    net.close()
+    assert np.array_equal(r_static, r_alloc)
+    assert np.array_equal(r_again, r_alloc)
+    assert r_alloc.sum() > 0
 
 
 def test_static_raster_rejects_more_than_its_scratch():
