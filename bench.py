@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="million", choices=["million", "scaling"],
+                   help="million: 1e6 LIF, in-degree 1000; scaling: the paper's scaling network "
+                        "(128k ignore-and-fire neurons, in-degree 10,000, 20 s)")
     p.add_argument("--n-rec", type=int, default=1_000_000)
     p.add_argument("--k-in", type=int, default=1000)
     p.add_argument("--T", type=int, default=1000)
@@ -183,12 +186,31 @@ def barrier(world):
 
 def workload_config(args, nnz, world=1):
     """The workload one step runs (both arms report it)."""
+    if args.workload == "scaling":
+        return {"workload": f"scaling: {SCALING['n_rec']} ignore-and-fire neurons at 5 Hz, recurrent "
+                            f"in-degree {SCALING['k_rec']}, {SCALING['n_in']} Poisson inputs at 5 Hz "
+                            f"(in-degree {SCALING['k_in']}), {SCALING['n_out']} readouts (in-degree "
+                            f"{SCALING['k_out']}), feedback out-degree {SCALING['fb_outdeg']}, delays 1-5, "
+                            f"update window {SCALING['update_interval']}, continuous, "
+                            f"{SCALING['T']} steps per bench step ({nnz} synapses)",
+                "n_rec": SCALING["n_rec"], "k_rec": SCALING["k_rec"], "synapses": nnz,
+                "T_per_step": SCALING["T"], "trace_storage": args.trace_dtype,
+                "trace_form": args.trace_kernel, "parallelism": f"replicas{world}",
+                "l2": "inputs larger than L2 (synapse records ~13 GB)"}
     return {"workload": f"million_sparse: {args.n_rec} LIF, in-degree {args.k_in} ({nnz} synapses), "
                         f"delays 1-5, ~5 Hz, {args.n_out} readouts, update window 100, continuous",
             "n_rec": args.n_rec, "k_in": args.k_in, "synapses": nnz, "T_per_step": args.T,
             "trace_storage": args.trace_dtype, "trace_form": args.trace_kernel,
             "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (synapse records ~10 GB per step)"}
+
+
+# the scaling experiment's network (Methods, "Scaling"): base size, 20 s
+SCALING = dict(n_rec=128_000, k_rec=10_000, n_in=1000, k_in=100, n_out=10, k_out=1000, fb_outdeg=100,
+               T=20_000, update_interval=1000)
+# the bounded sample of it the CPU oracle runs
+SCALING_SAMPLE = dict(n_rec=2000, k_rec=1000, n_in=100, k_in=10, n_out=10, k_out=100, fb_outdeg=20,
+                      T=100, update_interval=100)
 
 
 def cpu_baseline(args, steps=1):
@@ -198,10 +220,19 @@ def cpu_baseline(args, steps=1):
     import oracle
     from workloads import configs as C
     oracle.build()
-    W = C.million_sparse(n_rec=args.cpu_sample_n, k_in=args.k_in, T=args.cpu_sample_T,
-                         n_out=args.n_out)
+    if args.workload == "scaling":
+        W = C.scaling_network(**SCALING_SAMPLE)
+        sample = ("scaling network sample: 2000 ignore-and-fire neurons, recurrent in-degree 1000, "
+                  "100 Poisson inputs (in-degree 10), 10 readouts (in-degree 100), feedback out-degree 20, "
+                  f"100 steps x {steps}, FP64 time-driven oracle, single thread")
+    else:
+        W = C.million_sparse(n_rec=args.cpu_sample_n, k_in=args.k_in, T=args.cpu_sample_T,
+                             n_out=args.n_out)
+        sample = (f"{args.cpu_sample_n} LIF neurons, in-degree {args.k_in}, delays 1-5, "
+                  f"~5 Hz, {args.n_out} readouts, {args.cpu_sample_T} steps x {steps}, "
+                  f"FP64 time-driven oracle, single thread")
     s = W["spec"]
-    s.update_interval = args.cpu_sample_T
+    s.update_interval = s.T
     o = oracle.Oracle(s, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["out_mask"],
                       W["feedback"])
     outdeg = np.diff(W["ptr"])
@@ -212,10 +243,7 @@ def cpu_baseline(args, steps=1):
         tot_time += time.perf_counter() - t0
         tot_events += int((r["raster"][0].sum(axis=0) * outdeg).sum())
     return {"value": tot_events / tot_time, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{args.cpu_sample_n} LIF neurons, in-degree {args.k_in}, delays 1-5, "
-                      f"~5 Hz, {args.n_out} readouts, {args.cpu_sample_T} steps x {steps}, "
-                      f"FP64 time-driven oracle, single thread",
-            "events": tot_events, "seconds": tot_time}
+            "sample": sample, "events": tot_events, "seconds": tot_time}
 
 
 def run_reference(args):
@@ -256,21 +284,24 @@ def _run_ours(args, rank, world, local):
     import paper_2511_21674_gb300 as ep
     from workloads import gpu_build as G
     torch.manual_seed(0)
-    W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
-                               seed=replica_seed(rank))
+    if args.workload == "scaling":
+        W = G.scaling_torch(seed=replica_seed(rank) + 4, **SCALING)
+    else:
+        W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
+                                   seed=replica_seed(rank))
     spec = W["spec"]
     trace_dtype = 1 if args.trace_dtype == "bf16" else 0
-    net = ep.Network(spec, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], None, W["feedback"],
+    net = ep.Network(spec, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["out_mask"], W["feedback"],
                      launch_mode=1, trace_dtype=trace_dtype, record_grad=0, record_raster=0,
                      profile=1, blocks_per_sm=args.blocks_per_sm,
                      trace_kernel=3 if args.trace_kernel == "dense" else 1)
     nnz = int(W["col"].shape[0])
-    del W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["feedback"]
+    del W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["feedback"], W["out_mask"]
     torch.cuda.empty_cache()
     T = spec.T
     # inputs: pinned host buffers (the same arrays serve every step)
     x_ptr = torch.from_numpy(W["x_ptr"]).pin_memory()
-    x_ids = torch.zeros(1, dtype=torch.int32).pin_memory()[:0]
+    x_ids = torch.from_numpy(np.concatenate([W["x_ids"], np.zeros(1, np.int32)])).pin_memory()[:len(W["x_ids"])]
     targets = torch.from_numpy(np.ascontiguousarray(W["targets"], np.float32)).pin_memory()
     window = torch.from_numpy(W["window"]).pin_memory()
     lengths = torch.from_numpy(W["lengths"]).pin_memory()
@@ -309,7 +340,8 @@ def _run_ours(args, rank, world, local):
     value = ev_total / (ms_max / 1000.0)
 
     # ---- end to end through the public API with host buffers
-    h2d = (x_ptr.numel() * 8 + targets.numel() * 4 + window.numel() + lengths.numel() * 4)
+    h2d = (x_ptr.numel() * 8 + x_ids.numel() * 4 + targets.numel() * 4 + window.numel() +
+           lengths.numel() * 4)
     loss_host = np.zeros(spec.batch, np.float32)
     y_host = np.zeros((spec.batch, T, spec.n_out), np.float32)
     barrier(world)
@@ -332,7 +364,7 @@ def _run_ours(args, rank, world, local):
     achieved = events * bytes_per_event / (trace_ms / 1000.0) / 1e9 if trace_ms > 0 else None
     # per window pass (the unit `achieved` averages over): DRAM bytes from
     # the committed ncu capture, scaled to full size (see profiles/)
-    traffic = recorded_traffic() if args.trace_kernel == "dense" else None
+    traffic = recorded_traffic() if (args.trace_kernel == "dense" and args.workload == "million") else None
     net.close()
     if rank != 0:
         return
@@ -342,6 +374,7 @@ def _run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args, nnz, world),
         "sim_time_per_wall_time": (T * spec.dt / 1000.0) / (ms_max / K / 1000.0),
+        "real_time_factor": (ms_max / K / 1000.0) / (T * spec.dt / 1000.0),
         "events_per_step": events / K,
         "mean_rate_hz": events / K / nnz / (T * spec.dt / 1000.0),
         "grad_error": "FP32 traces: within 1e-5 of each gradient's magnitude sum vs the FP64 oracle "

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define EPROP_ABI_VERSION 1
+#define EPROP_ABI_VERSION 2
 #define EPROP_MAX_DRIVE_THR 64
 
 typedef enum {
@@ -82,6 +82,36 @@ typedef struct eprop_net eprop_net; /* opaque; owned by the library */
  * every update window.  update_interval = U steps (0: one window per
  * simulate call); windows are counted from the last state reset.
  *
+ * Variants of the paper's e-prop+ and constraints (all 0 = the plain method):
+ *   surrogate 1: psi = gamma exp(-beta_sg |v - v_th|) (Eq. exponential-
+ *     surrogate-gradient);
+ *   reset_mode 1: fixed reset (Methods, neuron models, e-prop+): the step
+ *     after a spike the decayed membrane alpha v is replaced by v_reset,
+ *     v^t = v_reset + I^t; like the soft reset it is a stop-gradient, so the
+ *     eligibility trace is unchanged;
+ *   loss 2: temporal MSE (1/K) sum_k (y_k - y*_k)^2, E_k = (2/K)(y_k - y*_k)
+ *     (Eq. temporal-mse);
+ *   c_reg != 0: firing-rate regularisation with the moving-average rate
+ *     f_j^t = beta_reg f_j^{t-1} + (1 - beta_reg) z_j^t (Eq. ema-rate) in
+ *     spikes per step and target f_target; adds c_reg (f_j^t - f_target)
+ *     G_beta(e^t) to the gradient of every synapse onto neuron j
+ *     (Eq. ema-gradient); needs continuous = 0 and update_interval = 0 (the
+ *     second filtered trace is not carried between windows);
+ *   sign_mask: weights keep the sign of their initial value (bit 0 input,
+ *     bit 1 recurrent, bit 2 readout weights; Dale's law when the initial
+ *     weights of each source share a sign); an update that would cross zero
+ *     leaves a zero of that sign;
+ *   optimizer 1: Adam (Eq. adam with the TensorFlow reordering Eq. eta-adam-
+ *     fast, Eq. delta-w-adam-fast, constant eps_hat = adam_eps): one step per
+ *     update window on the window's batch-mean gradient, k = steps taken,
+ *     eta_k = lr sqrt(1 - b2^k) / (1 - b1^k), w -= eta_k m / (sqrt(v) + eps_hat);
+ *   if_period > 0: ignore-and-fire neurons (Methods, "Scaling"): z_j^t = 1
+ *     iff (t_abs + phase_j) mod if_period == 0 regardless of the membrane,
+ *     phase_j = (upper 32 bits of mix(if_seed ^ j)) mod if_period; v and psi
+ *     are still integrated.
+ * sign_mask & 3 and optimizer 1 are not available with the lazy window form
+ * that carries state (trace_kernel 1 with continuous or update_interval).
+ *
  * External drive: n_j^t = #{m < n_drive_thr : u >= drive_thr[m]} with u the
  * upper 32 bits of h = mix(mix(mix(drive_seed ^ j) ^ t_abs) ^ sample),
  * mix = the SplitMix64 output function, t_abs = the network's absolute step
@@ -97,7 +127,7 @@ typedef struct eprop_config {
     int32_t batch;            /* samples simulated together, >= 1            */
     int32_t neuron_model;     /* 0 LIF, 1 ALIF                                */
     int32_t t_ref;            /* refractory steps, >= 0                       */
-    int32_t loss;             /* 0 MSE, 1 softmax cross-entropy               */
+    int32_t loss;             /* 0 MSE, 1 softmax cross-entropy, 2 temporal MSE */
     int32_t feedback;         /* 0 symmetric B = W_out^T, 1 fixed random B    */
     int32_t update_interval;  /* U in steps; 0 = one window per call          */
     int32_t continuous;       /* 1: keep all state between simulate calls     */
@@ -129,6 +159,16 @@ typedef struct eprop_config {
     float drive_weight;
     uint64_t drive_seed;
     uint32_t drive_thr[EPROP_MAX_DRIVE_THR];
+    /* variants (see above) */
+    int32_t surrogate;        /* 0 piecewise linear, 1 exponential            */
+    int32_t reset_mode;       /* 0 subtract the threshold, 1 fixed v_reset     */
+    float v_reset;
+    float c_reg, f_target, beta_reg;
+    int32_t sign_mask;        /* 1 input, 2 recurrent, 4 readout weights       */
+    int32_t optimizer;        /* 0 SGD, 1 Adam                                 */
+    float adam_b1, adam_b2, adam_eps;
+    int32_t if_period;        /* ignore-and-fire period in steps, 0 = off      */
+    uint64_t if_seed;
 } eprop_config;
 
 /*
@@ -149,8 +189,10 @@ typedef struct eprop_synapses {
 /*
  * Creates a network on the current CUDA device.
  *   w_out     [n_rec][n_out] readout weights (W_out[j][k] = weight j -> k)
- *   out_mask  [n_rec] 1 if neuron j projects to the readouts, else its row of
- *             W_out is held at its value and gets no gradient; NULL = all 1
+ *   out_mask  [n_rec][n_out] 1 where the readout synapse j -> k exists: its
+ *             weight W_out[j][k] learns; 0: the weight is held at its value
+ *             and gets no gradient (a sparse readout, e.g. an output in-degree
+ *             below n_rec, Methods "Scaling"); NULL = all 1
  *   feedback  [n_rec][n_out] fixed random B (required iff cfg->feedback == 1)
  *   cuda_stream  cudaStream_t to issue all work on (NULL: legacy stream);
  *             the network also creates one stream and two events of its own

@@ -70,7 +70,14 @@ class _Cfg(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("beta_sg", ctypes.c_double),
                 ("lr", ctypes.c_double), ("drive_weight", ctypes.c_double),
                 ("drive_seed", ctypes.c_uint64),
-                ("drive_thr", ctypes.c_void_p)]
+                ("drive_thr", ctypes.c_void_p),
+                ("surrogate", ctypes.c_int32), ("reset_mode", ctypes.c_int32),
+                ("v_reset", ctypes.c_double), ("c_reg", ctypes.c_double),
+                ("f_target", ctypes.c_double), ("beta_reg", ctypes.c_double),
+                ("sign_mask", ctypes.c_int32), ("optimizer", ctypes.c_int32),
+                ("adam_b1", ctypes.c_double), ("adam_b2", ctypes.c_double),
+                ("adam_eps", ctypes.c_double), ("if_period", ctypes.c_int32),
+                ("if_seed", ctypes.c_uint64)]
 
 
 class _State(ctypes.Structure):
@@ -80,7 +87,8 @@ class _State(ctypes.Structure):
             "psi_prev", "ref", "z_prev", "ring", "src_hist", "zbar", "epsa",
             "ebar", "g", "y", "zk", "g_out", "grad_acc", "grad_out_acc",
             "counters", "g_abs", "g_out_abs", "grad_abs_acc", "grad_out_abs_acc",
-            "y_abs", "g_lsens", "g_out_lsens", "grad_lsens_acc", "grad_out_lsens_acc")]
+            "y_abs", "g_lsens", "g_out_lsens", "grad_lsens_acc", "grad_out_lsens_acc",
+            "rate", "ebar_reg", "w_neg", "w_out_neg", "adam_m", "adam_v", "adam_m_out", "adam_v_out")]
 
 
 def _load():
@@ -141,7 +149,8 @@ def arrival_contrib(spec, psi, L, U=None):
 def error_signal(spec, y, targets, window, y_abs):
     """Error signal E [T, K] of one sample and its sensitivity Esens [T, K]
     from a readout y and its magnitude y_abs ([T, K]), as the C oracle forms
-    them: MSE E_k = win (y_k - y*_k) (Eq. mean-squared-error), softmax CE
+    them: MSE E_k = win (y_k - y*_k) (Eq. mean-squared-error), temporal MSE
+    E_k = win (2 / K)(y_k - y*_k) (Eq. temporal-mse), softmax CE
     E_k = win (pi_k - pi*_k) (Eq. softmax, Eq. cross-entropy-loss);
     Esens = win (y_abs + |y*|) for MSE and win (pi (y_abs + sum_l pi_l
     y_abs_l) + pi + |pi*|) for CE."""
@@ -151,6 +160,9 @@ def error_signal(spec, y, targets, window, y_abs):
     ya = np.asarray(y_abs, np.float64)
     if spec.loss == 0:
         return win * (y - tg), win * (ya + np.abs(tg))
+    if spec.loss == 2:          # temporal MSE (Eq. temporal-mse)
+        c = 2.0 / y.shape[1]
+        return win * c * (y - tg), win * c * (ya + np.abs(tg))
     e = np.exp(y - y.max(axis=1, keepdims=True))
     pi = e / e.sum(axis=1, keepdims=True)
     pya = (pi * ya).sum(axis=1, keepdims=True)
@@ -262,7 +274,11 @@ class Oracle:
         if self.nnz:
             assert int(self.delay.min()) >= 1 and int(self.delay.max()) <= spec.max_delay
         self.w_out = np.array(w_out, dtype=np.float64).reshape(N, K)
-        self.out_mask = np.ascontiguousarray(out_mask, dtype=np.uint8)
+        # per-weight readout mask [N, K]; a per-neuron mask [N] applies to the row
+        om = np.ones(N, np.uint8) if out_mask is None else np.asarray(out_mask, dtype=np.uint8)
+        if om.ndim == 1:
+            om = np.repeat(om[:, None], K, axis=1)
+        self.out_mask = np.ascontiguousarray(om.reshape(N, K))
         self.fb = None if feedback is None else np.array(feedback, dtype=np.float64).reshape(N, K)
         if spec.feedback and self.fb is None:
             raise ValueError("random feedback needs a feedback matrix")
@@ -279,7 +295,7 @@ class Oracle:
         self.g_out = z((N, K))
         self.grad_acc = z(self.nnz)
         self.grad_out_acc = z((N, K))
-        self.counters = z(2, np.int64)
+        self.counters = z(3, np.int64)   # absolute step, step since reset, Adam steps
         self.g_abs = z(self.nnz)
         self.g_out_abs = z((N, K))
         self.grad_abs_acc = z(self.nnz)
@@ -289,6 +305,14 @@ class Oracle:
         self.g_out_lsens = z((N, K))
         self.grad_lsens_acc = z(self.nnz)
         self.grad_out_lsens_acc = z((N, K))
+        self.rate = z((B, N))
+        self.ebar_reg = z((B, self.nnz))
+        # fixed signs: the sign bit of each initial weight (float32 values as given)
+        self.w_neg = np.ascontiguousarray(np.signbit(np.asarray(w, np.float32)), dtype=np.uint8)
+        self.w_out_neg = np.ascontiguousarray(np.signbit(np.asarray(w_out, np.float32)).reshape(N, K),
+                                              dtype=np.uint8)
+        self.adam_m, self.adam_v = z(self.nnz), z(self.nnz)
+        self.adam_m_out, self.adam_v_out = z((N, K)), z((N, K))
 
     def _cfg(self, T):
         s = self.spec
@@ -306,7 +330,12 @@ class Oracle:
                     beta_a=s.beta_a if s.neuron_model == 1 else 0.0,
                     v_th=s.v_th, gamma=s.gamma, beta_sg=s.beta_sg, lr=s.lr,
                     drive_weight=s.drive_weight, drive_seed=s.drive_seed,
-                    drive_thr=_p(self.thr) if self.thr.shape[0] else None)
+                    drive_thr=_p(self.thr) if self.thr.shape[0] else None,
+                    surrogate=s.surrogate, reset_mode=s.reset_mode, v_reset=s.v_reset,
+                    c_reg=s.c_reg, f_target=s.f_target, beta_reg=s.beta_reg,
+                    sign_mask=s.sign_mask, optimizer=s.optimizer, adam_b1=s.adam_b1,
+                    adam_b2=s.adam_b2, adam_eps=s.adam_eps, if_period=s.if_period,
+                    if_seed=s.if_seed)
 
     def _state(self):
         st = _State(n_src=self.n_src, nnz=self.nnz)
@@ -315,7 +344,8 @@ class Oracle:
                      "epsa", "ebar", "g", "y", "zk", "g_out", "grad_acc",
                      "grad_out_acc", "counters", "g_abs", "g_out_abs", "grad_abs_acc",
                      "grad_out_abs_acc", "y_abs", "g_lsens", "g_out_lsens", "grad_lsens_acc",
-                     "grad_out_lsens_acc"):
+                     "grad_out_lsens_acc", "rate", "ebar_reg", "w_neg", "w_out_neg", "adam_m",
+                     "adam_v", "adam_m_out", "adam_v_out"):
             setattr(st, name, _p(getattr(self, name)))
         st.fb = _p(self.fb)
         return st

@@ -49,6 +49,34 @@
  * pi_k (|y|_k + sum_l pi_l |y|_l) + pi_k + pi*_k for softmax CE.  They do
  * not feed back into any result.
  *
+ * Variants (e-prop+, Methods and Supplement), each off by default:
+ *   - exponential surrogate psi = gamma exp(-beta |v - v_th|)  (Eq. exponential-
+ *     surrogate-gradient);
+ *   - fixed reset: the step after a spike the decayed membrane alpha v is
+ *     replaced by v_reset (v^t = v_reset + I^t instead of alpha v - v_th + I);
+ *     the reset stays outside the eligibility (it is a stop-gradient, as the
+ *     soft reset is), so the eligibility vector keeps F_alpha;
+ *   - temporal MSE: loss (1/K) sum_k (y_k - y*_k)^2, E_k = (2/K)(y_k - y*_k)
+ *     (Eq. temporal-mse);
+ *   - firing-rate regularisation with the exponential moving average
+ *     f_j^t = beta_reg f_j^{t-1} + (1 - beta_reg) z_j^t (Eq. ema-rate), adding
+ *     c_reg (f_j^t - f*) G_beta(e^t) to every synapse onto neuron j
+ *     (Eq. ema-gradient); G_beta(e^t) = (1 - beta_reg) F_beta(e^t) is a second
+ *     filtered copy of the same eligibility trace e^t; rates are in spikes
+ *     per step;
+ *   - fixed weight signs (Dale's law when the initial weights of each source
+ *     share a sign): bit 0 input, bit 1 recurrent, bit 2 readout weights keep
+ *     the sign of their initial value; an update that would cross zero stops
+ *     at zero (a signed zero, keeping the sign);
+ *   - Adam (Eq. adam, Eq. eta-adam-fast, Eq. delta-w-adam-fast): one Adam step
+ *     per update window on the window's batch-mean gradient, k = number of
+ *     steps taken, eta_k = eta sqrt(1 - b2^k) / (1 - b1^k),
+ *     w -= eta_k m / (sqrt(v) + eps_hat) with the TensorFlow constant eps_hat;
+ *   - ignore-and-fire neurons (Methods, "Scaling"): z_j^t = 1 iff
+ *     (t_abs + phase_j) mod period == 0, whatever the membrane does; v and psi
+ *     are still integrated; phase_j = (upper 32 bits of mix(if_seed ^ j))
+ *     mod period.
+ *
  * E_override (optional, [B][T][K]): where window = 0, E^t is taken from it
  * instead of from the loss (the learned predictor's error estimate).
  *
@@ -70,6 +98,16 @@ typedef struct {
     double lr, drive_weight;
     uint64_t drive_seed;
     const uint32_t *drive_thr;
+    /* variants (see the header comment) */
+    int32_t surrogate;            /* 0 piecewise linear, 1 exponential */
+    int32_t reset_mode;           /* 0 soft, 1 fixed value */
+    double v_reset;
+    double c_reg, f_target, beta_reg;
+    int32_t sign_mask;            /* bit 0 input, bit 1 recurrent, bit 2 readout */
+    int32_t optimizer;            /* 0 SGD, 1 Adam */
+    double adam_b1, adam_b2, adam_eps;
+    int32_t if_period;            /* ignore-and-fire period in steps, 0: off */
+    uint64_t if_seed;
 } oracle_cfg;
 
 typedef struct {
@@ -81,7 +119,7 @@ typedef struct {
     const uint8_t *delay;
     double *w;                    /* [nnz], updated in place */
     double *w_out;                /* [n_rec][n_out], updated in place */
-    const uint8_t *out_mask;      /* [n_rec] 1 = neuron projects to readouts */
+    const uint8_t *out_mask;      /* [n_rec][n_out] 1 = readout synapse j -> k exists */
     const double *fb;             /* [n_rec][n_out] or NULL (B = W_out^T) */
     /* persistent state */
     double *v, *a, *psi_prev;     /* [B][N] */
@@ -100,6 +138,11 @@ typedef struct {
     double *y_abs;                /* [B][K] kappa-filtered sum of |W_out| z  */
     double *g_lsens, *g_out_lsens;        /* sensitivity sums, current window */
     double *grad_lsens_acc, *grad_out_lsens_acc; /* the same, batch mean, summed */
+    double *rate;                 /* [B][N] f_j of the rate regularisation */
+    double *ebar_reg;             /* [B][nnz] F_beta(e) of each synapse */
+    const uint8_t *w_neg, *w_out_neg; /* [nnz], [N][K] 1 where the initial weight is negative */
+    double *adam_m, *adam_v;      /* [nnz] */
+    double *adam_m_out, *adam_v_out; /* [N][K] */
 } oracle_state;
 
 /* SplitMix64 output function (Steele, Lea & Flood 2014). */
@@ -119,6 +162,21 @@ static int drive_count(const oracle_cfg *c, int64_t b, int64_t t_abs, int64_t j)
     return n;
 }
 
+/* Phase of ignore-and-fire neuron j: (upper 32 bits of mix(if_seed ^ j)) mod
+   period. */
+static int64_t if_phase(const oracle_cfg *c, int64_t j) {
+    return (int64_t)((uint32_t)(mix64(c->if_seed ^ (uint64_t)j) >> 32) % (uint32_t)c->if_period);
+}
+
+/* Weight after an update w - dw, kept on the side of zero of its initial
+   value when its sign is fixed (neg: initial weight negative). */
+static double signed_update(double w, double dw, int fixed, int neg) {
+    double x = w - dw;
+    if (!fixed) return x;
+    if (neg) return x < 0.0 ? x : -0.0;
+    return x > 0.0 ? x : 0.0;
+}
+
 /* One step of the per-synapse eligibility recursion (Eq. eligibility-vector-
  * substituted and Eq. filtered-eligibility-trace):
  *   eps_a^t = psi^{t-1} zbar^{t-1} + (rho - psi^{t-1} beta_a) eps_a^{t-1}
@@ -126,15 +184,21 @@ static int drive_count(const oracle_cfg *c, int64_t b, int64_t t_abs, int64_t j)
  *   e^t     = psi^t (zbar^t - beta_a eps_a^t)
  *   ebar^t  = kappa_e ebar^{t-1} + e^t        (F_kappa)
  * and returns the per-step gradient g^t = L^t ebar^t. */
-double oracle_eligibility_step(double alpha, double rho, double beta_a,
-                               double kappa_e, double psi_prev, double psi,
-                               double L, double arrive, double *zbar,
-                               double *epsa, double *ebar) {
+static double eligibility_e(double alpha, double rho, double beta_a, double kappa_e, double psi_prev,
+                            double psi, double arrive, double *zbar, double *epsa, double *ebar) {
     double epsa_new = psi_prev * (*zbar) + (rho - psi_prev * beta_a) * (*epsa);
     *zbar = alpha * (*zbar) + arrive;
     *epsa = epsa_new;
     double e = psi * ((*zbar) - beta_a * (*epsa));
     *ebar = kappa_e * (*ebar) + e;
+    return e;
+}
+
+double oracle_eligibility_step(double alpha, double rho, double beta_a,
+                               double kappa_e, double psi_prev, double psi,
+                               double L, double arrive, double *zbar,
+                               double *epsa, double *ebar) {
+    eligibility_e(alpha, rho, beta_a, kappa_e, psi_prev, psi, arrive, zbar, epsa, ebar);
     return L * (*ebar);
 }
 
@@ -216,6 +280,8 @@ static void reset_state(const oracle_cfg *c, oracle_state *s) {
     memset(s->y, 0, sizeof(double) * B * K);
     memset(s->y_abs, 0, sizeof(double) * B * K);
     memset(s->zk, 0, sizeof(double) * B * N);
+    memset(s->rate, 0, sizeof(double) * B * N);
+    memset(s->ebar_reg, 0, sizeof(double) * B * s->nnz);
     s->counters[1] = 0;
 }
 
@@ -256,6 +322,7 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
             uint8_t *hist = s->src_hist + b * D1 * NS;
             double *y = s->y + b * K, *zk = s->zk + b * N;
             double *y_abs = s->y_abs + b * K;
+            double *rate = s->rate + b * N;
             const int64_t bt = b * (int64_t)T + (t - 1);
 
             /* sources that spike at this step: inputs from the raster */
@@ -271,15 +338,24 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     I += c->drive_weight * drive_count(c, b, t_abs, j);
                 a[j] = c->rho * a[j] + z_prev[j];
                 double vth = c->v_th + c->beta_a * a[j];
-                v[j] = c->alpha * v[j] + I - z_prev[j] * vth;
+                if (c->reset_mode == 1)           /* fixed reset value */
+                    v[j] = (z_prev[j] ? c->v_reset : c->alpha * v[j]) + I;
+                else                              /* reset by subtraction */
+                    v[j] = c->alpha * v[j] + I - z_prev[j] * vth;
                 int refractory = ref[j] > 0;
                 double m = v[j] - vth;
                 if (forced)
                     z[j] = forced[bt * N + j];
+                else if (c->if_period > 0)        /* ignore-and-fire */
+                    z[j] = ((t_abs + if_phase(c, j)) % c->if_period) == 0 ? 1 : 0;
                 else
                     z[j] = (!refractory && m > 0.0) ? 1 : 0;
-                double h = 1.0 - c->beta_sg * fabs(m);
-                psi[j] = refractory ? 0.0 : c->gamma * (h > 0.0 ? h : 0.0);
+                if (c->surrogate == 1) {
+                    psi[j] = refractory ? 0.0 : c->gamma * exp(-c->beta_sg * fabs(m));
+                } else {
+                    double h = 1.0 - c->beta_sg * fabs(m);
+                    psi[j] = refractory ? 0.0 : c->gamma * (h > 0.0 ? h : 0.0);
+                }
                 if (forced_psi) psi[j] = forced_psi[bt * N + j];
                 if (refractory) ref[j] -= 1;
                 if (z[j]) ref[j] = c->t_ref;
@@ -287,6 +363,7 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 margin[bt * N + j] = m;
                 if (psi_rec) psi_rec[bt * N + j] = psi[j];
                 hist[slot * NS + NI + j] = z[j];
+                rate[j] = c->beta_reg * rate[j] + (1.0 - c->beta_reg) * z[j];
             }
 
             /* readout, error signal, loss */
@@ -310,6 +387,12 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     E[k] = win * diff;
                     loss[b] += 0.5 * win * diff * diff;
                 }
+            } else if (c->loss == 2) {            /* temporal MSE */
+                for (int64_t k = 0; k < K; ++k) {
+                    double diff = y[k] - tgt[k];
+                    E[k] = win * (2.0 / (double)K) * diff;
+                    loss[b] += win * diff * diff / (double)K;
+                }
             } else {
                 double mx = y[0];
                 for (int64_t k = 1; k < K; ++k) mx = y[k] > mx ? y[k] : mx;
@@ -331,6 +414,8 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     (the last two: rounding of pi_k and of the difference) */
             if (c->loss == 0) {
                 for (int64_t k = 0; k < K; ++k) Esens[k] = win * (y_abs[k] + fabs(tgt[k]));
+            } else if (c->loss == 2) {
+                for (int64_t k = 0; k < K; ++k) Esens[k] = win * (2.0 / (double)K) * (y_abs[k] + fabs(tgt[k]));
             } else {
                 double pya = 0.0;
                 for (int64_t k = 0; k < K; ++k) pya += pi[k] * y_abs[k];
@@ -364,19 +449,27 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     const int64_t d = s->delay[q];
                     double arrive = 0.0;
                     if (t_abs - d >= 1) arrive = hist[((t_abs - d) % D1) * NS + i];
-                    const double gt = oracle_eligibility_step(
-                        c->alpha, c->rho, c->beta_a, c->kappa_e, psi_prev[j],
-                        psi[j], L[j], arrive, s->zbar + b * NNZ + q,
-                        s->epsa + b * NNZ + q, s->ebar + b * NNZ + q);
+                    const double e = eligibility_e(c->alpha, c->rho, c->beta_a, c->kappa_e, psi_prev[j],
+                                                   psi[j], arrive, s->zbar + b * NNZ + q,
+                                                   s->epsa + b * NNZ + q, s->ebar + b * NNZ + q);
+                    double gt = L[j] * s->ebar[b * NNZ + q];
+                    double gabs = fabs(gt);
+                    if (c->c_reg != 0.0) {        /* Eq. ema-gradient */
+                        double *er = s->ebar_reg + b * NNZ + q;
+                        *er = c->beta_reg * (*er) + e;
+                        const double greg = c->c_reg * (rate[j] - c->f_target) * (1.0 - c->beta_reg) * (*er);
+                        gt += greg;
+                        gabs += fabs(greg);
+                    }
                     s->g[q] += gt;
-                    s->g_abs[q] += fabs(gt);
+                    s->g_abs[q] += gabs;
                     s->g_lsens[q] += Ls[j] * fabs(s->ebar[b * NNZ + q]);
                 }
             }
             for (int64_t j = 0; j < N; ++j) {
                 zk[j] = c->kappa * zk[j] + z[j];
-                if (s->out_mask[j])
-                    for (int64_t k = 0; k < K; ++k) {
+                for (int64_t k = 0; k < K; ++k)
+                    if (s->out_mask[j * K + k]) {
                         s->g_out[j * K + k] += E[k] * zk[j];
                         s->g_out_abs[j * K + k] += fabs(E[k] * zk[j]);
                         s->g_out_lsens[j * K + k] += Esens[k] * zk[j];
@@ -399,9 +492,22 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
 
         /* end of an update window: gradient descent with the batch mean */
         if (s->counters[1] % U == 0) {
+            double eta = c->lr;
+            if (c->optimizer == 1) {              /* Eq. eta-adam-fast */
+                const double k = (double)(++s->counters[2]);
+                eta = c->lr * sqrt(1.0 - pow(c->adam_b2, k)) / (1.0 - pow(c->adam_b1, k));
+            }
+            const int64_t nnz_in = s->ptr[NI];
             for (int64_t q = 0; q < NNZ; ++q) {
                 double gm = s->g[q] / (double)B;
-                s->w[q] -= c->lr * gm;
+                double dw = c->lr * gm;
+                if (c->optimizer == 1) {          /* Eq. delta-w-adam-fast */
+                    s->adam_m[q] = c->adam_b1 * s->adam_m[q] + (1.0 - c->adam_b1) * gm;
+                    s->adam_v[q] = c->adam_b2 * s->adam_v[q] + (1.0 - c->adam_b2) * gm * gm;
+                    dw = eta * s->adam_m[q] / (sqrt(s->adam_v[q]) + c->adam_eps);
+                }
+                const int fixed = (c->sign_mask >> (q < nnz_in ? 0 : 1)) & 1;
+                s->w[q] = signed_update(s->w[q], dw, fixed, s->w_neg[q]);
                 s->grad_acc[q] += gm;
                 s->g[q] = 0.0;
                 s->grad_abs_acc[q] += s->g_abs[q] / (double)B;
@@ -410,10 +516,18 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 s->g_lsens[q] = 0.0;
             }
             for (int64_t j = 0; j < N; ++j) {
-                if (!s->out_mask[j]) continue;
                 for (int64_t k = 0; k < K; ++k) {
+                    if (!s->out_mask[j * K + k]) continue;
                     double gm = s->g_out[j * K + k] / (double)B;
-                    s->w_out[j * K + k] -= c->lr * gm;
+                    double dw = c->lr * gm;
+                    if (c->optimizer == 1) {
+                        double *mo = s->adam_m_out + j * K + k, *vo = s->adam_v_out + j * K + k;
+                        *mo = c->adam_b1 * (*mo) + (1.0 - c->adam_b1) * gm;
+                        *vo = c->adam_b2 * (*vo) + (1.0 - c->adam_b2) * gm * gm;
+                        dw = eta * (*mo) / (sqrt(*vo) + c->adam_eps);
+                    }
+                    s->w_out[j * K + k] = signed_update(s->w_out[j * K + k], dw, (c->sign_mask >> 2) & 1,
+                                                        s->w_out_neg[j * K + k]);
                     s->grad_out_acc[j * K + k] += gm;
                     s->g_out[j * K + k] = 0.0;
                     s->grad_out_abs_acc[j * K + k] += s->g_out_abs[j * K + k] / (double)B;

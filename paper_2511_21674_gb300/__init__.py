@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libeprop.so")
 
 PROJ_IN, PROJ_REC, PROJ_OUT = 0, 1, 2
-ABI_VERSION = 1
+ABI_VERSION = 2
 MAX_DRIVE_THR = 64
 
 _STATUS = {0: "EPROP_OK", 1: "EPROP_EINVAL", 2: "EPROP_ENOMEM", 3: "EPROP_ECUDA",
@@ -47,7 +47,12 @@ class Config(ctypes.Structure):
             "dt", "tau_m", "tau_a", "beta_a", "v_th", "tau_out", "kappa_e", "gamma",
             "beta_sg", "lr", "drive_weight")] + [
         ("drive_seed", ctypes.c_uint64),
-        ("drive_thr", ctypes.c_uint32 * MAX_DRIVE_THR)]
+        ("drive_thr", ctypes.c_uint32 * MAX_DRIVE_THR),
+        ("surrogate", ctypes.c_int32), ("reset_mode", ctypes.c_int32), ("v_reset", ctypes.c_float),
+        ("c_reg", ctypes.c_float), ("f_target", ctypes.c_float), ("beta_reg", ctypes.c_float),
+        ("sign_mask", ctypes.c_int32), ("optimizer", ctypes.c_int32),
+        ("adam_b1", ctypes.c_float), ("adam_b2", ctypes.c_float), ("adam_eps", ctypes.c_float),
+        ("if_period", ctypes.c_int32), ("if_seed", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):
@@ -180,6 +185,11 @@ def make_config(spec, launch_mode: int = 1, trace_dtype: int = 0, record_grad: i
     c.n_drive_thr = int(thr.shape[0]) if spec.drive_weight != 0.0 else 0
     for m in range(int(thr.shape[0])):
         c.drive_thr[m] = int(thr[m])
+    c.surrogate, c.reset_mode, c.v_reset = spec.surrogate, spec.reset_mode, spec.v_reset
+    c.c_reg, c.f_target, c.beta_reg = spec.c_reg, spec.f_target, spec.beta_reg
+    c.sign_mask, c.optimizer = spec.sign_mask, spec.optimizer
+    c.adam_b1, c.adam_b2, c.adam_eps = spec.adam_b1, spec.adam_b2, spec.adam_eps
+    c.if_period, c.if_seed = spec.if_period, spec.if_seed
     return c
 
 
@@ -227,7 +237,11 @@ class Network:
             ptr, col = _np(ptr, np.int64), _np(col, np.int32)
             w, delay = _np(w, np.float32), _np(delay, np.uint8)
             w_out = _np(w_out, np.float32)
-            out_mask = None if out_mask is None else _np(out_mask, np.uint8)
+            if out_mask is not None:
+                # a per-neuron mask [n_rec] applies to every readout of the neuron
+                out_mask = _np(out_mask, np.uint8)
+                if out_mask.ndim == 1:
+                    out_mask = np.ascontiguousarray(np.repeat(out_mask[:, None], spec.n_out, axis=1))
             feedback = None if feedback is None else _np(feedback, np.float32)
         self._keep = (ptr, col, w, delay, w_out, out_mask, feedback)
         is_dev = _same_place([ptr, col, w, delay, w_out, out_mask, feedback])

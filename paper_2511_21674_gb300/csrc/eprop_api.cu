@@ -193,6 +193,7 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     WA(psi_hist, float, B * (U + 1) * N);
     WA(E_win, float, B * U * K);
     WA(L_win, float, B * (long long)U * N);
+    if (c.c_reg != 0.f) WA(R_win, float, B * (long long)U * N);
     WA(Ebar_win, float, B * U * K);
     WA(qp, float, B * (long long)U * N * net->qp_stride);
     WA(win_off, long long, U + D + 2 + eprop::kWorkCounters);
@@ -216,7 +217,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         c.batch < 1 || c.batch >= (1 << 11))
         return fail(nullptr, EPROP_EINVAL, "sizes out of range (n_rec < 2^24, 1 <= n_out <= 1024, batch < 2048)");
     if (c.max_delay < 1 || c.max_delay > eprop::kMaxDelay) return fail(nullptr, EPROP_EINVAL, "max_delay must be 1..8");
-    if (c.neuron_model < 0 || c.neuron_model > 1 || c.loss < 0 || c.loss > 1 || c.feedback < 0 ||
+    if (c.neuron_model < 0 || c.neuron_model > 1 || c.loss < 0 || c.loss > 2 || c.feedback < 0 ||
         c.feedback > 1 || c.trace_dtype < 0 || c.trace_dtype > 1 || c.t_ref < 0 || c.update_interval < 0)
         return fail(nullptr, EPROP_EINVAL, "invalid enum or negative parameter");
     if (c.batch > 1 && (c.continuous || c.update_interval > 0))
@@ -227,6 +228,18 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         return fail(nullptr, EPROP_EINVAL, "the window trace kernels need batch = 1");
     if (c.trace_kernel == 2 && (c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL, "the batched trace kernel cannot carry state between windows");
+    if (c.surrogate < 0 || c.surrogate > 1 || c.reset_mode < 0 || c.reset_mode > 1 || c.sign_mask < 0 ||
+        c.sign_mask > 7 || c.optimizer < 0 || c.optimizer > 1 || c.if_period < 0)
+        return fail(nullptr, EPROP_EINVAL, "invalid variant switch (surrogate, reset_mode, sign_mask, optimizer, if_period)");
+    if (c.c_reg != 0.f && (!(c.beta_reg >= 0.f && c.beta_reg < 1.f) || c.continuous || c.update_interval > 0))
+        return fail(nullptr, EPROP_EINVAL,
+                    "rate regularisation needs 0 <= beta_reg < 1, continuous = 0 and update_interval = 0");
+    if (c.optimizer == 1 && !(c.adam_b1 >= 0.f && c.adam_b1 < 1.f && c.adam_b2 >= 0.f && c.adam_b2 < 1.f &&
+                              c.adam_eps > 0.f))
+        return fail(nullptr, EPROP_EINVAL, "Adam needs 0 <= b1, b2 < 1 and eps > 0");
+    if ((c.optimizer == 1 || (c.sign_mask & 3)) && c.trace_kernel == 1 && (c.continuous || c.update_interval > 0))
+        return fail(nullptr, EPROP_EINVAL,
+                    "Adam and fixed synapse signs need a trace form without lazy catch-up (not trace_kernel 1 with state)");
     if (c.n_drive_thr < 0 || c.n_drive_thr > EPROP_MAX_DRIVE_THR)
         return fail(nullptr, EPROP_EINVAL, "n_drive_thr out of range");
     for (int m = 1; m < c.n_drive_thr; ++m)
@@ -284,6 +297,11 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     n.drive_weight = c.drive_weight; n.drive_seed = c.drive_seed;
     n.log2_alpha = (float)std::log2(alpha); n.log2_kappa = (float)std::log2(kappa);
     n.inv_B = (float)(1.0 / c.batch);
+    n.surrogate = c.surrogate; n.reset_mode = c.reset_mode; n.v_reset = c.v_reset;
+    n.c_reg = c.c_reg; n.f_target = c.f_target; n.beta_reg = c.beta_reg;
+    n.sign_mask = c.sign_mask; n.adam = c.optimizer == 1;
+    n.adam_b1 = c.adam_b1; n.adam_b2 = c.adam_b2; n.adam_eps = c.adam_eps;
+    n.if_period = c.if_period; n.if_seed = c.if_seed;
 
     std::vector<DevAlloc> &o = net->fixed_allocs;
     void *p;
@@ -311,6 +329,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             for (long long i = 0; i < S; ++i)
                 if (hp[i + 1] < hp[i]) { s = fail(nullptr, EPROP_EINVAL, "row_ptr must be non-decreasing"); goto fail_out; }
             net->nnz_in = hp[c.n_in];
+            n.nnz_in = hp[c.n_in];
             long long mx = 0;
             for (long long i = 0; i < S; ++i) mx = std::max(mx, hp[i + 1] - hp[i]);
             n.segs = (int)std::max(1LL, (mx + eprop::kSeg - 1) / eprop::kSeg);
@@ -371,10 +390,10 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         cudaMemcpy(n.w_out, w_out, N * K * 4, kind);
         {
             uint8_t *m;
-            FA(out_mask, uint8_t, N);
+            FA(out_mask, uint8_t, N * K);
             m = const_cast<uint8_t *>(n.out_mask);
-            if (out_mask) cudaMemcpy(m, out_mask, N, kind);
-            else cudaMemset(m, 1, N);
+            if (out_mask) cudaMemcpy(m, out_mask, N * K, kind);
+            else cudaMemset(m, 1, N * K);
         }
         if (c.feedback == 1) {
             float *f;
@@ -391,6 +410,15 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         FA(zk, float, 2 * B * N);
         FA(loss_acc, float, B);
         FA(ro_done, int, B);
+        if (c.c_reg != 0.f) FA(rate, float, B * N);
+        if (n.adam) {
+            FA(gwin, float, nnz + 16);
+            FA(adam_m, float, nnz + 16);
+            FA(adam_v, float, nnz + 16);
+            FA(gwin_out, float, N * K);
+            FA(adam_m_out, float, N * K);
+            FA(adam_v_out, float, N * K);
+        }
         FA(events, unsigned long long, 1);
         FA(err_flags, unsigned int, 1);
         FA(clock, eprop::Clock, 1);
@@ -552,6 +580,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         cudaMemsetAsync(n.zk, 0, 2 * B * N * 4, st);
         cudaMemsetAsync(n.psi_hist, 0, B * (U + 1) * N * 4, st);
         cudaMemsetAsync(n.anchor_z, 0, B * S * 4, st);
+        if (n.rate) cudaMemsetAsync(n.rate, 0, B * N * 4, st);
         eprop::launch_fill_int(n.anchor_t, B * S, eprop::kNoSpike, st);
         if (n.has_state) {
             const size_t tb = n.trace_bf16 ? 2 : 4;
@@ -651,6 +680,10 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             }
             if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin + 1], st, cudaEventRecordExternal);
             join_readout();
+            if (n.adam) {                // after the readout gradient has landed
+                eprop::launch_adam(n, net->sm_count, st);
+                L += 2;
+            }
             if (i < T || n.has_state) { eprop::launch_rollover(n, i, st); L += 1; }
             nwin += 1;
         }
@@ -831,7 +864,7 @@ extern "C" eprop_status eprop_autotune(eprop_net *net, eprop_tune_result *out) {
     // candidates: the trace form (only before the first call, while the
     // carried state is still zero) and the CTAs per SM of the row kernels
     std::vector<int> tks;
-    if (pristine && c.batch == 1 && net->n.has_state) tks = {3, 1};
+    if (pristine && c.batch == 1 && net->n.has_state && !net->n.adam && !(c.sign_mask & 3)) tks = {3, 1};
     else tks = {tk0};
     const int bps_list[4] = {1, 2, 3, 4};
     std::memset(out, 0, sizeof(*out));

@@ -44,6 +44,7 @@ struct Clock {            // device-resident time base (graph-safe)
     long long t_abs_base; // absolute steps completed before the current call
     int r_base;           // steps since the last state reset before the call
     int ring0;            // t_abs_base mod (D + 1): ring slot of absolute step t_abs_base
+    int adam_k;           // Adam steps taken
 };
 
 struct Net {
@@ -120,6 +121,21 @@ struct Net {
     unsigned long long *events;
     unsigned int *err_flags;  // bit 0: catch-up ring overflow
     Clock *clock;
+    // e-prop+ variants and constraints
+    int surrogate;            // 0 piecewise linear, 1 exponential
+    int reset_mode;           // 0 subtract the threshold, 1 fixed value
+    float v_reset;
+    float c_reg, f_target, beta_reg;   // firing-rate regularisation (c_reg 0: off)
+    float *rate;              // [B][N] moving-average rate f_j
+    float *R_win;             // [B][U][N] c_reg (1 - beta_reg) (f_j^t - f_target) of the window
+    int sign_mask;            // fixed weight signs: 1 input, 2 recurrent, 4 readout
+    long long nnz_in;         // input synapses come first in the CSR order
+    int adam;                 // 1: Adam steps at window ends
+    float adam_b1, adam_b2, adam_eps;
+    float *gwin, *gwin_out;   // [nnz], [N][K] batch-mean gradient of the window (Adam)
+    float *adam_m, *adam_v, *adam_m_out, *adam_v_out;
+    int if_period;            // ignore-and-fire period (0: off)
+    unsigned long long if_seed;
 };
 
 // ----------------------------------------------------------------- helpers
@@ -285,6 +301,28 @@ __device__ __forceinline__ float load_trace(const void *base, long long q, int b
 __device__ __forceinline__ void store_trace(void *base, long long q, float x, int bf16) {
     if (bf16) __stcs(reinterpret_cast<unsigned short *>(base) + q, __bfloat16_as_ushort(__float2bfloat16_rn(x)));
     else __stcs(reinterpret_cast<float *>(base) + q, x);
+}
+
+// Weight after an update, kept on the side of zero of the old weight (the
+// old weight's sign bit is the synapse's fixed sign: a weight that reaches
+// zero becomes a zero of its own sign, so the sign survives).
+__device__ __forceinline__ float keep_sign(float w_old, float w_new) {
+    if (signbit(w_old)) return w_new < 0.0f ? w_new : -0.0f;
+    return w_new > 0.0f ? w_new : 0.0f;
+}
+__device__ __forceinline__ bool sign_fixed(const Net &n, long long q) {
+    return (n.sign_mask >> (q < n.nnz_in ? 0 : 1)) & 1;
+}
+// Window-end update of synapse q from its batch-summed gradient G (Eq.
+// gradient-descent): returns the new weight, or, with Adam, records the
+// batch mean for the Adam step and returns the weight unchanged.
+__device__ __forceinline__ float window_update(const Net &n, long long q, float w_old, float G) {
+    if (n.adam) {
+        n.gwin[q] = n.inv_B * G;
+        return w_old;
+    }
+    const float w = w_old - n.lr * n.inv_B * G;
+    return (n.sign_mask && sign_fixed(n, q)) ? keep_sign(w_old, w) : w;
 }
 
 // Presynaptic summary of one source row for one delay d, relative to the

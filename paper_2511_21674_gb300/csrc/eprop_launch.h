@@ -28,6 +28,7 @@ void launch_flush(const Net &n, int i_end, float *w_dst, float *g_dst, long long
                   int write_back, int sm_count, cudaStream_t st);
 void launch_fill_int(int *p, long long count, int value, cudaStream_t st);
 void launch_unpack_raster(const Net &n, unsigned char *dst, cudaStream_t st);
+void launch_adam(const Net &n, int sm_count, cudaStream_t st);
 void prepare_learning_signal_attributes();
 void launch_learning_signals(const float *fb, const float *E, float *L, int N, int U, int K, int B,
                              unsigned *err, cudaStream_t st);

@@ -11,9 +11,11 @@
 // Precision: the tensor cores take TF32 operands (10 explicit mantissa
 // bits).  Each operand x is split into hi = tf32(x) (round to nearest) and
 // lo = tf32(x - hi); x - hi is exact in FP32 and lo keeps its top 11 bits,
-// so hi + lo equals x to 2^-22 |x|.  The tile is accumulated in FP32 (TMEM)
-// as hi*hi + hi*lo + lo*hi; the dropped lo*lo product is below 2^-22 |a||b|.
-// The result matches an FP32 FMA loop to a few 1e-7 of sum_k |B_jk E_k|.
+// so hi + lo equals x to 2^-22 |x|.  The products hi*hi go into one FP32
+// TMEM accumulator and the corrections hi*lo + lo*hi into a second one, so
+// the large running sum takes one rounding per K-step of 8 (not three), and
+// the epilogue adds the two; the dropped lo*lo product is below 2^-22 |a||b|.
+// The result matches FP32 arithmetic to a few 1e-7 of sum_k |B_jk E_k|.
 //
 // Kernel shape: one CTA per tile of 128 neurons and sample (grid x = tiles,
 // y = samples), 256 threads.  For each chunk of 32 K-elements the threads
@@ -21,15 +23,16 @@
 // multiple of 16) with coalesced loads, split them and store hi and lo in
 // the 128-byte-swizzled K-major layout of the UMMA operand descriptors; one
 // thread then issues the 3 x (K-steps of 8) tcgen05.mma of the chunk into
-// the TMEM accumulator and commits them to an mbarrier, which every thread
+// the TMEM accumulators and commits them to an mbarrier, which every thread
 // waits on (bounded) before the chunk buffers are refilled.  The epilogue
-// reads the accumulator with tcgen05.ld (warp w % 4 owns TMEM lanes
-// 32 (w % 4) .. +31, i.e. neurons; the two warpgroups split the columns)
-// and stores L[b][u][j] with the 32 lanes of a warp on 32 consecutive
-// neurons (coalesced 128-byte rows).  Windows longer than 256 steps are
-// done in passes of at most 256 columns.  ~97 KB of shared memory per CTA
-// keeps at most two CTAs on an SM, whose TMEM allocations (<= 256 columns
-// each) then always fit the SM's 512 columns.
+// reads both accumulators with tcgen05.ld (warp w % 4 owns TMEM lanes
+// 32 (w % 4) .. +31, i.e. neurons; the two warpgroups split the columns),
+// adds them and stores L[b][u][j] with the 32 lanes of a warp on 32
+// consecutive neurons (coalesced 128-byte rows).  Windows longer than 128
+// steps are done in passes of at most 128 columns.  The operand regions
+// take ~65 KB of shared memory; the launch requests 100 KB so that at most
+// two CTAs are resident on an SM, whose TMEM allocations (two accumulators,
+// <= 256 columns per CTA) then always fit the SM's 512 columns.
 #include <cstdint>
 
 #include "eprop_internal.cuh"
@@ -39,11 +42,14 @@ namespace eprop {
 
 constexpr int kLsM = 128;          // neurons per tile (UMMA M)
 constexpr int kLsKC = 32;          // K elements per chunk: one 128-byte swizzle row
-constexpr int kLsNmax = 256;       // window steps per pass (UMMA N <= 256)
+constexpr int kLsNmax = 128;       // window steps per pass (two accumulators of <= 128 columns)
 constexpr int kLsThreads = 256;
 constexpr int kLsAreg = kLsM * 128;        // bytes of one A region (hi or lo)
 constexpr int kLsEreg = kLsNmax * 128;     // bytes of one E region
-constexpr size_t kLsSmem = 1024 + 2 * (size_t)kLsAreg + 2 * (size_t)kLsEreg;
+// dynamic shared memory requested per CTA (the operand regions need less):
+// 100 KB caps the residency at two CTAs per SM
+constexpr size_t kLsSmem = 100 * 1024;
+static_assert(1024 + 2 * (size_t)kLsAreg + 2 * (size_t)kLsEreg <= kLsSmem, "operand regions exceed the request");
 
 // ---- PTX wrappers (tcgen05, sm_100 family)
 
@@ -145,10 +151,12 @@ __global__ void __launch_bounds__(kLsThreads) learning_signal_kernel(const float
     unsigned char *e_hi = base + 2 * kLsAreg, *e_lo = e_hi + kLsEreg;
     const float *Eb = E + (long long)b * U * K;
     float *Lb = L + (long long)b * U * N;
-    // TMEM columns: a power of two >= 32 covering the widest pass
+    // TMEM: two accumulators (hi*hi, corrections) of a power of two >= 32
+    // columns covering the widest pass
     const int npad_max = (min(U, kLsNmax) + 15) & ~15;
-    uint32_t ncols = 32;
-    while ((int)ncols < npad_max) ncols <<= 1;
+    uint32_t half = 32;
+    while ((int)half < npad_max) half <<= 1;
+    const uint32_t ncols = 2 * half;
     if (warp == 0) tmem_alloc(&tmem_slot, ncols);
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -193,9 +201,9 @@ __global__ void __launch_bounds__(kLsThreads) learning_signal_kernel(const float
                 for (int s = 0; s < nks; ++s) {
                     const uint32_t o = 32u * s;                      // 8 TF32 = 32 bytes along K
                     umma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(eh + o), idesc, acc);
+                    umma_tf32(tmem + half, sdesc_sw128(ah + o), sdesc_sw128(el + o), idesc, acc);
+                    umma_tf32(tmem + half, sdesc_sw128(al + o), sdesc_sw128(eh + o), idesc, 1);
                     acc = 1;
-                    umma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(el + o), idesc, 1);
-                    umma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(eh + o), idesc, 1);
                 }
                 umma_commit(&bar);
             }
@@ -214,13 +222,15 @@ __global__ void __launch_bounds__(kLsThreads) learning_signal_kernel(const float
         const int ngrp = npad >> 4;
         const int g_lo = warp < 4 ? 0 : (ngrp + 1) / 2, g_hi = warp < 4 ? (ngrp + 1) / 2 : ngrp;
         for (int g = g_lo; g < g_hi; ++g) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * g), v);
+            uint32_t v[16], w[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * g);
+            tmem_ld16(ta, v);
+            tmem_ld16(ta + half, w);
             if (j < N) {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const int u = 16 * g + c;
-                    if (u < nu) Lb[(long long)(u0 + u) * N + j] = __uint_as_float(v[c]);
+                    if (u < nu) Lb[(long long)(u0 + u) * N + j] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
                 }
             }
         }

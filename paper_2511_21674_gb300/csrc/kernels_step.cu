@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
             const int j = jb + q * kNeuronThreads;
             if (j >= n.n_rec) break;
             psi_row[j] = 0.0f;
+            if (n.R_win) n.R_win[((long long)b * n.U + (r - a0 - 1)) * n.n_rec + j] = 0.0f;
             if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
         }
         continue;
@@ -138,23 +139,53 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
             vth = fmaf(n.beta_a, a_hi[q], n.v_th);
             vth_lo = fmaf(n.beta_a, a_hi[q], n.v_th - vth) + n.beta_a * a_lo[q];
         }
-        // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
-        {
-            float e;
-            two_sum(u_hi, -zp * vth, u_hi, e);
-            u_lo += e - zp * vth_lo;
+        if (n.reset_mode == 1 && zp != 0.0f) {
+            // fixed reset: v' = v_reset + I (the decayed membrane is replaced)
+            float s, e;
+            two_sum(n.v_reset, u_hi, s, e);
+            const float lo = e + u_lo;
+            const float hi = s + lo;
+            v_lo[q] = lo - (hi - s);
+            v_hi[q] = hi;
+        } else {
+            // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
+            if (n.reset_mode == 0) {
+                float e;
+                two_sum(u_hi, -zp * vth, u_hi, e);
+                u_lo += e - zp * vth_lo;
+            }
+            comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi[q], v_lo[q]);
         }
-        comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi[q], v_lo[q]);
         n.v[nb] = v_hi[q];
         n.v_lo[nb] = v_lo[q];
         const float m = (v_hi[q] - vth) + (v_lo[q] - vth_lo);
         const bool refractory = ref[q] > 0;
         int z;
-        if (n.forced) z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
-        else z = (!refractory && m > 0.0f) ? 1 : 0;
-        const float hh = 1.0f - n.beta_sg * fabsf(m);
-        const float psi = refractory ? 0.0f : n.gamma * fmaxf(hh, 0.0f);
+        if (n.forced) {
+            z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
+        } else if (n.if_period > 0) {
+            // ignore-and-fire: a fixed schedule with the neuron's own phase
+            const uint32_t ph = (uint32_t)(mix64(n.if_seed ^ (uint64_t)j) >> 32) % (uint32_t)n.if_period;
+            z = ((t_abs + (long long)ph) % n.if_period) == 0 ? 1 : 0;
+        } else {
+            z = (!refractory && m > 0.0f) ? 1 : 0;
+        }
+        float psi;
+        if (n.surrogate == 1) {      // Eq. exponential-surrogate-gradient
+            psi = refractory ? 0.0f : n.gamma * expf(-n.beta_sg * fabsf(m));
+        } else {                     // Eq. piecewise-linear-surrogate-gradient
+            const float hh = 1.0f - n.beta_sg * fabsf(m);
+            psi = refractory ? 0.0f : n.gamma * fmaxf(hh, 0.0f);
+        }
         psi_row[j] = psi;
+        if (n.R_win) {
+            // moving-average rate (Eq. ema-rate) and the regularisation
+            // signal of Eq. ema-gradient, with G_beta's factor (1 - beta)
+            const float f = n.beta_reg * n.rate[nb] + (1.0f - n.beta_reg) * (float)z;
+            n.rate[nb] = f;
+            n.R_win[((long long)b * n.U + (r - a0 - 1)) * n.n_rec + j] =
+                n.c_reg * (1.0f - n.beta_reg) * (f - n.f_target);
+        }
         if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = psi;
         int rf = ref[q];
         if (refractory) rf -= 1;
@@ -233,6 +264,11 @@ __device__ void readout_finish(const Net &n, int i, int b) {
         const float diff = y - tgt;
         if (has_k) E[k] = win * diff;
         l = has_k ? 0.5f * win * diff * diff : 0.0f;
+    } else if (n.loss == 2) {        // temporal MSE (Eq. temporal-mse)
+        const float diff = y - tgt;
+        const float invK = 1.0f / (float)n.n_out;
+        if (has_k) E[k] = win * (2.0f * invK) * diff;
+        l = has_k ? win * diff * diff * invK : 0.0f;
     } else {
         const float mx = block_max(has_k ? y : -INFINITY, sh);
         const float ex = has_k ? expf(y - mx) : 0.0f;

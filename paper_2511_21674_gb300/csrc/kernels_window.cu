@@ -91,7 +91,7 @@ __global__ void filter_error_kernel(Net n) {
 // the whole window beforehand by one strided-batched SGEMM, L_win) are
 // loaded into registers, then the adjoint recursion writes the per-step
 // tables and, at the window start, the window coefficients.
-template <bool ALIF>
+template <bool ALIF, bool REG>
 __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     constexpr int kTC = ALIF ? 16 : 32;     // window steps per chunk
     const int b = blockIdx.y;
@@ -102,6 +102,11 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     const bool act = j < N;
     const float *psi_g = n.psi_hist + (long long)b * (U + 1) * N + (act ? j : 0);
     const float *L_g = n.L_win + (long long)b * U * N + (act ? j : 0);    // [U][N], row u - 1 = step u
+    // firing-rate regularisation (single-window calls only): a second
+    // filtered copy of the eligibility trace, F_beta(e), weighted by the
+    // signal R^t (Eq. ema-gradient); its adjoint mb joins me wherever the
+    // eligibility e^t enters (e^t feeds both filters)
+    const float *R_g = REG ? n.R_win + (long long)b * U * N + (act ? j : 0) : nullptr;
     // The adjoint sweep is the per-window reduction of the gradient.  For
     // ALIF the eligibility psi (zbar - beta eps_a) is a near-cancellation of
     // two long-memory traces, so the sweep runs in FP64 there (FP32 loses up
@@ -119,6 +124,8 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     R ez = 0, ea = 0, ee = 1;
     R az = 0, aa = 1, ae = 0;
     R pn = 0;
+    R mb = 0;                                  // adjoint of F_beta(e) (regularisation)
+    const R breg = (R)n.beta_reg;
     const float psi_b = act ? psi_g[(long long)U * N] : 0.f;
     const long long qbase = ((long long)b * U) * N + j;
     // Steps are taken backwards in chunks of kTC: the chunk's psi and
@@ -134,6 +141,12 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
             Lc[c] = in ? L_g[(long long)(u - 1) * N] : 0.f;
             Pc[c] = in ? psi_g[(long long)u * N] : 0.f;
         }
+        float Rc[REG ? kTC : 1];
+#pragma unroll
+        for (int c = 0; c < (REG ? kTC : 1); ++c) {
+            const int u = u1 - c;
+            Rc[c] = (REG && act && u >= u0) ? R_g[(long long)(u - 1) * N] : 0.f;
+        }
         Pc[kTC] = act ? psi_g[(long long)(u0 - 1) * N] : 0.f;   // psi of the step before the chunk
         if (!act) continue;
 #pragma unroll
@@ -142,11 +155,14 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
             if (u < u0) break;
             const R p = Pc[c];                               // psi^{a0+u}
             if (u < U) {
-                // x -> (A^{u+1})^T x with A^{u+1} from psi^u = p, psi^{u+1} = pn
+                // x -> (A^{u+1})^T x with A^{u+1} from psi^u = p, psi^{u+1} = pn;
+                // D = adjoint of e^{u+1} (both filters of the eligibility)
+                const R D = REG ? me + mb : me;
+                if (REG) mb = breg * mb;
                 if (ALIF) {
                     const R g1 = alpha - beta * p, g2 = rho - beta * p;
-                    R nz = alpha * mz + p * ma + pn * g1 * me;
-                    R na = g2 * ma - beta * pn * g2 * me;
+                    R nz = alpha * mz + p * ma + pn * g1 * D;
+                    R na = g2 * ma - beta * pn * g2 * D;
                     R ne = ke * me;
                     mz = nz; ma = na; me = ne;
                     nz = alpha * ez + p * ea + pn * g1 * ee;
@@ -158,29 +174,34 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
                     ne = ke * ae;
                     az = nz; aa = na; ae = ne;
                 } else {
-                    mz = alpha * mz + alpha * pn * me;
+                    mz = alpha * mz + alpha * pn * D;
                     me = ke * me;
                     ez = alpha * ez + alpha * pn * ee;
                     ee = ke * ee;
                 }
             }
             me += (R)Lc[c];
+            if (REG) mb += (R)Rc[c];
+            const R De = REG ? me + mb : me;           // adjoint of e^u
             if (ALIF) {
                 reinterpret_cast<float4 *>(n.qp)[qbase + (long long)(u - 1) * N] =
-                    make_float4((float)(mz + p * me), (float)(ez + p * ee), (float)(az + p * ae), 0.f);
+                    make_float4((float)(mz + p * De), (float)(ez + p * ee), (float)(az + p * ae), 0.f);
             } else {
                 reinterpret_cast<float2 *>(n.qp)[qbase + (long long)(u - 1) * N] =
-                    make_float2((float)(mz + p * me), (float)(ez + p * ee));
+                    make_float2((float)(mz + p * De), (float)(ez + p * ee));
             }
             pn = p;
         }
         if (u0 == 1) {
             // step a0 (u = 0): the window coefficients c = (A^{a0+1})^T mu^{a0+1}
+            // (regularisation runs without carried state: no coefficients
+            // of F_beta are kept, only G's adjoint sees it)
             const R p = Pc[kTC];
+            const R D = REG ? me + mb : me;
             if (ALIF) {
                 const R g1 = alpha - beta * p, g2 = rho - beta * p;
-                R nz = alpha * mz + p * ma + pn * g1 * me;
-                R na = g2 * ma - beta * pn * g2 * me;
+                R nz = alpha * mz + p * ma + pn * g1 * D;
+                R na = g2 * ma - beta * pn * g2 * D;
                 R ne = ke * me;
                 mz = nz; ma = na; me = ne;
                 nz = alpha * ez + p * ea + pn * g1 * ee;
@@ -192,7 +213,7 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
                 ne = ke * ae;
                 az = nz; aa = na; ae = ne;
             } else {
-                mz = alpha * mz + alpha * pn * me;
+                mz = alpha * mz + alpha * pn * D;
                 me = ke * me;
                 ez = alpha * ez + alpha * pn * ee;
                 ee = ke * ee;
@@ -561,7 +582,10 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
                 } else {            // rows with more spikes than the cache holds
                     G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - dl), r_end - dl, dl, qa + j, ebar, epsa);
                 }
-                __stcs(n.w + q, wv[u] - step * G);
+                {
+                    const float wn = window_update(n, q, wv[u], G);
+                    if (!n.adam) __stcs(n.w + q, wn);
+                }
                 if (STATE) {
                     store_trace(n.ebar, q, ebar, n.trace_bf16);
                     if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
@@ -872,7 +896,10 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                                                  r_end - dl, dl, qa + j, ebar, epsa);
                     }
                 }
-                if (G != 0.f) __stcs(wq + idx, wv[u] - step * G);
+                if (G != 0.f) {
+                    const float wn = window_update(n, d.q0 + idx, wv[u], G);
+                    if (!n.adam) __stcs(wq + idx, wn);
+                }
                 if (TB) __stcs(reinterpret_cast<uint16_t *>(n.ebar) + d.q0 + idx,
                                __bfloat16_as_ushort(__float2bfloat16_rn(ebar)));
                 else __stcs(reinterpret_cast<float *>(n.ebar) + d.q0 + idx, ebar);
@@ -943,7 +970,11 @@ __global__ void __launch_bounds__(256) trace_batched_kernel(Net n) {
                     });
                 }
             }
-            n.w[q] -= n.lr * n.inv_B * G;
+            {
+                const float w0 = n.w[q];
+                const float wn = window_update(n, q, w0, G);
+                if (!n.adam) n.w[q] = wn;
+            }
             if (n.record_grad) n.grad[q] += n.inv_B * G;
         }
         __syncwarp();
@@ -966,7 +997,7 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
     const float *zk_cur = n.zk + (long long)par * n.B * N;
     float *zk_nxt = n.zk + (long long)(par ^ 1) * n.B * N;
     const float kU = exp2f(n.log2_kappa * (float)U);
-    const bool upd = n.out_mask[j] != 0;
+    const uint8_t *mrow = n.out_mask + j * K;          // per-weight readout mask
     if ((K & 3) == 0) {
         // four readouts per lane (float4 rows; K % 4 == 0 keeps every row
         // 16-byte aligned).  The weight row is requested first and the
@@ -982,6 +1013,9 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
             float4 w = make_float4(0.f, 0.f, 0.f, 0.f), gg = w;
             float4 *wp = reinterpret_cast<float4 *>(n.w_out + j * K + k);
             float4 *gp = reinterpret_cast<float4 *>(n.grad_out + j * K + k);
+            uchar4 mk = make_uchar4(0, 0, 0, 0);
+            if (has_k) mk = *reinterpret_cast<const uchar4 *>(mrow + k);
+            const bool upd = (mk.x | mk.y | mk.z | mk.w) != 0;
             if (upd && has_k) {
                 w = *wp;
                 if (n.record_grad) gg = *gp;
@@ -1021,8 +1055,27 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
                 if (k0 == 0 && lane == 0) zk_nxt[(long long)b * N + j] = zn;
             }
             if (upd && has_k) {
-                w.x -= s * g.x; w.y -= s * g.y; w.z -= s * g.z; w.w -= s * g.w;
-                *wp = w;
+                // weights without a synapse (mask 0) keep their value and get
+                // no gradient
+                if (!mk.x) g.x = 0.f;
+                if (!mk.y) g.y = 0.f;
+                if (!mk.z) g.z = 0.f;
+                if (!mk.w) g.w = 0.f;
+                if (n.adam) {
+                    *reinterpret_cast<float4 *>(n.gwin_out + j * K + k) =
+                        make_float4(n.inv_B * g.x, n.inv_B * g.y, n.inv_B * g.z, n.inv_B * g.w);
+                } else {
+                    const float4 w0 = w;
+                    if (mk.x) w.x -= s * g.x;
+                    if (mk.y) w.y -= s * g.y;
+                    if (mk.z) w.z -= s * g.z;
+                    if (mk.w) w.w -= s * g.w;
+                    if (n.sign_mask & 4) {
+                        w.x = keep_sign(w0.x, w.x); w.y = keep_sign(w0.y, w.y);
+                        w.z = keep_sign(w0.z, w.z); w.w = keep_sign(w0.w, w.w);
+                    }
+                    *wp = w;
+                }
                 if (n.record_grad) {
                     gg.x += n.inv_B * g.x; gg.y += n.inv_B * g.y; gg.z += n.inv_B * g.z; gg.w += n.inv_B * g.w;
                     *gp = gg;
@@ -1047,9 +1100,15 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
             g += gb;
             if (k0 == 0 && lane == 0) zk_nxt[(long long)b * N + j] = zn;
         }
-        if (upd && has_k) {
+        if (has_k && mrow[k]) {
             const long long idx = j * K + k;
-            n.w_out[idx] -= n.lr * n.inv_B * g;
+            if (n.adam) {
+                n.gwin_out[idx] = n.inv_B * g;
+            } else {
+                const float w0 = n.w_out[idx];
+                const float wn = w0 - n.lr * n.inv_B * g;
+                n.w_out[idx] = (n.sign_mask & 4) ? keep_sign(w0, wn) : wn;
+            }
             if (n.record_grad) n.grad_out[idx] += n.inv_B * g;
         }
     }
@@ -1156,7 +1215,57 @@ __global__ void unpack_raster_kernel(Net n, unsigned char *dst) {
     }
 }
 
+// Adam step at a window end (Eq. adam with the reordering of Eq. eta-adam-
+// fast and Eq. delta-w-adam-fast, constant eps_hat): every synapse and every
+// readout weight of a projecting neuron, from the window's batch-mean
+// gradient left by the trace and readout kernels (cleared here for the next
+// window).  k = the network's Adam steps so far + 1 (device counter, so a
+// captured call replays correctly); the counter advances in the next kernel.
+__global__ void adam_kernel(Net n) {
+    const int k = n.clock->adam_k + 1;
+    const double bc = sqrt(1.0 - pow((double)n.adam_b2, (double)k)) / (1.0 - pow((double)n.adam_b1, (double)k));
+    const float eta = (float)((double)n.lr * bc);
+    const long long nout = (long long)n.n_rec * n.n_out;
+    const long long tot = n.nnz + nout;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        float *gp, *mp, *vp, *wp;
+        bool fixed;
+        if (i < n.nnz) {
+            gp = n.gwin + i; mp = n.adam_m + i; vp = n.adam_v + i; wp = n.w + i;
+            fixed = n.sign_mask && sign_fixed(n, i);
+        } else {
+            const long long o = i - n.nnz;
+            if (!n.out_mask[o]) continue;
+            gp = n.gwin_out + o; mp = n.adam_m_out + o; vp = n.adam_v_out + o; wp = n.w_out + o;
+            fixed = (n.sign_mask & 4) != 0;
+        }
+        const float g = *gp;
+        *gp = 0.0f;
+        const float m = n.adam_b1 * *mp + (1.0f - n.adam_b1) * g;
+        const float v = n.adam_b2 * *vp + (1.0f - n.adam_b2) * g * g;
+        *mp = m;
+        *vp = v;
+        const float w0 = *wp;
+        const float w = w0 - eta * m / (sqrtf(v) + n.adam_eps);
+        *wp = fixed ? keep_sign(w0, w) : w;
+    }
+}
+
+__global__ void adam_count_kernel(Net n) {
+    if (threadIdx.x == 0) n.clock->adam_k += 1;
+}
+
 // ----------------------------------------------------------------- launches
+
+void launch_adam(const Net &n, int sm_count, cudaStream_t st) {
+    const long long tot = n.nnz + (long long)n.n_rec * n.n_out;
+    long long blocks = (tot + 255) / 256;
+    if (blocks > 8LL * sm_count) blocks = 8LL * sm_count;
+    if (blocks < 1) blocks = 1;
+    adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(n);
+    adam_count_kernel<<<1, 32, 0, st>>>(n);
+}
 
 void prepare_kernel_attributes() {
     const int tl = 200 * 1024;
@@ -1188,8 +1297,13 @@ void launch_filter_error(const Net &n, int i_end, cudaStream_t st) {
 int launch_tables(const Net &n, int i_end, cudaStream_t st) {
     const int bd = 128;
     const dim3 grid((n.n_rec + bd - 1) / bd, n.B);
-    if (n.alif) tables_kernel<true><<<grid, bd, 0, st>>>(n, i_end);
-    else tables_kernel<false><<<grid, bd, 0, st>>>(n, i_end);
+    if (n.R_win) {
+        if (n.alif) tables_kernel<true, true><<<grid, bd, 0, st>>>(n, i_end);
+        else tables_kernel<false, true><<<grid, bd, 0, st>>>(n, i_end);
+    } else {
+        if (n.alif) tables_kernel<true, false><<<grid, bd, 0, st>>>(n, i_end);
+        else tables_kernel<false, false><<<grid, bd, 0, st>>>(n, i_end);
+    }
     return 0;
 }
 

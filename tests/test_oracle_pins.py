@@ -168,24 +168,33 @@ torch = pytest.importorskip("torch")
 
 
 class _Spike(torch.autograd.Function):
-    """Heaviside forward (values given), surrogate psi backward."""
+    """Heaviside forward (values given), surrogate psi backward: piecewise
+    linear (Eq. piecewise-linear-surrogate-gradient) or exponential
+    (Eq. exponential-surrogate-gradient)."""
 
     @staticmethod
-    def forward(ctx, m, z_given, refr, gamma, beta):
+    def forward(ctx, m, z_given, refr, gamma, beta, kind=0):
         ctx.save_for_backward(m, refr)
-        ctx.gamma, ctx.beta = gamma, beta
+        ctx.gamma, ctx.beta, ctx.kind = gamma, beta, kind
         return z_given.clone()
 
     @staticmethod
     def backward(ctx, gz):
         m, refr = ctx.saved_tensors
-        psi = ctx.gamma * torch.clamp(1.0 - ctx.beta * m.abs(), min=0.0) * (~refr)
-        return gz * psi, None, None, None, None
+        if ctx.kind == 1:
+            psi = ctx.gamma * torch.exp(-ctx.beta * m.abs()) * (~refr)
+        else:
+            psi = ctx.gamma * torch.clamp(1.0 - ctx.beta * m.abs(), min=0.0) * (~refr)
+        return gz * psi, None, None, None, None, None
 
 
 def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
     """Autograd gradient of the batch-mean loss; recurrent spike inputs and
-    the reset term are detached, the neuron's own adaptation path is not."""
+    the reset term are detached, the neuron's own adaptation path is not.
+    Variants of the spec: exponential surrogate, fixed reset (the whole
+    reset correction detached), temporal MSE, and the firing-rate
+    regularisation loss (c_reg / 2) sum_t sum_j (f_j^t - f*)^2 with the
+    exponential moving average rate (Eq. ema-rate)."""
     s = net["spec"]
     B, N, K, NI = s.batch, s.n_rec, s.n_out, s.n_in
     alpha, rho = math.exp(-1 / s.tau_m), math.exp(-1 / s.tau_a)
@@ -202,6 +211,7 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
         v = torch.zeros(N, dtype=torch.float64)
         a = torch.zeros(N, dtype=torch.float64)
         zprev = torch.zeros(N, dtype=torch.float64)
+        f = torch.zeros(N, dtype=torch.float64)
         ref = np.zeros(N, dtype=np.int64)
         y = torch.zeros(K, dtype=torch.float64)
         hist = {}
@@ -214,10 +224,13 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
             I = torch.zeros(N, dtype=torch.float64).index_add(0, col, w * arrive)
             a = rho * a + zprev
             vth = s.v_th + beta_a * a
-            v = alpha * v + I - (zprev * vth).detach()
+            if s.reset_mode == 1:
+                v = alpha * v + I + (zprev * (s.v_reset - alpha * v)).detach()
+            else:
+                v = alpha * v + I - (zprev * vth).detach()
             refr = torch.tensor(ref > 0)
             zg = torch.tensor(z_raster[b, t - 1].astype(np.float64))
-            z = _Spike.apply(v - vth, zg, refr, s.gamma, s.beta_sg)
+            z = _Spike.apply(v - vth, zg, refr, s.gamma, s.beta_sg, s.surrogate)
             ref = np.where(ref > 0, ref - 1, 0)
             ref[z_raster[b, t - 1] > 0] = s.t_ref
             hist[t] = torch.cat([torch.tensor(x_raster[b, t - 1].astype(np.float64)),
@@ -227,8 +240,13 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
             tg = torch.tensor(targets[b, t - 1].astype(np.float64))
             if s.loss == 0:
                 total = total + 0.5 * win * ((y - tg) ** 2).sum()
+            elif s.loss == 2:
+                total = total + win * ((y - tg) ** 2).sum() / K
             else:
                 total = total - win * (tg * torch.log_softmax(y, 0)).sum()
+            if s.c_reg != 0.0:
+                f = s.beta_reg * f + (1.0 - s.beta_reg) * z
+                total = total + 0.5 * s.c_reg * ((f - s.f_target) ** 2).sum()
             zprev = z
     (total / B).backward()
     return w.grad.numpy(), wo.grad.numpy()
@@ -255,17 +273,32 @@ def _random_small(model, loss, seed, B=2, T=40, n_in=3, N=6, K=2, max_delay=3):
         tg[np.arange(B), :, rng.integers(0, K, B)] = 1.0
     lengths = np.array([T - 7 * b for b in range(B)], np.int32)
     window = np.ones((B, T), np.uint8)
-    if loss == 1:
+    if loss >= 1:
         window[:] = 0
         for b in range(B):
             window[b, lengths[b] - 10:lengths[b]] = 1
     return net, x, tg, window, lengths
 
 
-@pytest.mark.parametrize("model,loss", [(0, 0), (1, 0), (0, 1), (1, 1)])
-def test_eprop_equals_bptt_with_stop_gradients(model, loss):
-    net, x, tg, window, lengths = _random_small(model, loss, seed=10 + 2 * model + loss)
+# e-prop+ variants, each alone: exponential surrogate, fixed reset, temporal
+# MSE, firing-rate regularisation (Eq. ema-gradient)
+VARIANTS = {
+    "plain": {},
+    "exp_surrogate": dict(surrogate=1),
+    "fixed_reset": dict(reset_mode=1, v_reset=0.15),
+    "rate_reg": dict(c_reg=3.0, f_target=0.05, beta_reg=0.9),
+}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("model,loss", [(0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2)])
+def test_eprop_equals_bptt_with_stop_gradients(model, loss, variant):
+    if loss == 2 and variant != "plain":
+        pytest.skip("temporal MSE is checked with the plain neuron")
+    net, x, tg, window, lengths = _random_small(model, loss, seed=10 + 2 * model + min(loss, 1))
     s = net["spec"]
+    for k, v in VARIANTS[variant].items():
+        setattr(s, k, v)
     o = oracle.Oracle(s, net["ptr"], net["col"], net["w"], net["delay"], net["w_out"],
                       net["out_mask"])
     x_ptr, x_ids = raster_to_lists(x)

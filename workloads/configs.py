@@ -21,6 +21,20 @@ Workloads (steps of 1 ms):
   autapses or multapses, 80 % excitatory / 20 % inhibitory sources, integer
   delays 1..5, external Poisson drive, random feedback, regression targets.
 
+* ``evidence_accumulation`` -- the cue task (Methods, "Evidence
+  accumulation"): left/right cue populations, a recall population and
+  background noise, label = the side with more cues, softmax cross-entropy
+  in the recall window (the learning window), ALIF neurons for memory.
+* ``scaling_network`` -- the scaling experiment's network (Methods,
+  "Scaling"): ignore-and-fire neurons at 5 Hz with random phases, Poisson
+  inputs, input in-degree 100, recurrent in-degree 10,000 (no autapses or
+  multapses), 10 readouts with in-degree 1000, feedback out-degree 100.
+
+Options shared by the sparse networks: ``fb_outdeg`` (each readout's
+feedback reaches only that many recurrent neurons) and ``dale`` (the
+excitatory / inhibitory sign of every recurrent synapse is kept through
+learning).
+
 The module holds the inputs' structure only; none of the learning method's
 arithmetic lives here.
 """
@@ -38,6 +52,7 @@ from . import hashrng as H
 _TAG_PRE, _TAG_DELAY, _TAG_W1, _TAG_W2, _TAG_WO1, _TAG_WO2 = 11, 12, 13, 14, 15, 16
 _TAG_B1, _TAG_B2, _TAG_X, _TAG_TGT, _TAG_BERN, _TAG_WIN = 17, 18, 19, 20, 21, 22
 _TAG_CLS, _TAG_LEN, _TAG_DRV = 23, 24, 25
+_TAG_FB, _TAG_OUT, _TAG_IN, _TAG_CUE, _TAG_IF = 26, 27, 28, 29, 30
 
 
 @dataclasses.dataclass
@@ -70,6 +85,20 @@ class Spec:
     drive_rate: float = 0.0        # mean drive events per neuron and step
     drive_seed: int = 0
     seed: int = 1234
+    # e-prop+ variants and constraints (defaults: the plain method)
+    surrogate: int = 0             # 0 piecewise linear, 1 exponential
+    reset_mode: int = 0            # 0 soft (subtract v_th), 1 fixed value v_reset
+    v_reset: float = 0.0
+    c_reg: float = 0.0             # firing-rate regularisation coefficient (0: off)
+    f_target: float = 0.0          # target rate in spikes per step
+    beta_reg: float = 0.0          # EMA constant of the rate filter
+    sign_mask: int = 0             # fixed weight signs: 1 input, 2 recurrent, 4 readout
+    optimizer: int = 0             # 0 SGD, 1 Adam
+    adam_b1: float = 0.9
+    adam_b2: float = 0.999
+    adam_eps: float = 1e-7         # TensorFlow's constant eps_hat
+    if_period: int = 0             # ignore-and-fire period in steps (0: off)
+    if_seed: int = 0
 
     @property
     def alpha(self) -> float:
@@ -324,6 +353,22 @@ def event_classification(seed: int = 1235, batch: int = 64, T: int = 350,
                 lengths=lengths, classes=cls)
 
 
+def sparse_feedback(seed: int, n_rec: int, n_out: int, outdeg: int, std: float = 1.0) -> np.ndarray:
+    """B [n_rec, n_out] with exactly `outdeg` nonzero N(0, std^2) entries per
+    readout k: target m of readout k is drawn uniformly inside stratum m of
+    the neurons (distinct targets by construction)."""
+    if outdeg > n_rec:
+        raise ValueError("feedback out-degree larger than the population")
+    fb = np.zeros((n_rec, n_out), dtype=np.float32)
+    s = n_rec // outdeg
+    m = np.arange(outdeg, dtype=np.uint64)
+    for k in range(n_out):
+        kk = np.full(outdeg, k, dtype=np.uint64)
+        j = m.astype(np.int64) * s + (_u64(seed, _TAG_FB, kk, m) % np.uint64(s)).astype(np.int64)
+        fb[j, k] = (std * _normal(seed, _TAG_B2, j.astype(np.uint64), kk)).astype(np.float32)
+    return fb
+
+
 def _ei_network_np(spec: Spec, k_in: int, J: float, g: float, seed: int):
     n = spec.n_rec
     pre, post, m = fixed_indegree_pairs(n, n, k_in, seed, True)
@@ -337,7 +382,8 @@ def sparse_balanced(seed: int = 1236, n_rec: int = 100_000, k_in: int = 1000,
                     T: int = 2000, n_out: int = 1, n_coupled: int = 500,
                     J: float = 0.01, g: float = 5.0,
                     drive_weight: float = 0.04, drive_rate: float = 1.2,
-                    name: str = "sparse_balanced", **over) -> dict:
+                    name: str = "sparse_balanced", fb_outdeg: Optional[int] = None,
+                    dale: bool = False, **over) -> dict:
     """E/I network with fixed in-degree and delays 1..5, numpy build."""
     # lr 1e-6 keeps the firing rate near its configured value while the
     # weights learn (1e-4 drives the network into a high-rate state)
@@ -355,6 +401,10 @@ def sparse_balanced(seed: int = 1236, n_rec: int = 100_000, k_in: int = 1000,
                      axis=1) * mask[:, None]
     fb = np.stack([_weights(seed, _TAG_B1, j, np.full(n_rec, k), 1.0)
                    for k in range(n_out)], axis=1)
+    if fb_outdeg is not None:
+        fb = sparse_feedback(seed, n_rec, n_out, fb_outdeg)
+    if dale:
+        spec.sign_mask |= 2
     B = spec.batch
     return dict(spec=spec, ptr=ptr, col=col, w=wv, delay=dv,
                 w_out=np.ascontiguousarray(w_out, dtype=np.float32),
@@ -380,7 +430,8 @@ def million_sparse_spec(n_rec: int = 1_000_000, T: int = 1000, n_out: int = 100,
 
 def million_sparse(seed: int = 1237, n_rec: int = 1_000_000, k_in: int = 1000,
                    T: int = 1000, n_out: int = 100, J: float = 0.01,
-                   g: float = 5.0, **over) -> dict:
+                   g: float = 5.0, fb_outdeg: Optional[int] = None, dale: bool = False,
+                   **over) -> dict:
     """Million-neuron workload built with numpy (use for scaled replicas).
 
     The full-size instance is built on the GPU by
@@ -394,6 +445,10 @@ def million_sparse(seed: int = 1237, n_rec: int = 1_000_000, k_in: int = 1000,
                      axis=1)
     fb = np.stack([_weights(seed, _TAG_B1, j, np.full(n_rec, k), 1.0 / math.sqrt(n_out))
                    for k in range(n_out)], axis=1)
+    if fb_outdeg is not None:
+        fb = sparse_feedback(seed, n_rec, n_out, fb_outdeg)
+    if dale:
+        spec.sign_mask |= 2
     B = spec.batch
     return dict(spec=spec, ptr=ptr, col=col, w=wv, delay=dv,
                 w_out=np.ascontiguousarray(w_out, dtype=np.float32),
@@ -404,3 +459,144 @@ def million_sparse(seed: int = 1237, n_rec: int = 1_000_000, k_in: int = 1000,
                 targets=sinusoid_targets(seed, T, n_out, B),
                 window=np.ones((B, T), dtype=np.uint8),
                 lengths=np.full(B, T, dtype=np.int32))
+
+
+# ---------------------------------------------------------------------------
+# evidence accumulation (Methods, "Evidence accumulation")
+
+
+def evidence_accumulation(seed: int = 1240, batch: int = 32, n_cues: int = 7,
+                          t_cue: int = 100, t_gap: int = 50, t_delay: int = 1000,
+                          t_recall: int = 150, pop: int = 10, n_rec: int = 100,
+                          rate_cue_hz: float = 40.0, rate_bg_hz: float = 10.0,
+                          sample_seed: Optional[int] = None, **over) -> dict:
+    """The cue task: input populations (pop channels each) 0 left cues,
+    1 right cues, 2 recall cue, 3 background noise.  Each of n_cues cue slots
+    shows one side's population at rate_cue for t_cue steps, then t_gap
+    silent steps; after t_delay steps of background only, the recall
+    population fires for t_recall steps.  The label is the side with more
+    cues; the softmax cross-entropy is applied in the recall steps only (the
+    learning window).  ALIF neurons (tau_a 2000 ms) keep the evidence; fully
+    connected recurrence without autapses; two readouts; Adam."""
+    ss = seed if sample_seed is None else sample_seed
+    n_in = 4 * pop
+    T = n_cues * (t_cue + t_gap) + t_delay + t_recall
+    spec = Spec(name="evidence_accumulation", n_in=n_in, n_rec=n_rec, n_out=2,
+                batch=batch, T=T, neuron_model=1, tau_a=2000.0, beta_a=1.7,
+                loss=1, lr=5e-3, optimizer=1, max_delay=1, seed=seed)
+    for key, val in over.items():
+        setattr(spec, key, val)
+    pre_i = np.repeat(np.arange(n_in), n_rec)
+    post_i = np.tile(np.arange(n_rec), n_in)
+    w_i = _weights(seed, _TAG_W1, pre_i, post_i, 1.0 / math.sqrt(n_in))
+    pre_r, post_r, _ = fixed_indegree_pairs(n_rec, n_rec, n_rec - 1, seed, True)
+    w_r = _weights(seed, _TAG_W2, pre_r, post_r, 1.0 / math.sqrt(n_rec))
+    src = np.concatenate([pre_i, pre_r + n_in])
+    post = np.concatenate([post_i, post_r])
+    w = np.concatenate([w_i, w_r])
+    d = np.ones(src.shape[0], dtype=np.uint8)
+    ptr, col, wv, dv = to_csr(src, post, w, d, n_in + n_rec)
+    j = np.arange(n_rec)
+    w_out = np.stack([_weights(seed, _TAG_WO1, j, np.full(n_rec, k), 1.0 / math.sqrt(n_rec))
+                      for k in range(2)], axis=1)
+    # cue sides per sample and slot; label = majority side (n_cues is odd)
+    bb = np.arange(batch, dtype=np.uint64)
+    sides = np.stack([(_u64(ss, _TAG_CUE, bb, np.uint64(c)) & np.uint64(1)).astype(np.int64)
+                      for c in range(n_cues)], axis=1)                 # [batch, n_cues]
+    label = (sides.sum(axis=1) * 2 > n_cues).astype(np.int64)          # 1: right wins
+    rate = np.zeros((batch, T, n_in))
+    rate[:, :, 3 * pop:] = rate_bg_hz
+    for c in range(n_cues):
+        t0 = c * (t_cue + t_gap)
+        for b in range(batch):
+            p0 = sides[b, c] * pop
+            rate[b, t0:t0 + t_cue, p0:p0 + pop] = rate_cue_hz
+    t_rec0 = T - t_recall
+    rate[:, t_rec0:, 2 * pop:3 * pop] = rate_cue_hz
+    u = _uniform(ss, _TAG_X, bb[:, None, None] * np.uint64(n_in) + np.arange(n_in, dtype=np.uint64)[None, None, :],
+                 np.arange(1, T + 1, dtype=np.uint64)[None, :, None])
+    raster = u < rate * spec.dt / 1000.0
+    x_ptr, x_ids = step_lists(raster)
+    targets = np.zeros((batch, T, 2), dtype=np.float32)
+    targets[np.arange(batch), :, label] = 1.0
+    window = np.zeros((batch, T), dtype=np.uint8)
+    window[:, t_rec0:] = 1
+    return dict(spec=spec, ptr=ptr, col=col, w=wv, delay=dv,
+                w_out=np.ascontiguousarray(w_out, dtype=np.float32),
+                out_mask=np.ones(n_rec, dtype=np.uint8), feedback=None,
+                x_ptr=x_ptr, x_ids=x_ids, targets=targets, window=window,
+                lengths=np.full(batch, T, dtype=np.int32), labels=label)
+
+
+# ---------------------------------------------------------------------------
+# the scaling experiment's network (Methods, "Scaling")
+
+
+def scaling_spec(n_rec: int = 128_000, n_in: int = 1000, n_out: int = 10, T: int = 20_000,
+                 update_interval: int = 1000, rate_hz: float = 5.0, seed: int = 1241, **over) -> Spec:
+    period = int(round(1000.0 / rate_hz))
+    spec = Spec(name="scaling", n_in=n_in, n_rec=n_rec, n_out=n_out, T=T, feedback=1,
+                update_interval=update_interval, continuous=1, lr=1e-6, max_delay=5,
+                if_period=period, if_seed=seed * 7919 + 29, seed=seed)
+    for key, val in over.items():
+        setattr(spec, key, val)
+    return spec
+
+
+def poisson_inputs(seed: int, n_in: int, T: int, rate_hz: float, batch: int = 1):
+    """Poisson spike generators (frozen): (x_ptr, x_ids)."""
+    ii = np.arange(n_in, dtype=np.uint64)[None, None, :]
+    tt = np.arange(1, T + 1, dtype=np.uint64)[None, :, None]
+    bb = np.arange(batch, dtype=np.uint64)[:, None, None]
+    raster = _uniform(seed, _TAG_IN, ii + np.uint64(n_in) * bb, tt) < rate_hz / 1000.0
+    return step_lists(raster)
+
+
+def readout_indegree_mask(seed: int, n_rec: int, n_out: int, k_out: int) -> np.ndarray:
+    """[n_rec, n_out] mask with exactly k_out recurrent sources per readout
+    (stratified draw, distinct sources)."""
+    mask = np.zeros((n_rec, n_out), dtype=np.uint8)
+    s = n_rec // k_out
+    m = np.arange(k_out, dtype=np.uint64)
+    for k in range(n_out):
+        kk = np.full(k_out, k, dtype=np.uint64)
+        j = m.astype(np.int64) * s + (_u64(seed, _TAG_OUT, kk, m) % np.uint64(s)).astype(np.int64)
+        mask[j, k] = 1
+    return mask
+
+
+def scaling_network(seed: int = 1241, n_rec: int = 128_000, k_rec: int = 10_000, n_in: int = 1000,
+                    k_in: int = 100, n_out: int = 10, k_out: int = 1000, fb_outdeg: int = 100,
+                    T: int = 20_000, update_interval: int = 1000, rate_hz: float = 5.0,
+                    J: float = 0.001, g: float = 5.0, dale: bool = False, **over) -> dict:
+    """numpy build of the scaling network (use scaled-down sizes here; the
+    full network is built on the GPU by `gpu_build.scaling_torch`): inputs
+    first in the CSR, recurrent E/I weights +J / -gJ (80/20 by source),
+    input weights +J."""
+    spec = scaling_spec(n_rec=n_rec, n_in=n_in, n_out=n_out, T=T,
+                        update_interval=update_interval, rate_hz=rate_hz, seed=seed, **over)
+    # input synapses: k_in distinct inputs per recurrent neuron
+    pre_i, post_i, _ = fixed_indegree_pairs(n_in, n_rec, k_in, seed ^ 0x5151, False)
+    w_i = np.full(pre_i.shape[0], J, dtype=np.float32)
+    pre_r, post_r, m = fixed_indegree_pairs(n_rec, n_rec, k_rec, seed, True)
+    w_r = np.where(pre_r < int(0.8 * n_rec), J, -g * J).astype(np.float32)
+    d_r = (1 + (_u64(seed, _TAG_DELAY, post_r.astype(np.uint64), m.astype(np.uint64))
+                % np.uint64(spec.max_delay))).astype(np.uint8)
+    d_i = np.ones(pre_i.shape[0], dtype=np.uint8)
+    src = np.concatenate([pre_i, pre_r + n_in])
+    post = np.concatenate([post_i, post_r])
+    ptr, col, wv, dv = to_csr(src, post, np.concatenate([w_i, w_r]), np.concatenate([d_i, d_r]),
+                              n_in + n_rec)
+    mask = readout_indegree_mask(seed, n_rec, n_out, k_out)
+    j = np.arange(n_rec)
+    w_out = np.stack([_weights(seed, _TAG_WO1, j, np.full(n_rec, k), 1.0 / math.sqrt(k_out))
+                      for k in range(n_out)], axis=1) * mask
+    fb = sparse_feedback(seed, n_rec, n_out, fb_outdeg)
+    if dale:
+        spec.sign_mask |= 2
+    x_ptr, x_ids = poisson_inputs(seed, n_in, T, rate_hz)
+    return dict(spec=spec, ptr=ptr, col=col, w=wv, delay=dv,
+                w_out=np.ascontiguousarray(w_out, dtype=np.float32), out_mask=mask,
+                feedback=fb, x_ptr=x_ptr, x_ids=x_ids,
+                targets=sinusoid_targets(seed, T, n_out, 1),
+                window=np.ones((1, T), dtype=np.uint8), lengths=np.full(1, T, dtype=np.int32))

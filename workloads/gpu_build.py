@@ -94,3 +94,41 @@ def million_sparse_torch(seed: int = 1237, n_rec: int = 1_000_000, k_in: int = 1
                 targets=C.sinusoid_targets(seed, T, n_out, B),
                 window=np.ones((B, T), dtype=np.uint8),
                 lengths=np.full(B, T, dtype=np.int32))
+
+
+def scaling_torch(seed: int = 1241, n_rec: int = 128_000, k_rec: int = 10_000, n_in: int = 1000,
+                  k_in: int = 100, n_out: int = 10, k_out: int = 1000, fb_outdeg: int = 100,
+                  T: int = 20_000, update_interval: int = 1000, rate_hz: float = 5.0,
+                  J: float = 0.001, g: float = 5.0, device="cuda", **over) -> dict:
+    """The scaling experiment's network (`configs.scaling_network`) with its
+    recurrent synapses built on the GPU: the same integer structure, weights
+    and inputs as the numpy build."""
+    import torch
+    spec = C.scaling_spec(n_rec=n_rec, n_in=n_in, n_out=n_out, T=T, update_interval=update_interval,
+                          rate_hz=rate_hz, seed=seed, **over)
+    pre_i, post_i, _ = C.fixed_indegree_pairs(n_in, n_rec, k_in, seed ^ 0x5151, False)
+    w_i = np.full(pre_i.shape[0], J, dtype=np.float32)
+    ptr_i, col_i, wv_i, dv_i = C.to_csr(pre_i, post_i, w_i, np.ones(pre_i.shape[0], np.uint8), n_in)
+    del pre_i, post_i, w_i
+    ptr_r, col_r, w_r, d_r = ei_network_torch(n_rec, k_rec, spec.max_delay, J, g, seed, device,
+                                              chunk_targets=max(1, 10_000_000 // k_rec))
+    nnz_in = int(ptr_i[-1])
+    ptr = torch.cat([torch.from_numpy(ptr_i).to(device), ptr_r[1:] + nnz_in])
+    col = torch.cat([torch.from_numpy(col_i).to(device), col_r])
+    del col_r
+    w = torch.cat([torch.from_numpy(wv_i).to(device), w_r])
+    del w_r
+    dly = torch.cat([torch.from_numpy(dv_i).to(device), d_r])
+    del d_r
+    mask = C.readout_indegree_mask(seed, n_rec, n_out, k_out)
+    j = np.arange(n_rec)
+    w_out = np.stack([C._weights(seed, C._TAG_WO1, j, np.full(n_rec, k), 1.0 / math.sqrt(k_out))
+                      for k in range(n_out)], axis=1) * mask
+    fb = C.sparse_feedback(seed, n_rec, n_out, fb_outdeg)
+    x_ptr, x_ids = C.poisson_inputs(seed, n_in, T, rate_hz)
+    return dict(spec=spec, ptr=ptr, col=col, w=w, delay=dly,
+                w_out=torch.from_numpy(np.ascontiguousarray(w_out, dtype=np.float32)).to(device),
+                out_mask=torch.from_numpy(mask).to(device),
+                feedback=torch.from_numpy(fb).to(device), x_ptr=x_ptr, x_ids=x_ids,
+                targets=C.sinusoid_targets(seed, T, n_out, 1),
+                window=np.ones((1, T), dtype=np.uint8), lengths=np.full(1, T, dtype=np.int32))
