@@ -241,7 +241,10 @@ def cpu_baseline(args, steps=1):
         t0 = time.perf_counter()
         r = o.simulate(s.T, W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"])
         tot_time += time.perf_counter() - t0
-        tot_events += int((r["raster"][0].sum(axis=0) * outdeg).sum())
+        tot_events += int((r["raster"][0].sum(axis=0) * outdeg[s.n_in:]).sum())
+        if s.n_in:
+            src = np.asarray(W["x_ids"], np.int64)
+            tot_events += int(outdeg[src].sum())
     return {"value": tot_events / tot_time, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": sample, "events": tot_events, "seconds": tot_time}
 

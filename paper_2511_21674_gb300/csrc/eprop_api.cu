@@ -291,6 +291,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     n.rho = n.alif ? (float)std::exp(-(double)c.dt / c.tau_a) : 0.f;
     n.alpha_lo = (float)(alpha - (double)n.alpha);
     n.kappa_e_lo = (float)(kappa_e - (double)n.kappa_e);
+    n.kappa_lo = (float)(kappa - (double)n.kappa);
     n.rho_lo = n.alif ? (float)(std::exp(-(double)c.dt / c.tau_a) - (double)n.rho) : 0.f;
     n.beta_a = n.alif ? c.beta_a : 0.f;
     n.v_th = c.v_th; n.gamma = c.gamma; n.beta_sg = c.beta_sg; n.lr = c.lr;

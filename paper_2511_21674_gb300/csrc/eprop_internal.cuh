@@ -61,6 +61,7 @@ struct Net {
     float alpha, rho, kappa, kappa_e, beta_a, v_th, gamma, beta_sg, lr, drive_weight;
     float alpha_lo, rho_lo;   // alpha - (float)alpha, rho - (float)rho
     float kappa_e_lo;         // kappa_e - (float)kappa_e (the FP64 adjoint sweep uses both)
+    float kappa_lo;           // kappa - (float)kappa (the FP64 error filter uses both)
     float log2_alpha, log2_kappa, alphaU, kappaeU, inv_B;
     unsigned long long drive_seed;
     const uint32_t *drive_thr;

@@ -77,12 +77,16 @@ __global__ void filter_error_kernel(Net n) {
     const int b = idx / n.n_out, k = idx % n.n_out;
     const float *E = n.E_win + (long long)b * n.U * n.n_out + k;
     float *Eb = n.Ebar_win + (long long)b * n.U * n.n_out + k;
-    float acc = 0.0f;
+    // FP64 recursion with the FP64 filter constant (kappa + kappa_lo): over a
+    // long window the FP32 chain of products would carry a relative error of
+    // about (window length) x 2^-24 on errors that arrive late in the window
+    const double kap = (double)n.kappa + (double)n.kappa_lo;
+    double acc = 0.0;
     for (int u = n.U - 1; u >= 0; --u) {
-        acc = E[(long long)u * n.n_out] + n.kappa * acc;
-        Eb[(long long)u * n.n_out] = acc;
+        acc = (double)E[(long long)u * n.n_out] + kap * acc;
+        Eb[(long long)u * n.n_out] = (float)acc;
     }
-    n.Cwin[idx] = n.kappa * acc;
+    n.Cwin[idx] = (float)(kap * acc);
 }
 
 // learning-signal tables: one thread per (sample, neuron), 128 neurons per
@@ -91,7 +95,7 @@ __global__ void filter_error_kernel(Net n) {
 // the whole window beforehand by one strided-batched SGEMM, L_win) are
 // loaded into registers, then the adjoint recursion writes the per-step
 // tables and, at the window start, the window coefficients.
-template <bool ALIF, bool REG>
+template <bool ALIF, bool REG, bool F64>
 __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     constexpr int kTC = ALIF ? 16 : 32;     // window steps per chunk
     const int b = blockIdx.y;
@@ -112,13 +116,16 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     // two long-memory traces, so the sweep runs in FP64 there (FP32 loses up
     // to 1e-1 relative on some elements over a few hundred steps); the LIF
     // sweep has no such cancellation and runs in FP32.
-    using R = typename std::conditional<ALIF, double, float>::type;
+    // Long LIF windows (more than 128 steps) sweep in FP64 as well: the FP32
+    // chain of decays carries a relative error of about (steps) x 2^-24 on
+    // the contributions of early arrivals.
+    using R = typename std::conditional<ALIF || F64, double, float>::type;
     const R alpha = (R)n.alpha + (R)n.alpha_lo;
     const R rho = ALIF ? (R)n.rho + (R)n.rho_lo : (R)0;
     const R beta = n.beta_a;
     // kappa_e^m over a window of hundreds of steps: in the FP64 sweep the
     // filter constant keeps its FP64 value (hi + lo), as alpha and rho do
-    const R ke = ALIF ? (R)n.kappa_e + (R)n.kappa_e_lo : (R)n.kappa_e;
+    const R ke = (ALIF || F64) ? (R)n.kappa_e + (R)n.kappa_e_lo : (R)n.kappa_e;
     // adjoint of G (mz, ma, me); of ebar^b (ez, ea, ee); of eps_a^b (az, aa, ae)
     R mz = 0, ma = 0, me = 0;
     R ez = 0, ea = 0, ee = 1;
@@ -955,27 +962,29 @@ __global__ void __launch_bounds__(256) trace_batched_kernel(Net n) {
             const uint32_t td = n.tgt_d[q];
             const int j = (int)(td & 0xFFFFFFu);
             const int d = (int)(td >> 24);
-            float G = 0.f;
+            // the batch's sum of arrival terms (up to samples x arrivals of
+            // them) is reduced in FP64
+            double G = 0.0;
             if (ns <= CAP) {
                 for (int c = 0; c < ns; ++c) {
                     const int v = sp[warp][c];
                     const int b = v >> 20, a = (v & 0xFFFFF) + d;
-                    if (a <= T) G += n.qp[(((long long)b * U + (a - 1)) * N + j) * QP_STRIDE];
+                    if (a <= T) G += (double)n.qp[(((long long)b * U + (a - 1)) * N + j) * QP_STRIDE];
                 }
             } else {
                 for (int b = 0; b < n.B; ++b) {
                     const uint32_t *words = src_words_c(n, b, src);
                     for_each_spike(words, n.RW, 1, T - d, [&](int st) {
-                        G += n.qp[(((long long)b * U + (st + d - 1)) * N + j) * QP_STRIDE];
+                        G += (double)n.qp[(((long long)b * U + (st + d - 1)) * N + j) * QP_STRIDE];
                     });
                 }
             }
             {
                 const float w0 = n.w[q];
-                const float wn = window_update(n, q, w0, G);
+                const float wn = window_update(n, q, w0, (float)G);
                 if (!n.adam) n.w[q] = wn;
             }
-            if (n.record_grad) n.grad[q] += n.inv_B * G;
+            if (n.record_grad) n.grad[q] += n.inv_B * (float)G;
         }
         __syncwarp();
     }
@@ -1297,12 +1306,15 @@ void launch_filter_error(const Net &n, int i_end, cudaStream_t st) {
 int launch_tables(const Net &n, int i_end, cudaStream_t st) {
     const int bd = 128;
     const dim3 grid((n.n_rec + bd - 1) / bd, n.B);
+    const bool f64 = n.U > 128;          // long LIF windows sweep in FP64 (ALIF always does)
     if (n.R_win) {
-        if (n.alif) tables_kernel<true, true><<<grid, bd, 0, st>>>(n, i_end);
-        else tables_kernel<false, true><<<grid, bd, 0, st>>>(n, i_end);
+        if (n.alif) tables_kernel<true, true, true><<<grid, bd, 0, st>>>(n, i_end);
+        else if (f64) tables_kernel<false, true, true><<<grid, bd, 0, st>>>(n, i_end);
+        else tables_kernel<false, true, false><<<grid, bd, 0, st>>>(n, i_end);
     } else {
-        if (n.alif) tables_kernel<true, false><<<grid, bd, 0, st>>>(n, i_end);
-        else tables_kernel<false, false><<<grid, bd, 0, st>>>(n, i_end);
+        if (n.alif) tables_kernel<true, false, true><<<grid, bd, 0, st>>>(n, i_end);
+        else if (f64) tables_kernel<false, false, true><<<grid, bd, 0, st>>>(n, i_end);
+        else tables_kernel<false, false, false><<<grid, bd, 0, st>>>(n, i_end);
     }
     return 0;
 }
