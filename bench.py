@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--trace-kernel", default="dense", choices=["dense", "lazy"],
                    help="synapse-trace form: dense window pass or lazy catch-up at arrivals")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the batched-form timing (event classification, batch 64)")
     p.add_argument("--cpu-sample-n", type=int, default=10_000)
     p.add_argument("--cpu-sample-T", type=int, default=100)
     return p.parse_args()
@@ -249,6 +251,44 @@ def cpu_baseline(args, steps=1):
             "sample": sample, "events": tot_events, "seconds": tot_time}
 
 
+def batched_form_timing(calls=10, warmup=3):
+    """Form (2) on the event-classification workload (batch 64, lengths
+    250-350, 200 ALIF, 2312 inputs): ms per simulate call with every kernel
+    launched eagerly (launch_mode 0), as a graph of per-step launches (1) and
+    with the step loop in one persistent cooperative kernel (2); CUDA events
+    on the network's stream, inputs resident."""
+    import torch
+    import paper_2511_21674_gb300 as ep
+    from workloads import configs as C
+    W = C.event_classification(batch=64)
+    s = W["spec"]
+    out = {"workload": "event classification: batch 64, lengths 250-350, 2312 inputs, 200 ALIF, "
+                       "10 readouts, CE on each sample's last 25 steps, one window per call"}
+    for mode in (0, 1, 2):
+        net = ep.Network(s, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["out_mask"],
+                         W["feedback"], launch_mode=mode, record_grad=0)
+        net.set_inputs(W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"], s.T)
+        for _ in range(warmup):
+            net.simulate(s.T)
+        net.sync()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(calls):
+            net.simulate(s.T)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / calls
+        stats = net.stats()
+        out[f"ms_per_call_mode{mode}"] = ms
+        out[f"kernel_launches_mode{mode}"] = stats["kernel_launches"]
+        if mode == 2:
+            out["samples_per_s"] = s.batch / (ms / 1000.0)
+            out["events_per_s"] = stats["events"] / (ms / 1000.0)
+        net.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -399,6 +439,11 @@ def _run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if not args.no_forms and args.workload == "million":
+        try:
+            line["form2_batched"] = batched_form_timing()
+        except Exception as exc:  # the main line stands on its own
+            line["form2_batched"] = {"error": str(exc)}
     if not args.no_cpu_baseline:
         try:
             cb = cpu_baseline(args, steps=1)

@@ -139,7 +139,14 @@ typedef struct eprop_config {
     int32_t n_drive_thr;      /* entries used in drive_thr (0: no drive)       */
     int32_t launch_mode;      /* 0: launch every kernel of a simulate call;
                                  1: capture a call once in a CUDA graph and
-                                 replay it for later calls with the same T   */
+                                 replay it for later calls with the same T;
+                                 2: as 1, with every step of the call in one
+                                 persistent cooperative kernel (grid barriers
+                                 between the neuron and the delivery phases,
+                                 bounded waits: EPROP_ETIMEOUT); needs one
+                                 update window per call (continuous = 0,
+                                 update_interval = 0), n_out <= 256 and no
+                                 predictor; results are bit-identical to 0/1 */
     int32_t trace_kernel;     /* synapse-trace kernel: 0 auto (2 for batch >
                                  1, else 3 when state is carried, else 1);
                                  1 lazy window work queue (batch 1): only

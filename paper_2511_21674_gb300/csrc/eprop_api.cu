@@ -55,6 +55,9 @@ struct eprop_net {
     long long tmp_raster_bytes = 0;
     eprop_predictor *pred = nullptr;    // attached learned learning-signal predictor
     int *pop_cnt_buf = nullptr;
+    eprop::GridBar *gridbar = nullptr;  // persistent step loop (launch_mode 2)
+    int pers_blocks = 0;
+    cudaError_t launch_err = cudaSuccess;
 };
 
 static thread_local std::string g_create_err;
@@ -222,6 +225,11 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         return fail(nullptr, EPROP_EINVAL, "invalid enum or negative parameter");
     if (c.batch > 1 && (c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL, "batch > 1 needs continuous = 0 and update_interval = 0");
+    if (c.launch_mode < 0 || c.launch_mode > 2)
+        return fail(nullptr, EPROP_EINVAL, "launch_mode must be 0, 1 or 2");
+    if (c.launch_mode == 2 && (c.continuous || c.update_interval > 0 || c.n_out > 256))
+        return fail(nullptr, EPROP_EINVAL,
+                    "launch_mode 2 (persistent step loop) needs one update window per call and n_out <= 256");
     if (c.trace_kernel < 0 || c.trace_kernel > 3 || c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
         return fail(nullptr, EPROP_EINVAL, "trace_kernel must be 0..3 and blocks_per_sm 0..64");
     if ((c.trace_kernel == 1 || c.trace_kernel == 3) && c.batch > 1)
@@ -419,6 +427,12 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             FA(gwin_out, float, N * K);
             FA(adam_m_out, float, N * K);
             FA(adam_v_out, float, N * K);
+        }
+        if (c.launch_mode == 2) {
+            if (dalloc(o, &p, sizeof(eprop::GridBar)) != cudaSuccess) { s = fail(nullptr, EPROP_ENOMEM, "allocation"); goto fail_out; }
+            net->gridbar = static_cast<eprop::GridBar *>(p);
+            net->pers_blocks = eprop::persistent_blocks(net->sm_count);
+            if (net->pers_blocks < 1) { s = fail(nullptr, EPROP_ECUDA, "persistent step loop cannot be resident"); goto fail_out; }
         }
         FA(events, unsigned long long, 1);
         FA(err_flags, unsigned int, 1);
@@ -641,7 +655,17 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         cudaEventRecord(net->ev_join, net->st2);
         cudaStreamWaitEvent(st, net->ev_join, 0);
     };
+    const bool persistent = c.launch_mode == 2;
+    if (persistent) {
+        // form (2): every step of the call in one cooperative launch
+        cudaError_t le = eprop::launch_persistent_steps(n, T, net->gridbar, net->pers_blocks, st);
+        if (le != cudaSuccess && net->launch_err == cudaSuccess) net->launch_err = le;
+        L += 1;
+    }
     for (int i = 1; i <= T; ++i) {
+        if (persistent) {
+            if (i % U != 0) continue;
+        } else {
         if (c.n_in > 0) { eprop::launch_inject(n, i, (int)net->max_in_per_step, st); L += 1; }
         eprop::launch_neuron(n, i, net->sm_count, st);
         fork_readout();
@@ -657,6 +681,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         }
         eprop::launch_deliver(n, i, deliver_rows, st);
         L += 3;
+        }
         if (i % U == 0) {
             join_readout();
             eprop::launch_filter_error(n, i, st);
@@ -713,7 +738,8 @@ extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t 
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(net, e, "pending error before simulate");
-    const bool use_graph = c.launch_mode == 1 && forced_raster == nullptr;
+    const bool use_graph = c.launch_mode >= 1 && forced_raster == nullptr;
+    net->launch_err = cudaSuccess;
     if (use_graph) {
         if (!net->gexec || net->g_T != T) {
             if (net->gexec) {
@@ -724,6 +750,10 @@ extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t 
             CK(net, cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal));
             issue_call(net, T, nullptr);
             CK(net, cudaStreamEndCapture(net->st, &g));
+            if (net->launch_err != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_fail(net, net->launch_err, "persistent step loop capture");
+            }
             e = cudaGraphInstantiate(&net->gexec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(net, e, "cudaGraphInstantiate");
@@ -735,6 +765,7 @@ extern "C" eprop_status eprop_simulate(eprop_net *net, int32_t T, const uint8_t 
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(net, e, "kernel launch");
+    if (net->launch_err != cudaSuccess) return cuda_fail(net, net->launch_err, "persistent step loop launch");
     net->t_abs += T;
     net->r_base = c.continuous ? net->r_base + T : T;
     net->have_sim = 1;
@@ -973,6 +1004,8 @@ extern "C" eprop_status eprop_attach_predictor(eprop_net *net, eprop_predictor *
     const eprop_config &c = net->cfg;
     if (mode < 0 || mode > 3) return fail(net, EPROP_EINVAL, "mode must be 0..3");
     if (mode != 0 && !pred) return fail(net, EPROP_EINVAL, "a predictor is required");
+    if (mode != 0 && c.launch_mode == 2)
+        return fail(net, EPROP_EINVAL, "the persistent step loop (launch_mode 2) runs without a predictor");
     CK(net, cudaStreamSynchronize(net->st));
     if (net->gexec) {                       // the captured call changes
         cudaGraphExecDestroy(net->gexec);
@@ -1168,9 +1201,10 @@ extern "C" eprop_status eprop_sync(eprop_net *net) {
     CK(net, cudaGetLastError());
     unsigned int f = 0;
     CK(net, cudaMemcpy(&f, net->n.err_flags, 4, cudaMemcpyDeviceToHost));
-    if (f & 2u) {
+    if (f & 6u) {
         net->bad = 1;
-        net->err = "a bounded wait for a bulk copy into shared memory gave up";
+        net->err = (f & 4u) ? "a bounded grid-barrier wait of the persistent step loop gave up"
+                            : "a bounded wait for a bulk copy or the tensor cores gave up";
         return EPROP_ETIMEOUT;
     }
     if (f & 1u) net->err = "warning: a synapse skipped more update windows than the coefficient ring holds";

@@ -47,6 +47,10 @@ struct Clock {            // device-resident time base (graph-safe)
     int adam_k;           // Adam steps taken
 };
 
+struct GridBar {           // grid barrier of the persistent step loop
+    unsigned count, gen, abort;
+};
+
 struct Net {
     // sizes
     int n_in, n_rec, n_out, n_src, B, D, U, RW, RS, RC;

@@ -5,6 +5,7 @@
 namespace eprop {
 
 struct Net;
+struct GridBar;
 
 void launch_inject(const Net &n, int i, int max_events_per_step, cudaStream_t st);
 void launch_neuron(const Net &n, int i, int sm_count, cudaStream_t st);
@@ -29,6 +30,8 @@ void launch_flush(const Net &n, int i_end, float *w_dst, float *g_dst, long long
 void launch_fill_int(int *p, long long count, int value, cudaStream_t st);
 void launch_unpack_raster(const Net &n, unsigned char *dst, cudaStream_t st);
 void launch_adam(const Net &n, int sm_count, cudaStream_t st);
+int persistent_blocks(int sm_count);
+cudaError_t launch_persistent_steps(const Net &n, int T, GridBar *gb, int blocks, cudaStream_t st);
 void prepare_learning_signal_attributes();
 void launch_learning_signals(const float *fb, const float *E, float *L, int N, int U, int K, int B,
                              unsigned *err, cudaStream_t st);

@@ -43,6 +43,106 @@ __global__ void inject_kernel(Net n, int i) {
         mark_spike(n, b, n.x_ids[q], r);
 }
 
+// One neuron's update at call step i from its loaded state (Eq. lif_update,
+// Eq. binary-spike-state-variable, Eq. spike-threshold-adaptation, the
+// surrogate): clears its ring slot, writes v, a, ref, z_prev, psi and the
+// rate regularisation signal, and marks a spike.  Shared by the per-step
+// neuron kernel and the persistent step loop.
+__device__ __forceinline__ void neuron_update(const Net &n, int i, int b, int j, long long nb, int r, int a0,
+                                              long long t_abs, const uint32_t *thr_s, float *psi_row,
+                                              long long *ring_row, long long acc_q, float v_hi_q, float v_lo_q,
+                                              float a_hi_q, float a_lo_q, int ref_q, uint8_t zp8_q) {
+    ring_row[j] = 0;
+    // exact fixed-point input split into an FP32 pair
+    const float acc_hi = (float)acc_q;
+    float u_hi = acc_hi * kFixInv;
+    float u_lo = (float)(acc_q - (long long)acc_hi) * kFixInv;
+    if (n.n_thr > 0) {
+        const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
+        const uint32_t u = (uint32_t)(h >> 32);
+        // thresholds are non-decreasing (checked at creation): the count of
+        // thresholds <= u is the index of the first one above u
+        int cnt = 0;
+        while (cnt < n.n_thr && u >= thr_s[cnt]) ++cnt;
+        const float dv = n.drive_weight * (float)cnt;
+        const float de = fmaf(n.drive_weight, (float)cnt, -dv);
+        float e;
+        two_sum(u_hi, dv, u_hi, e);
+        u_lo += e + de;
+    }
+    const float zp = (float)zp8_q;
+    float vth = n.v_th, vth_lo = 0.0f;
+    if (n.alif) {
+        comp_step(n.rho, n.rho_lo, zp, 0.0f, a_hi_q, a_lo_q);
+        n.a[nb] = a_hi_q;
+        n.a_lo[nb] = a_lo_q;
+        vth = fmaf(n.beta_a, a_hi_q, n.v_th);
+        vth_lo = fmaf(n.beta_a, a_hi_q, n.v_th - vth) + n.beta_a * a_lo_q;
+    }
+    if (n.reset_mode == 1 && zp != 0.0f) {
+        // fixed reset: v' = v_reset + I (the decayed membrane is replaced)
+        float s, e;
+        two_sum(n.v_reset, u_hi, s, e);
+        const float lo = e + u_lo;
+        const float hi = s + lo;
+        v_lo_q = lo - (hi - s);
+        v_hi_q = hi;
+    } else {
+        // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
+        if (n.reset_mode == 0) {
+            float e;
+            two_sum(u_hi, -zp * vth, u_hi, e);
+            u_lo += e - zp * vth_lo;
+        }
+        comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi_q, v_lo_q);
+    }
+    n.v[nb] = v_hi_q;
+    n.v_lo[nb] = v_lo_q;
+    const float m = (v_hi_q - vth) + (v_lo_q - vth_lo);
+    const bool refractory = ref_q > 0;
+    int z;
+    if (n.forced) {
+        z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
+    } else if (n.if_period > 0) {
+        // ignore-and-fire: a fixed schedule with the neuron's own phase
+        const uint32_t ph = (uint32_t)(mix64(n.if_seed ^ (uint64_t)j) >> 32) % (uint32_t)n.if_period;
+        z = ((t_abs + (long long)ph) % n.if_period) == 0 ? 1 : 0;
+    } else {
+        z = (!refractory && m > 0.0f) ? 1 : 0;
+    }
+    float psi;
+    if (n.surrogate == 1) {      // Eq. exponential-surrogate-gradient
+        psi = refractory ? 0.0f : n.gamma * expf(-n.beta_sg * fabsf(m));
+    } else {                     // Eq. piecewise-linear-surrogate-gradient
+        const float hh = 1.0f - n.beta_sg * fabsf(m);
+        psi = refractory ? 0.0f : n.gamma * fmaxf(hh, 0.0f);
+    }
+    psi_row[j] = psi;
+    if (n.R_win) {
+        // moving-average rate (Eq. ema-rate) and the regularisation
+        // signal of Eq. ema-gradient, with G_beta's factor (1 - beta)
+        const float f = n.beta_reg * n.rate[nb] + (1.0f - n.beta_reg) * (float)z;
+        n.rate[nb] = f;
+        n.R_win[((long long)b * n.U + (r - a0 - 1)) * n.n_rec + j] =
+            n.c_reg * (1.0f - n.beta_reg) * (f - n.f_target);
+    }
+    if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = psi;
+    int rf = ref_q;
+    if (refractory) rf -= 1;
+    if (z) rf = n.t_ref;
+    n.ref[nb] = rf;
+    n.z_prev[nb] = (uint8_t)z;
+    if (z) {
+        mark_spike(n, b, n.n_in + j, r);
+        if (n.pop_cnt) atomicAdd(&n.pop_cnt[b * kPopGroups + (j & (kPopGroups - 1))], 1);
+        if (n.record_raster) {
+            const int W32 = (n.T + 31) / 32;
+            atomicOr(&n.rec_raster[((long long)b * W32 + ((i - 1) >> 5)) * n.n_rec + j],
+                     1u << ((i - 1) & 31));
+        }
+    }
+}
+
 // K1: LIF / ALIF neuron update (Eq. lif_update, Eq. binary-spike-state-
 // variable, Eq. spike-threshold-adaptation, Eq. piecewise-linear-surrogate-
 // gradient).  Each thread updates kNPT neurons of one sample (strided by the
@@ -112,95 +212,8 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
         const int j = jb + q * kNeuronThreads;
         if (j >= n.n_rec) break;
         const long long nb = nb0 + j;
-        ring_row[j] = 0;
-        // exact fixed-point input split into an FP32 pair
-        const float acc_hi = (float)acc[q];
-        float u_hi = acc_hi * kFixInv;
-        float u_lo = (float)(acc[q] - (long long)acc_hi) * kFixInv;
-        if (n.n_thr > 0) {
-            const uint64_t h = mix64(mix64(mix64(n.drive_seed ^ (uint64_t)j) ^ (uint64_t)t_abs) ^ (uint64_t)b);
-            const uint32_t u = (uint32_t)(h >> 32);
-            // thresholds are non-decreasing (checked at creation): the count of
-            // thresholds <= u is the index of the first one above u
-            int cnt = 0;
-            while (cnt < n.n_thr && u >= thr_s[cnt]) ++cnt;
-            const float dv = n.drive_weight * (float)cnt;
-            const float de = fmaf(n.drive_weight, (float)cnt, -dv);
-            float e;
-            two_sum(u_hi, dv, u_hi, e);
-            u_lo += e + de;
-        }
-        const float zp = (float)zp8[q];
-        float vth = n.v_th, vth_lo = 0.0f;
-        if (n.alif) {
-            comp_step(n.rho, n.rho_lo, zp, 0.0f, a_hi[q], a_lo[q]);
-            n.a[nb] = a_hi[q];
-            n.a_lo[nb] = a_lo[q];
-            vth = fmaf(n.beta_a, a_hi[q], n.v_th);
-            vth_lo = fmaf(n.beta_a, a_hi[q], n.v_th - vth) + n.beta_a * a_lo[q];
-        }
-        if (n.reset_mode == 1 && zp != 0.0f) {
-            // fixed reset: v' = v_reset + I (the decayed membrane is replaced)
-            float s, e;
-            two_sum(n.v_reset, u_hi, s, e);
-            const float lo = e + u_lo;
-            const float hi = s + lo;
-            v_lo[q] = lo - (hi - s);
-            v_hi[q] = hi;
-        } else {
-            // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
-            if (n.reset_mode == 0) {
-                float e;
-                two_sum(u_hi, -zp * vth, u_hi, e);
-                u_lo += e - zp * vth_lo;
-            }
-            comp_step(n.alpha, n.alpha_lo, u_hi, u_lo, v_hi[q], v_lo[q]);
-        }
-        n.v[nb] = v_hi[q];
-        n.v_lo[nb] = v_lo[q];
-        const float m = (v_hi[q] - vth) + (v_lo[q] - vth_lo);
-        const bool refractory = ref[q] > 0;
-        int z;
-        if (n.forced) {
-            z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
-        } else if (n.if_period > 0) {
-            // ignore-and-fire: a fixed schedule with the neuron's own phase
-            const uint32_t ph = (uint32_t)(mix64(n.if_seed ^ (uint64_t)j) >> 32) % (uint32_t)n.if_period;
-            z = ((t_abs + (long long)ph) % n.if_period) == 0 ? 1 : 0;
-        } else {
-            z = (!refractory && m > 0.0f) ? 1 : 0;
-        }
-        float psi;
-        if (n.surrogate == 1) {      // Eq. exponential-surrogate-gradient
-            psi = refractory ? 0.0f : n.gamma * expf(-n.beta_sg * fabsf(m));
-        } else {                     // Eq. piecewise-linear-surrogate-gradient
-            const float hh = 1.0f - n.beta_sg * fabsf(m);
-            psi = refractory ? 0.0f : n.gamma * fmaxf(hh, 0.0f);
-        }
-        psi_row[j] = psi;
-        if (n.R_win) {
-            // moving-average rate (Eq. ema-rate) and the regularisation
-            // signal of Eq. ema-gradient, with G_beta's factor (1 - beta)
-            const float f = n.beta_reg * n.rate[nb] + (1.0f - n.beta_reg) * (float)z;
-            n.rate[nb] = f;
-            n.R_win[((long long)b * n.U + (r - a0 - 1)) * n.n_rec + j] =
-                n.c_reg * (1.0f - n.beta_reg) * (f - n.f_target);
-        }
-        if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = psi;
-        int rf = ref[q];
-        if (refractory) rf -= 1;
-        if (z) rf = n.t_ref;
-        n.ref[nb] = rf;
-        n.z_prev[nb] = (uint8_t)z;
-        if (z) {
-            mark_spike(n, b, n.n_in + j, r);
-            if (n.pop_cnt) atomicAdd(&n.pop_cnt[b * kPopGroups + (j & (kPopGroups - 1))], 1);
-            if (n.record_raster) {
-                const int W32 = (n.T + 31) / 32;
-                atomicOr(&n.rec_raster[((long long)b * W32 + ((i - 1) >> 5)) * n.n_rec + j],
-                         1u << ((i - 1) & 31));
-            }
-        }
+        neuron_update(n, i, b, j, nb, r, a0, t_abs, thr_s, psi_row, ring_row, acc[q], v_hi[q], v_lo[q],
+                      a_hi[q], a_lo[q], ref[q], zp8[q]);
     }
     }
 }
@@ -608,6 +621,134 @@ __global__ void __launch_bounds__(256, STATE ? 2 : 4) deliver_kernel(Net n, int 
     if (threadIdx.x == 0 && ev_block) atomicAdd(n.events, ev_block);
 }
 
+// ---------------------------------------------------- persistent step loop
+//
+// Form (2): all T steps of a single-window call in one cooperative launch
+// (captured in the call's CUDA graph like any kernel).  Per step two phases
+// separated by grid barriers:
+//   A  readout finish of step i - 1 (one block per sample), input injection
+//      and every neuron update of step i;
+//   B  readout accumulation and spike delivery of step i (warps dealt to
+//      samples, each warp walking its share of the sample's spike list).
+// The arithmetic is that of the per-step kernels (the neuron update is the
+// same device function, readout and ring sums are the same exact int64
+// fixed-point additions), so the results are bit-identical to them.  The
+// barrier waits are bounded: a wait that gives up sets error bit 2 and an
+// abort flag that every block checks, so all blocks leave the loop.
+
+constexpr int kPersThreads = 256;
+constexpr unsigned kBarrierLimit = 1u << 22;
+
+__device__ bool grid_barrier(GridBar *gb, unsigned nblocks, unsigned *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        volatile unsigned *vgen = &gb->gen;
+        volatile unsigned *vab = &gb->abort;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*vgen == g) {
+                if (*vab || ++it > kBarrierLimit) {
+                    atomicOr(err, 4u);
+                    atomicExch(&gb->abort, 1u);
+                    s_ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kPersThreads) persistent_steps_kernel(Net n, int T, GridBar *gb) {
+    __shared__ uint32_t thr_s[EPROP_MAX_DRIVE_THR];
+    for (int m = threadIdx.x; m < n.n_thr; m += blockDim.x) thr_s[m] = n.drive_thr[m];
+    const Clock ck = *n.clock;                   // constant during a call
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)(tid >> 5), nwarps = (int)(nth >> 5);
+    const int ws = max(1, nwarps / n.B);         // warps per sample in phase B
+    const int D1 = n.D + 1;
+    __syncthreads();
+    for (int i = 1; i <= T; ++i) {
+        const int r = ck.r_base + i;
+        const int a0 = ((r - 1) / n.U) * n.U;
+        const long long t_abs = ck.t_abs_base + i;
+        const int slot = (ck.ring0 + i) % D1;
+        // ---- phase A
+        if (i > 1)
+            for (int b = blockIdx.x; b < n.B; b += gridDim.x) readout_finish(n, i - 1, b);
+        if (n.n_in > 0)
+            for (int b = 0; b < n.B; ++b) {
+                if (i > n.lengths[b]) continue;
+                const long long q0 = n.x_ptr[(long long)b * n.T + i - 1];
+                const long long q1 = n.x_ptr[(long long)b * n.T + i];
+                for (long long q = q0 + tid; q < q1; q += nth) mark_spike(n, b, n.x_ids[q], r);
+            }
+        for (long long idx = tid; idx < (long long)n.B * n.n_rec; idx += nth) {
+            const int b = (int)(idx / n.n_rec), j = (int)(idx - (long long)b * n.n_rec);
+            float *psi_row = n.psi_hist + ((long long)b * (n.U + 1) + (r - a0)) * n.n_rec;
+            long long *ring_row = n.ring + ((long long)b * D1 + slot) * n.n_rec;
+            if (i > n.lengths[b]) {              // sample already finished: frozen, silent
+                psi_row[j] = 0.0f;
+                if (n.R_win) n.R_win[((long long)b * n.U + (r - a0 - 1)) * n.n_rec + j] = 0.0f;
+                if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
+                continue;
+            }
+            neuron_update(n, i, b, j, idx, r, a0, t_abs, thr_s, psi_row, ring_row, ring_row[j], n.v[idx],
+                          n.v_lo[idx], n.alif ? n.a[idx] : 0.f, n.alif ? n.a_lo[idx] : 0.f, n.ref[idx],
+                          n.z_prev[idx]);
+        }
+        if (!grid_barrier(gb, gridDim.x, n.err_flags)) return;
+        // ---- phase B
+        for (int vw = gwarp; vw < n.B * ws; vw += nwarps) {
+            const int b = vw / ws, sub = vw - b * ws;
+            const long long li = list_index(n, b, r % n.RS);
+            if (sub == 0 && lane < kBkt)         // next step's list slot (its readers are done)
+                n.list_cnt[list_index(n, b, (r + 1) % n.RS) + lane] = 0;
+            if (i > n.lengths[b]) continue;
+            const int *ids = n.list_ids + li * n.list_cap;
+            const BucketScan bs = bucket_scan(n.list_cnt + li);
+            long long *ring_b = n.ring + (long long)b * D1 * n.n_rec;
+            unsigned long long ev = 0;
+            for (int e = sub; e < bs.total; e += ws) {
+                const int src = bucket_entry(n, ids, bs, e);
+                const long long rb = n.row_ptr[src], re = n.row_ptr[src + 1];
+                ev += (unsigned long long)(re - rb);
+                if (src >= n.n_in)               // readout input sum_j W_out[j][k] z_j (exact)
+                    for (int k = lane; k < n.n_out; k += 32) {
+                        const long long fx =
+                            __float2ll_rn(n.w_out[(long long)(src - n.n_in) * n.n_out + k] * 4294967296.0f);
+                        if (fx) atomicAdd(reinterpret_cast<unsigned long long *>(&n.y_acc[(long long)b * n.n_out + k]),
+                                          (unsigned long long)fx);
+                    }
+                for (long long q = rb + lane; q < re; q += 32) {
+                    const uint32_t td = n.tgt_d[q];
+                    const int j = (int)(td & 0xFFFFFFu), dl = (int)(td >> 24);
+                    const long long fx = __float2ll_rn(n.w[q] * 4294967296.0f);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(
+                                  &ring_b[(long long)((ck.ring0 + i + dl) % D1) * n.n_rec + j]),
+                              (unsigned long long)fx);
+                }
+            }
+            if (lane == 0 && ev) atomicAdd(n.events, ev);
+        }
+        if (!grid_barrier(gb, gridDim.x, n.err_flags)) return;
+    }
+    for (int b = blockIdx.x; b < n.B; b += gridDim.x) readout_finish(n, T, b);
+}
+
 // ----------------------------------------------------------------- launches
 
 void launch_inject(const Net &n, int i, int max_events_per_step, cudaStream_t st) {
@@ -652,6 +793,26 @@ void launch_deliver(const Net &n, int i, int grid_x, cudaStream_t st) {
         const size_t sm = deliver_stage_bytes(false) * 8 * kDStages;
         deliver_kernel<false, false><<<grid, 256, sm, st>>>(n, i);
     }
+}
+
+int persistent_blocks(int sm_count) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_steps_kernel, kPersThreads, 0);
+    return occ >= 1 ? sm_count : 0;          // one block per SM (all co-resident)
+}
+
+cudaError_t launch_persistent_steps(const Net &n, int T, GridBar *gb, int blocks, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kPersThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, persistent_steps_kernel, n, T, gb);
 }
 
 void prepare_step_kernel_attributes() {
