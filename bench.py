@@ -45,14 +45,18 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="million", choices=["million", "scaling"],
+    p.add_argument("--workload", default="million", choices=["million", "scaling", "batched"],
                    help="million: 1e6 LIF, in-degree 1000; scaling: the paper's scaling network "
-                        "(128k ignore-and-fire neurons, in-degree 10,000, 20 s)")
+                        "(128k ignore-and-fire neurons, in-degree 10,000, 20 s); batched: event "
+                        "classification, 64 samples of uneven length per call")
+    p.add_argument("--launch-mode", type=int, default=None,
+                   help="0 eager launches, 1 graph of launches, 2 persistent step loop "
+                        "(default: 1, and 2 for the batched workload)")
     p.add_argument("--n-rec", type=int, default=1_000_000)
     p.add_argument("--k-in", type=int, default=1000)
     p.add_argument("--T", type=int, default=1000)
     p.add_argument("--n-out", type=int, default=100)
-    p.add_argument("--trace-dtype", default="bf16", choices=["bf16", "fp32"])
+    p.add_argument("--trace-dtype", default="bf16", choices=["bf16", "fp16", "fp32"])
     p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--trace-kernel", default="dense", choices=["dense", "lazy"],
                    help="synapse-trace form: dense window pass or lazy catch-up at arrivals")
@@ -60,7 +64,7 @@ def parse():
     p.add_argument("--no-forms", action="store_true",
                    help="skip the batched-form timing (event classification, batch 64)")
     p.add_argument("--cpu-sample-n", type=int, default=10_000)
-    p.add_argument("--cpu-sample-T", type=int, default=100)
+    p.add_argument("--cpu-sample-T", type=int, default=300)
     return p.parse_args()
 
 
@@ -188,6 +192,13 @@ def barrier(world):
 
 def workload_config(args, nnz, world=1):
     """The workload one step runs (both arms report it)."""
+    if args.workload == "batched":
+        return {"workload": "event classification (N-MNIST-shaped, synthetic): batch 64, lengths 250-350, "
+                            "2312 inputs, 200 ALIF (10% recurrent), 10 readouts, CE on each sample's last "
+                            f"25 steps, one update window per call ({nnz} synapses)",
+                "batch": 64, "T_per_step": 350, "synapses": nnz, "launch_mode": launch_mode(args),
+                "trace_storage": "fp32", "parallelism": f"replicas{world}",
+                "l2": "small working set (L2-resident): a latency-bound workload"}
     if args.workload == "scaling":
         return {"workload": f"scaling: {SCALING['n_rec']} ignore-and-fire neurons at 5 Hz, recurrent "
                             f"in-degree {SCALING['k_rec']}, {SCALING['n_in']} Poisson inputs at 5 Hz "
@@ -215,6 +226,25 @@ SCALING_SAMPLE = dict(n_rec=2000, k_rec=1000, n_in=100, k_in=10, n_out=10, k_out
                       T=100, update_interval=100)
 
 
+def launch_mode(args):
+    if args.launch_mode is not None:
+        return args.launch_mode
+    return 2 if args.workload == "batched" else 1
+
+
+def cpu_model():
+    """The host CPU's model string (lscpu / /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for key in ("Model name", "Vendor ID"):
+            for line in out.splitlines():
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(args, steps=1):
     """The FP64 oracle (test infrastructure, untuned) on a bounded sample of
     the same workload: cpu_sample_n neurons with the same in-degree, delays,
@@ -222,19 +252,25 @@ def cpu_baseline(args, steps=1):
     import oracle
     from workloads import configs as C
     oracle.build()
-    if args.workload == "scaling":
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    if args.workload == "batched":
+        W = C.event_classification(batch=4)
+        sample = (f"event classification, 4 samples of 250-350 steps x {steps}, FP64 time-driven "
+                  f"oracle, {threads} threads")
+    elif args.workload == "scaling":
         W = C.scaling_network(**SCALING_SAMPLE)
         sample = ("scaling network sample: 2000 ignore-and-fire neurons, recurrent in-degree 1000, "
                   "100 Poisson inputs (in-degree 10), 10 readouts (in-degree 100), feedback out-degree 20, "
-                  f"100 steps x {steps}, FP64 time-driven oracle, single thread")
+                  f"100 steps x {steps}, FP64 time-driven oracle, {threads} threads")
     else:
         W = C.million_sparse(n_rec=args.cpu_sample_n, k_in=args.k_in, T=args.cpu_sample_T,
                              n_out=args.n_out)
         sample = (f"{args.cpu_sample_n} LIF neurons, in-degree {args.k_in}, delays 1-5, "
                   f"~5 Hz, {args.n_out} readouts, {args.cpu_sample_T} steps x {steps}, "
-                  f"FP64 time-driven oracle, single thread")
+                  f"FP64 time-driven oracle, {threads} threads")
     s = W["spec"]
-    s.update_interval = s.T
+    if args.workload != "batched":
+        s.update_interval = s.T
     o = oracle.Oracle(s, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["out_mask"],
                       W["feedback"])
     outdeg = np.diff(W["ptr"])
@@ -243,12 +279,12 @@ def cpu_baseline(args, steps=1):
         t0 = time.perf_counter()
         r = o.simulate(s.T, W["x_ptr"], W["x_ids"], W["targets"], W["window"], W["lengths"])
         tot_time += time.perf_counter() - t0
-        tot_events += int((r["raster"][0].sum(axis=0) * outdeg[s.n_in:]).sum())
+        tot_events += int((r["raster"].sum(axis=(0, 1)) * outdeg[s.n_in:]).sum())
         if s.n_in:
             src = np.asarray(W["x_ids"], np.int64)
             tot_events += int(outdeg[src].sum())
-    return {"value": tot_events / tot_time, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample, "events": tot_events, "seconds": tot_time}
+    return {"value": tot_events / tot_time, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": sample, "events": tot_events, "seconds": tot_time, "cpu_model": cpu_model()}
 
 
 def batched_form_timing(calls=10, warmup=3):
@@ -303,7 +339,8 @@ def run_reference(args):
             "ms_per_step": 1000.0 * sec_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, args.n_rec * args.k_in, args.gpus),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"],
+            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "sample": res["sample"],
+                             "cpu_model": res["cpu_model"],
                              "value": res["value"], "unit": UNIT},
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -325,19 +362,25 @@ def run_ours(args):
 def _run_ours(args, rank, world, local):
     import torch
     import paper_2511_21674_gb300 as ep
+    from workloads import configs as C
     from workloads import gpu_build as G
     torch.manual_seed(0)
-    if args.workload == "scaling":
+    if args.workload == "batched":
+        W = C.event_classification(batch=64, seed=1235 + rank)
+    elif args.workload == "scaling":
         W = G.scaling_torch(seed=replica_seed(rank) + 4, **SCALING)
     else:
         W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
                                    seed=replica_seed(rank))
     spec = W["spec"]
-    trace_dtype = 1 if args.trace_dtype == "bf16" else 0
+    trace_dtype = {"fp32": 0, "bf16": 1, "fp16": 2}[args.trace_dtype]
+    if args.workload == "batched":
+        trace_dtype = 0                  # single-window form: no traces are stored
     net = ep.Network(spec, W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["out_mask"], W["feedback"],
-                     launch_mode=1, trace_dtype=trace_dtype, record_grad=0, record_raster=0,
+                     launch_mode=launch_mode(args), trace_dtype=trace_dtype, record_grad=0, record_raster=0,
                      profile=1, blocks_per_sm=args.blocks_per_sm,
-                     trace_kernel=3 if args.trace_kernel == "dense" else 1)
+                     trace_kernel=(0 if args.workload == "batched" else
+                                   3 if args.trace_kernel == "dense" else 1))
     nnz = int(W["col"].shape[0])
     del W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["feedback"], W["out_mask"]
     torch.cuda.empty_cache()
@@ -402,7 +445,7 @@ def _run_ours(args, rank, world, local):
     del y_host
 
     # ---- roofline of the synapse-trace kernel
-    bytes_per_event = 16.0 if trace_dtype == 1 else 20.0     # j|d 4 r, w 4 r/w, trace 2|4 r/w
+    bytes_per_event = 16.0 if trace_dtype else 20.0          # j|d 4 r, w 4 r/w, trace 2|4 r/w
     peak, peak_src = measured_peaks()
     achieved = events * bytes_per_event / (trace_ms / 1000.0) / 1e9 if trace_ms > 0 else None
     # per window pass (the unit `achieved` averages over): DRAM bytes from
@@ -434,11 +477,17 @@ def _run_ours(args, rank, world, local):
                      "traffic_unit": "DRAM bytes per window pass (both launches)",
                      "peak_source": f"{peak_src} (hbm_gbs)",
                      "trace_ms_per_step": trace_ms / K, "trace_launches_per_step": trace_launches / K},
+        "samples_per_s": spec.batch * K / (ms_max / 1000.0),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(loss_host.nbytes)},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if args.workload == "batched":
+        # a latency-bound workload (a few MB, L2-resident): no HBM roofline
+        line["roofline"] = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                            "traffic": None, "note": "64 samples x 200 neurons: launch and barrier latency "
+                                                     "bound; the HBM fraction is not meaningful"}
     if not args.no_forms and args.workload == "million":
         try:
             line["form2_batched"] = batched_form_timing()
@@ -447,7 +496,7 @@ def _run_ours(args, rank, world, local):
     if not args.no_cpu_baseline:
         try:
             cb = cpu_baseline(args, steps=1)
-            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model")}
         except Exception as exc:  # the GPU line stands on its own
             line["cpu_baseline"] = {"error": str(exc)}
     print(json.dumps(line), flush=True)

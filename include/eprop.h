@@ -132,7 +132,9 @@ typedef struct eprop_config {
     int32_t update_interval;  /* U in steps; 0 = one window per call          */
     int32_t continuous;       /* 1: keep all state between simulate calls     */
     int32_t max_delay;        /* D, 1..8                                      */
-    int32_t trace_dtype;      /* storage of per-synapse traces: 0 FP32, 1 BF16 */
+    int32_t trace_dtype;      /* storage of per-synapse traces: 0 FP32, 1 BF16,
+                                 2 FP16 (16-bit forms rounded to nearest even,
+                                 arithmetic in FP32)                          */
     int32_t record_grad;      /* 1: keep per-synapse gradient sums             */
     int32_t record_raster;    /* 1: keep the spike raster of the last call     */
     int32_t record_psi;       /* 1: keep the surrogate values of the last call */

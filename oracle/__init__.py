@@ -45,12 +45,14 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle (plain -O2, no fast-math) and return the path."""
+    """Compile the C oracle (plain -O2, no fast-math, OpenMP over the
+    per-synapse loop) and return the path.  The thread count follows
+    OMP_NUM_THREADS (the tests run it with one thread unless set)."""
     src = os.path.join(_HERE, "eprop_oracle.c")
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                                "-fno-fast-math", "-ffp-contract=off", src,
                                "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
@@ -99,6 +101,8 @@ def _load():
             lib.oracle_simulate.restype = ctypes.c_int
             lib.oracle_simulate.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_State),
                                             ctypes.c_int32] + [ctypes.c_void_p] * 15
+            lib.oracle_set_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
             lib.oracle_eligibility_step.restype = ctypes.c_double
             lib.oracle_eligibility_step.argtypes = [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3
             lib.oracle_synapse_sample.restype = None
@@ -109,6 +113,37 @@ def _load():
                                                                            ctypes.c_int64] + [ctypes.c_void_p] * 3
             _lib = lib
     return _lib
+
+
+def _f32(x) -> float:
+    return float(np.float32(x))
+
+
+def params(spec) -> dict:
+    """The model constants of a spec as the oracle uses them: every
+    coefficient the library takes as an FP32 field and uses as it is (the
+    adaptation strength, threshold, surrogate constants, learning rate,
+    drive weight, filter constant kappa_e when given, reset value,
+    regularisation and Adam constants) is taken at its FP32 value, so both
+    evaluate the method for the same numbers; the decay factors alpha =
+    exp(-dt / tau_m), rho = exp(-dt / tau_a), kappa = exp(-dt / tau_out) are
+    formed in FP64 from the spec's time constants (the workloads use time
+    constants that FP32 holds exactly)."""
+    dt, tau_m, tau_a, tau_out = spec.dt, spec.tau_m, spec.tau_a, spec.tau_out
+    kappa = math.exp(-dt / tau_out)
+    return dict(alpha=math.exp(-dt / tau_m), rho=math.exp(-dt / tau_a), kappa=kappa,
+                kappa_e=kappa if spec.kappa_e is None or spec.kappa_e < 0 else _f32(spec.kappa_e),
+                beta_a=_f32(spec.beta_a) if spec.neuron_model == 1 else 0.0,
+                v_th=_f32(spec.v_th), gamma=_f32(spec.gamma), beta_sg=_f32(spec.beta_sg),
+                lr=_f32(spec.lr), drive_weight=_f32(spec.drive_weight), v_reset=_f32(spec.v_reset),
+                c_reg=_f32(spec.c_reg), f_target=_f32(spec.f_target), beta_reg=_f32(spec.beta_reg),
+                adam_b1=_f32(spec.adam_b1), adam_b2=_f32(spec.adam_b2), adam_eps=_f32(spec.adam_eps))
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's per-synapse loop (results do not depend
+    on it); returns the count in effect."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def _p(a):
@@ -138,11 +173,9 @@ def arrival_contrib(spec, psi, L, U=None):
     L = np.ascontiguousarray(L, dtype=np.float64)
     T, N = psi.shape
     Q = np.zeros((T, N))
-    alpha = math.exp(-spec.dt / spec.tau_m)
-    rho = math.exp(-spec.dt / spec.tau_a)
-    kappa_e = math.exp(-spec.dt / spec.tau_out) if spec.kappa_e is None else float(spec.kappa_e)
-    beta = spec.beta_a if spec.neuron_model == 1 else 0.0
-    lib.oracle_arrival_contrib(alpha, rho, beta, kappa_e, T, U or T, N, _p(psi), _p(L), _p(Q))
+    p = params(spec)
+    lib.oracle_arrival_contrib(p["alpha"], p["rho"], p["beta_a"], p["kappa_e"], T, U or T, N, _p(psi),
+                               _p(L), _p(Q))
     return Q
 
 
@@ -213,14 +246,10 @@ def sampled_gradients(spec, src_spikes, delay, psi, y, targets, window, fb_rows,
             arrive[s, d[s]:] = src[s, :T - d[s]]
     psi = np.ascontiguousarray(psi, np.float64)
     assert psi.shape == (S, T)
-    alpha = math.exp(-spec.dt / spec.tau_m)
-    rho = math.exp(-spec.dt / spec.tau_a)
-    kappa = math.exp(-spec.dt / spec.tau_out)
-    kappa_e = kappa if spec.kappa_e is None else float(spec.kappa_e)
-    beta = spec.beta_a if spec.neuron_model == 1 else 0.0
+    p = params(spec)
     G, mag, sens = np.zeros(S), np.zeros(S), np.zeros(S)
-    lib.oracle_synapse_sample(alpha, rho, beta, kappa_e, S, T, _p(arrive), _p(psi), _p(L), _p(Ls),
-                              _p(G), _p(mag), _p(sens))
+    lib.oracle_synapse_sample(p["alpha"], p["rho"], p["beta_a"], p["kappa_e"], S, T, _p(arrive), _p(psi),
+                              _p(L), _p(Ls), _p(G), _p(mag), _p(sens))
     return G, mag, sens
 
 
@@ -316,25 +345,20 @@ class Oracle:
 
     def _cfg(self, T):
         s = self.spec
-        import math
-        kappa = math.exp(-s.dt / s.tau_out)
+        p = params(s)
         return _Cfg(n_in=s.n_in, n_rec=s.n_rec, n_out=s.n_out, batch=s.batch,
                     neuron_model=s.neuron_model, t_ref=s.t_ref, loss=s.loss,
                     feedback=s.feedback, update_interval=s.update_interval,
                     continuous=s.continuous, max_delay=s.max_delay,
                     n_drive_thr=int(self.thr.shape[0]),
-                    alpha=math.exp(-s.dt / s.tau_m),
-                    rho=math.exp(-s.dt / s.tau_a),
-                    kappa=kappa,
-                    kappa_e=kappa if s.kappa_e is None else float(s.kappa_e),
-                    beta_a=s.beta_a if s.neuron_model == 1 else 0.0,
-                    v_th=s.v_th, gamma=s.gamma, beta_sg=s.beta_sg, lr=s.lr,
-                    drive_weight=s.drive_weight, drive_seed=s.drive_seed,
+                    alpha=p["alpha"], rho=p["rho"], kappa=p["kappa"], kappa_e=p["kappa_e"],
+                    beta_a=p["beta_a"], v_th=p["v_th"], gamma=p["gamma"], beta_sg=p["beta_sg"],
+                    lr=p["lr"], drive_weight=p["drive_weight"], drive_seed=s.drive_seed,
                     drive_thr=_p(self.thr) if self.thr.shape[0] else None,
-                    surrogate=s.surrogate, reset_mode=s.reset_mode, v_reset=s.v_reset,
-                    c_reg=s.c_reg, f_target=s.f_target, beta_reg=s.beta_reg,
-                    sign_mask=s.sign_mask, optimizer=s.optimizer, adam_b1=s.adam_b1,
-                    adam_b2=s.adam_b2, adam_eps=s.adam_eps, if_period=s.if_period,
+                    surrogate=s.surrogate, reset_mode=s.reset_mode, v_reset=p["v_reset"],
+                    c_reg=p["c_reg"], f_target=p["f_target"], beta_reg=p["beta_reg"],
+                    sign_mask=s.sign_mask, optimizer=s.optimizer, adam_b1=p["adam_b1"],
+                    adam_b2=p["adam_b2"], adam_eps=p["adam_eps"], if_period=s.if_period,
                     if_seed=s.if_seed)
 
     def _state(self):
@@ -428,11 +452,8 @@ def event_driven_gradients(spec, ptr, col, delay, src_raster, psi, L, T_len=None
     """
     import math
     T = psi.shape[0] if T_len is None else T_len
-    alpha = math.exp(-spec.dt / spec.tau_m)
-    rho = math.exp(-spec.dt / spec.tau_a)
-    kappa = math.exp(-spec.dt / spec.tau_out)
-    kappa_e = kappa if spec.kappa_e is None else spec.kappa_e
-    beta_a = spec.beta_a if spec.neuron_model == 1 else 0.0
+    p = params(spec)
+    alpha, rho, kappa_e, beta_a = p["alpha"], p["rho"], p["kappa_e"], p["beta_a"]
     n_src = ptr.shape[0] - 1
     grads = np.zeros(int(ptr[-1]))
     for i in range(n_src):

@@ -80,6 +80,11 @@
  * E_override (optional, [B][T][K]): where window = 0, E^t is taken from it
  * instead of from the loss (the learned predictor's error estimate).
  *
+ * Threads: the per-synapse loop of each step may run on several host
+ * threads (OpenMP, when built with it); every synapse is updated by exactly
+ * one thread and no sum crosses synapses, so the results do not depend on
+ * the thread count.
+ *
  * Teacher forcing: `forced` replaces the spikes z; `forced_psi` (optional)
  * replaces the surrogate values psi used by the traces, so that the trace
  * and gradient arithmetic can be compared in isolation.
@@ -88,6 +93,21 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the per-synapse loop (1 without OpenMP); returns the count in
+   effect. */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 typedef struct {
     int32_t n_in, n_rec, n_out, batch;
@@ -442,7 +462,10 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 if (L_rec) L_rec[bt * N + j] = acc;
             }
 
-            /* eligibility traces and gradients, every synapse, every step */
+            /* eligibility traces and gradients, every synapse, every step;
+               each synapse's state and sums are its own, so the sources may
+               be visited by several threads (OpenMP) with identical results */
+#pragma omp parallel for schedule(dynamic, 64)
             for (int64_t i = 0; i < NS; ++i) {
                 for (int64_t q = s->ptr[i]; q < s->ptr[i + 1]; ++q) {
                     const int64_t j = s->col[q];

@@ -221,7 +221,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         return fail(nullptr, EPROP_EINVAL, "sizes out of range (n_rec < 2^24, 1 <= n_out <= 1024, batch < 2048)");
     if (c.max_delay < 1 || c.max_delay > eprop::kMaxDelay) return fail(nullptr, EPROP_EINVAL, "max_delay must be 1..8");
     if (c.neuron_model < 0 || c.neuron_model > 1 || c.loss < 0 || c.loss > 2 || c.feedback < 0 ||
-        c.feedback > 1 || c.trace_dtype < 0 || c.trace_dtype > 1 || c.t_ref < 0 || c.update_interval < 0)
+        c.feedback > 1 || c.trace_dtype < 0 || c.trace_dtype > 2 || c.t_ref < 0 || c.update_interval < 0)
         return fail(nullptr, EPROP_EINVAL, "invalid enum or negative parameter");
     if (c.batch > 1 && (c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL, "batch > 1 needs continuous = 0 and update_interval = 0");
@@ -264,7 +264,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     if (!net) return fail(nullptr, EPROP_ENOMEM, "host allocation failed");
     net->cfg = c;
     net->st = (cudaStream_t)cuda_stream;
-    if (net->st == nullptr && c.launch_mode == 1) {
+    if (net->st == nullptr && c.launch_mode >= 1) {
         // graphs cannot be captured on the legacy default stream
         if (cudaStreamCreateWithFlags(&net->st, cudaStreamNonBlocking) != cudaSuccess) {
             delete net;
@@ -290,7 +290,7 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     n.D = c.max_delay; n.nnz = nnz;
     n.alif = c.neuron_model == 1; n.t_ref = c.t_ref; n.loss = c.loss; n.feedback = c.feedback;
     n.has_state = (c.continuous || c.update_interval > 0) ? 1 : 0;
-    n.trace_bf16 = c.trace_dtype == 1; n.record_grad = c.record_grad != 0;
+    n.trace_bf16 = c.trace_dtype != 0; n.trace_type = c.trace_dtype; n.record_grad = c.record_grad != 0;
     n.record_raster = c.record_raster != 0; n.record_psi = c.record_psi != 0; n.n_thr = c.drive_weight != 0.f ? c.n_drive_thr : 0;
     const double alpha = std::exp(-(double)c.dt / c.tau_m);
     const double kappa = std::exp(-(double)c.dt / c.tau_out);
@@ -621,6 +621,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     // window pass: two blocks per SM by default (a third fits, but the
     // smaller L1 that leaves for the table lookups measured slower)
     const int pass_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 2) * net->sm_count;
+    const int idle_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 3) * net->sm_count;
     const int nw = T / U;
     if (c.profile && (int)net->ev.size() < 2 * nw) {
         for (int q = (int)net->ev.size(); q < 2 * nw; ++q) {
@@ -698,7 +699,7 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
                 LT += 1;
             } else if (net->trace_mode == 2) {
-                eprop::launch_window_pass(n, i, pass_rows, st);
+                eprop::launch_window_pass(n, i, pass_rows, idle_rows, st);
                 LT += 3;
             } else {
                 eprop::launch_trace_window(n, i, grid_rows, st);

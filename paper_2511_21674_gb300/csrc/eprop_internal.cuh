@@ -27,6 +27,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace eprop {
@@ -57,6 +58,7 @@ struct Net {
     long long nnz;
     // model switches
     int alif, t_ref, loss, feedback, has_state, trace_bf16, record_grad, record_raster, record_psi;
+    int trace_type;           // trace storage: 0 FP32, 1 BF16, 2 FP16 (trace_bf16: any 16-bit form)
     int dense;                // 1: every synapse advanced at every window end (no catch-up)
     int n_thr, T;             // T of the current call
     int segs;                 // segments per row: ceil(max out-degree / kSeg)
@@ -296,15 +298,23 @@ __device__ __forceinline__ bool bit_at(const uint32_t *words, int RW, int r) {
 
 // Record streams are touched once per event: evict-first loads and
 // streaming stores keep them from displacing the lookup tables in L2.
-__device__ __forceinline__ float load_trace(const void *base, long long q, int bf16) {
-    if (bf16) {
+// 16-bit trace values: BF16 (type 1) or FP16 (type 2), rounded to nearest
+// even on the way in
+__device__ __forceinline__ float trace16_to_float(unsigned short h, int type) {
+    return type == 2 ? __half2float(__ushort_as_half(h)) : __bfloat162float(__ushort_as_bfloat16(h));
+}
+__device__ __forceinline__ unsigned short float_to_trace16(float x, int type) {
+    return type == 2 ? __half_as_ushort(__float2half_rn(x)) : __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float load_trace(const void *base, long long q, int type) {
+    if (type) {
         const unsigned short h = __ldcs(reinterpret_cast<const unsigned short *>(base) + q);
-        return __bfloat162float(__ushort_as_bfloat16(h));
+        return trace16_to_float(h, type);
     }
     return __ldcs(reinterpret_cast<const float *>(base) + q);
 }
-__device__ __forceinline__ void store_trace(void *base, long long q, float x, int bf16) {
-    if (bf16) __stcs(reinterpret_cast<unsigned short *>(base) + q, __bfloat16_as_ushort(__float2bfloat16_rn(x)));
+__device__ __forceinline__ void store_trace(void *base, long long q, float x, int type) {
+    if (type) __stcs(reinterpret_cast<unsigned short *>(base) + q, float_to_trace16(x, type));
     else __stcs(reinterpret_cast<float *>(base) + q, x);
 }
 

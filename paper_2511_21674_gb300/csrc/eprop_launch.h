@@ -20,7 +20,7 @@ void launch_filter_error(const Net &n, int i_end, cudaStream_t st);
 int launch_tables(const Net &n, int i_end, cudaStream_t st);
 void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st);
 void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st);
-void launch_window_pass(const Net &n, int i_end, int grid_x, cudaStream_t st);
+void launch_window_pass(const Net &n, int i_end, int grid_x, int grid_idle, cudaStream_t st);
 void launch_pred_input(const Net &n, int i, cudaStream_t st);
 void launch_pred_apply(const Net &n, int i, cudaStream_t st);
 void launch_readout_weights(const Net &n, int i_end, cudaStream_t st);

@@ -421,7 +421,7 @@ __device__ __forceinline__ void issue_chunk(const Net &n, StageBuf &sb, uint64_t
 
 __device__ __forceinline__ float stage_trace(const Net &n, const StageBuf &sb, const StageDesc &d, long long q) {
     if (n.trace_bf16)
-        return __bfloat162float(__ushort_as_bfloat16(reinterpret_cast<const uint16_t *>(sb.tr)[q - d.q_al2]));
+        return trace16_to_float(reinterpret_cast<const uint16_t *>(sb.tr)[q - d.q_al2], n.trace_type);
     return reinterpret_cast<const float *>(sb.tr)[q - d.q_al];
 }
 
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(256, STATE ? 2 : 4) deliver_kernel(Net n, int 
                     const long long j = td[u] & 0xFFFFFFu;
                     float zbar = info[warp][k][td[u] >> 24].zbar_bp;
                     float ebar = eb[u], G = 0.f;
-                    float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+                    float epsa = ALIF ? load_trace(n.epsa, q, n.trace_type) : 0.f;
                     apply_coef<ALIF>(n, cf0[u], zbar, epsa, ebar, G);
                     if (k0 + 1 < k1) apply_coef<ALIF>(n, cf1[u], zbar, epsa, ebar, G);
                     for (int kk = k0 + 2; kk < k1; ++kk) apply_window<ALIF>(n, j, kk, zbar, epsa, ebar, G);

@@ -365,7 +365,7 @@ __device__ __forceinline__ void issue_chunk_w(const Net &n, StageBuf &sb, uint64
 
 __device__ __forceinline__ float stage_trace_w(const Net &n, const StageBuf &sb, const StageDesc &d, long long q) {
     if (n.trace_bf16)
-        return __bfloat162float(__ushort_as_bfloat16(reinterpret_cast<const uint16_t *>(sb.tr)[q - d.q_al2]));
+        return trace16_to_float(reinterpret_cast<const uint16_t *>(sb.tr)[q - d.q_al2], n.trace_type);
     return reinterpret_cast<const float *>(sb.tr)[q - d.q_al];
 }
 
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
                 k0s[u] = -1;
                 wv[u] = has ? sb.w[q - d.q_al] : 0.f;
                 eb[u] = (STATE && has) ? stage_trace_w(n, sb, d, q) : 0.f;
-                ep[u] = (STATE && ALIF && has) ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+                ep[u] = (STATE && ALIF && has) ? load_trace(n.epsa, q, n.trace_type) : 0.f;
                 t0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (has && listed) {
                     const long long qi = qa + (long long)(sp[cc] + dl) * N + j;
@@ -594,8 +594,8 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
                     if (!n.adam) __stcs(n.w + q, wn);
                 }
                 if (STATE) {
-                    store_trace(n.ebar, q, ebar, n.trace_bf16);
-                    if (ALIF) store_trace(n.epsa, q, epsa, n.trace_bf16);
+                    store_trace(n.ebar, q, ebar, n.trace_type);
+                    if (ALIF) store_trace(n.epsa, q, epsa, n.trace_type);
                 }
                 if (n.record_grad) n.grad[q] += n.inv_B * G;
             }
@@ -653,8 +653,13 @@ __device__ __forceinline__ float4 load_table(const Net &n, long long qi) {
     return make_float4(t.x, t.y, 0.f, 0.f);
 }
 
-template <bool ALIF, int MODE, bool TB>
-__global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
+// The idle-row launch fits three blocks per SM (more warps for its
+// coefficient gathers); the spiking-row launch keeps two (it needs the
+// registers of its table lookups).
+// TB: trace storage (0 FP32, 1 BF16, 2 FP16); GEN: the general weight update
+// (Adam or fixed signs), else plain gradient descent in place.
+template <bool ALIF, int MODE, int TB, bool GEN>
+__global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_kernel(Net n, int i_end) {
     constexpr bool LISTS = MODE != kPassIdle;        // work items from the spike lists
     constexpr int kBatch = LISTS ? 1 : 32;           // work items per fetch
     constexpr unsigned kFull = 0xffffffffu;
@@ -857,8 +862,8 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                 td[u] = in ? sb.td[o4 + idx] : 0u;
                 const int dl = (int)(td[u] >> 24);
                 wv[u] = in ? sb.w[o4 + idx] : 0.f;
-                if (TB) eb[u] = in ? __bfloat162float(__ushort_as_bfloat16(
-                                         reinterpret_cast<const uint16_t *>(sb.tr)[o2 + idx])) : 0.f;
+                if (TB) eb[u] = in ? trace16_to_float(reinterpret_cast<const uint16_t *>(sb.tr)[o2 + idx], TB)
+                                   : 0.f;
                 else eb[u] = in ? reinterpret_cast<const float *>(sb.tr)[o4 + idx] : 0.f;
                 c0[u] = -1;
                 t0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -904,11 +909,14 @@ __global__ void __launch_bounds__(256, 2) window_pass_kernel(Net n, int i_end) {
                     }
                 }
                 if (G != 0.f) {
-                    const float wn = window_update(n, d.q0 + idx, wv[u], G);
-                    if (!n.adam) __stcs(wq + idx, wn);
+                    if (GEN) {
+                        const float wn = window_update(n, d.q0 + idx, wv[u], G);
+                        if (!n.adam) __stcs(wq + idx, wn);
+                    } else {
+                        __stcs(wq + idx, wv[u] - step * G);
+                    }
                 }
-                if (TB) __stcs(reinterpret_cast<uint16_t *>(n.ebar) + d.q0 + idx,
-                               __bfloat16_as_ushort(__float2bfloat16_rn(ebar)));
+                if (TB) __stcs(reinterpret_cast<uint16_t *>(n.ebar) + d.q0 + idx, float_to_trace16(ebar, TB));
                 else __stcs(reinterpret_cast<float *>(n.ebar) + d.q0 + idx, ebar);
                 if (ALIF) store_trace(n.epsa, d.q0 + idx, epsa, TB);
                 if (n.record_grad) gq[idx] += n.inv_B * G;
@@ -1181,8 +1189,8 @@ __global__ void flush_kernel(Net n, int i_end, float *w_dst, float *g_dst, long 
             float G = 0.f;
             if (ri.b_prev != kNoSpike && ri.b_prev < a0) {
                 float zbar = ri.zbar_bp;
-                float ebar = load_trace(n.ebar, q, n.trace_bf16);
-                float epsa = ALIF ? load_trace(n.epsa, q, n.trace_bf16) : 0.f;
+                float ebar = load_trace(n.ebar, q, n.trace_type);
+                float epsa = ALIF ? load_trace(n.epsa, q, n.trace_type) : 0.f;
                 int k0 = ri.k_prev;
                 const int k1 = a0 / U;
                 if (k1 - k0 > n.RC) {
@@ -1278,12 +1286,14 @@ void launch_adam(const Net &n, int sm_count, cudaStream_t st) {
 
 void prepare_kernel_attributes() {
     const int tl = 200 * 1024;
-#define EPROP_PASS_ATTR(A, P, T) \
-    cudaFuncSetAttribute(window_pass_kernel<A, P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl)
-#define EPROP_PASS_ATTR3(A, T) EPROP_PASS_ATTR(A, kPassIdle, T); EPROP_PASS_ATTR(A, kPassFirst, T)
+#define EPROP_PASS_ATTR(A, P, T, G) \
+    cudaFuncSetAttribute(window_pass_kernel<A, P, T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl)
+#define EPROP_PASS_ATTR2(A, T, G) EPROP_PASS_ATTR(A, kPassIdle, T, G); EPROP_PASS_ATTR(A, kPassFirst, T, G)
+#define EPROP_PASS_ATTR3(A, G) EPROP_PASS_ATTR2(A, 0, G); EPROP_PASS_ATTR2(A, 1, G); EPROP_PASS_ATTR2(A, 2, G)
     EPROP_PASS_ATTR3(true, true); EPROP_PASS_ATTR3(true, false);
     EPROP_PASS_ATTR3(false, true); EPROP_PASS_ATTR3(false, false);
 #undef EPROP_PASS_ATTR3
+#undef EPROP_PASS_ATTR2
 #undef EPROP_PASS_ATTR
     cudaFuncSetAttribute(trace_window_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
     cudaFuncSetAttribute(trace_window_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tl);
@@ -1331,20 +1341,28 @@ void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st) {
     }
 }
 
-void launch_window_pass(const Net &n, int i_end, int grid_x, cudaStream_t st) {
+void launch_window_pass(const Net &n, int i_end, int grid_x, int grid_idle, cudaStream_t st) {
     window_offsets_kernel<<<1, 32, 0, st>>>(n, i_end);
     const size_t sb = sizeof(StageBuf) * 8 * kPStages;
     const size_t sm = sb + (size_t)(n.U + n.D + 2) * sizeof(long long);
-#define EPROP_PASS(A, T)                                                  \
-    do {                                                                  \
-        window_pass_kernel<A, kPassFirst, T><<<grid_x, 256, sm, st>>>(n, i_end); \
-        window_pass_kernel<A, kPassIdle, T><<<grid_x, 256, sb, st>>>(n, i_end);  \
+#define EPROP_PASS(A, T, G)                                                             \
+    do {                                                                                \
+        window_pass_kernel<A, kPassFirst, T, G><<<grid_x, 256, sm, st>>>(n, i_end);     \
+        window_pass_kernel<A, kPassIdle, T, G><<<grid_idle, 256, sb, st>>>(n, i_end);   \
     } while (0)
+#define EPROP_PASS_T(A, G)                                        \
+    do {                                                          \
+        if (n.trace_type == 1) EPROP_PASS(A, 1, G);               \
+        else if (n.trace_type == 2) EPROP_PASS(A, 2, G);          \
+        else EPROP_PASS(A, 0, G);                                 \
+    } while (0)
+    const bool gen = n.adam || n.sign_mask;
     if (n.alif) {
-        if (n.trace_bf16) EPROP_PASS(true, true); else EPROP_PASS(true, false);
+        if (gen) EPROP_PASS_T(true, true); else EPROP_PASS_T(true, false);
     } else {
-        if (n.trace_bf16) EPROP_PASS(false, true); else EPROP_PASS(false, false);
+        if (gen) EPROP_PASS_T(false, true); else EPROP_PASS_T(false, false);
     }
+#undef EPROP_PASS_T
 #undef EPROP_PASS
 }
 

@@ -183,6 +183,7 @@ def sample_oracle_job(job):
     of one sample of a single-window batched call; returns everything the
     parity check aggregates over the batch."""
     import oracle
+    oracle.set_threads(1)                 # one thread per worker process
     Wb, raster, psi = job
     s = Wb["spec"]
     mk = lambda: oracle.Oracle(s, Wb["ptr"], Wb["col"], Wb["w"], Wb["delay"], Wb["w_out"],

@@ -423,12 +423,13 @@ def test_single_step_samples_and_length_one():
     run_parity(W)
 
 
+@pytest.mark.parametrize("dtype", [pytest.param(1, id="bf16"), pytest.param(2, id="fp16")])
 @pytest.mark.parametrize("tk", STATE_KERNELS)
-def test_bf16_traces_report_error(tk):
-    # form (1): traces stored in BF16, FP32 accumulation; error vs the FP64
-    # oracle is reported, not gated at 1e-5
+def test_16bit_traces_report_error(tk, dtype):
+    # form (1): traces stored in BF16 or FP16, FP32 accumulation; error vs the
+    # FP64 oracle is reported, not gated at 1e-5
     W = _replica(True, 200)
-    rep = run_parity(W, calls=3, gpu_kw=dict(trace_dtype=1, trace_kernel=tk), check=False)
-    print("bf16 traces: rel_l2", {k: f"{v:.3g}" for k, v in rep["rel_l2"].items()},
-          "decision mismatches", rep["mismatches"])
+    rep = run_parity(W, calls=3, gpu_kw=dict(trace_dtype=dtype, trace_kernel=tk), check=False)
+    print(("bf16" if dtype == 1 else "fp16") + " traces: rel_l2",
+          {k: f"{v:.3g}" for k, v in rep["rel_l2"].items()}, "decision mismatches", rep["mismatches"])
     assert rep["rel_l2"]["g_rec"] < 1e-2

@@ -197,9 +197,11 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
     exponential moving average rate (Eq. ema-rate)."""
     s = net["spec"]
     B, N, K, NI = s.batch, s.n_rec, s.n_out, s.n_in
-    alpha, rho = math.exp(-1 / s.tau_m), math.exp(-1 / s.tau_a)
-    kappa = math.exp(-1 / s.tau_out)
-    beta_a = s.beta_a if s.neuron_model == 1 else 0.0
+    # the parameter values as the oracle (and the library) take them
+    pv = oracle.params(s)
+    alpha, rho, kappa, beta_a = pv["alpha"], pv["rho"], pv["kappa"], pv["beta_a"]
+    v_th, gamma, beta_sg, v_reset = pv["v_th"], pv["gamma"], pv["beta_sg"], pv["v_reset"]
+    c_reg, f_target, beta_reg = pv["c_reg"], pv["f_target"], pv["beta_reg"]
     ptr = net["ptr"]
     src = torch.tensor(np.repeat(np.arange(len(ptr) - 1), np.diff(ptr)))
     col = torch.tensor(net["col"].astype(np.int64))
@@ -223,14 +225,14 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
                     arrive[q] = hist[tt][int(src[q])]
             I = torch.zeros(N, dtype=torch.float64).index_add(0, col, w * arrive)
             a = rho * a + zprev
-            vth = s.v_th + beta_a * a
+            vth = v_th + beta_a * a
             if s.reset_mode == 1:
-                v = alpha * v + I + (zprev * (s.v_reset - alpha * v)).detach()
+                v = alpha * v + I + (zprev * (v_reset - alpha * v)).detach()
             else:
                 v = alpha * v + I - (zprev * vth).detach()
             refr = torch.tensor(ref > 0)
             zg = torch.tensor(z_raster[b, t - 1].astype(np.float64))
-            z = _Spike.apply(v - vth, zg, refr, s.gamma, s.beta_sg, s.surrogate)
+            z = _Spike.apply(v - vth, zg, refr, gamma, beta_sg, s.surrogate)
             ref = np.where(ref > 0, ref - 1, 0)
             ref[z_raster[b, t - 1] > 0] = s.t_ref
             hist[t] = torch.cat([torch.tensor(x_raster[b, t - 1].astype(np.float64)),
@@ -244,9 +246,9 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
                 total = total + win * ((y - tg) ** 2).sum() / K
             else:
                 total = total - win * (tg * torch.log_softmax(y, 0)).sum()
-            if s.c_reg != 0.0:
-                f = s.beta_reg * f + (1.0 - s.beta_reg) * z
-                total = total + 0.5 * s.c_reg * ((f - s.f_target) ** 2).sum()
+            if c_reg != 0.0:
+                f = beta_reg * f + (1.0 - beta_reg) * z
+                total = total + 0.5 * c_reg * ((f - f_target) ** 2).sum()
             zprev = z
     (total / B).backward()
     return w.grad.numpy(), wo.grad.numpy()

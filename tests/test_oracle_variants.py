@@ -50,11 +50,12 @@ def test_adam_per_window_equals_torch_adam(eps_hat):
     W = _small()
     s = W["spec"]
     s.optimizer, s.adam_eps = 1, eps_hat
-    b1, b2 = s.adam_b1, s.adam_b2
+    pv = oracle.params(s)                        # the constants as the oracle takes them
+    b1, b2, eps_hat = pv["adam_b1"], pv["adam_b2"], pv["adam_eps"]
     o_adam = _oracle(W)
     w = torch.tensor(np.asarray(W["w"], np.float64), requires_grad=True)
     wo = torch.tensor(np.asarray(W["w_out"], np.float64), requires_grad=True)
-    opt = torch.optim.Adam([w, wo], lr=s.lr, betas=(b1, b2), eps=0.0)
+    opt = torch.optim.Adam([w, wo], lr=pv["lr"], betas=(b1, b2), eps=0.0)
     for k in range(1, 5):
         _sim(o_adam, W)
         # the plain gradient at the current weights (SGD oracle, lr 0)

@@ -190,3 +190,111 @@ def test_trained_predictor_brings_the_gradient_closer_to_the_full_signal():
     # gradient it drives is measurably closer to the full-signal gradient
     assert corr > 0.1
     assert c_pred > c_plain + 0.05
+
+
+def _pairs(net, W, seeds, T):
+    """(x^t, E^t) of every live step of the given sample batches, target
+    known at every step (the network is frozen: lr 0)."""
+    X, E = [], []
+    for sd in seeds:
+        Ws = C.event_classification(batch=W["spec"].batch, sample_seed=sd)
+        net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], np.ones_like(Ws["window"]),
+                       Ws["lengths"], T)
+        net.simulate(T)
+        y, _ = net.readout()
+        x = net.predictor_inputs()
+        live = np.arange(T)[None, :] < Ws["lengths"][:, None]
+        X.append(x[live])
+        E.append(P.softmax_error(y, Ws["targets"])[live])
+    return np.concatenate(X).astype(np.float32), np.concatenate(E).astype(np.float32)
+
+
+def _train_eprop(W, pred, seeds, eval_sets):
+    """e-prop training on the given batches (predictor attached with mode 1
+    when pred is given), then the mean windowed loss on the held-out
+    batches with frozen weights."""
+    import paper_2511_21674_gb300 as ep
+    s = W["spec"]
+    net = _net(W, launch_mode=1)
+    if pred is not None:
+        net.attach_predictor(pred, mode=1)
+    curve = []
+    for sd in seeds:
+        Ws = C.event_classification(batch=s.batch, sample_seed=sd)
+        net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], Ws["window"], Ws["lengths"], s.T)
+        net.simulate(s.T)
+        curve.append(float(net.readout()[1].mean()))
+    w_in = net.weights(ep.PROJ_IN)
+    w_rec = net.weights(ep.PROJ_REC)
+    w_out = net.weights(ep.PROJ_OUT)
+    net.close()
+    # held-out loss with the trained weights (plain network, lr 0)
+    s2 = C.Spec(**{**s.__dict__, "lr": 0.0})
+    W2 = dict(W, spec=s2, w=np.concatenate([w_in, w_rec]), w_out=w_out)
+    net = _net(W2, launch_mode=1)
+    losses = []
+    for Ws in eval_sets:
+        net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], Ws["window"], Ws["lengths"], s.T)
+        net.simulate(s.T)
+        losses.append(net.readout()[1])
+    net.close()
+    return float(np.concatenate(losses).mean()), curve
+
+
+def test_predictor_at_scale_final_loss_against_plain_eprop():
+    # the stated experiment: the predictor trained on ~1e6 (state, E) pairs
+    # that plain e-prop runs of the event-classification network generate,
+    # then e-prop trained with and without it on the same batches and
+    # judged by the held-out loss in the target window; the batch-256
+    # inference time per step is reported
+    import torch
+    import paper_2511_21674_gb300 as ep
+    W = C.event_classification(batch=64)
+    s = W["spec"]
+    K, T = s.n_out, s.T
+    s0 = C.Spec(**{**s.__dict__, "lr": 0.0})
+    net = _net(dict(W, spec=s0))
+    pred = ep.Predictor(K + 64, K, seed=11, max_rows=4096)
+    net.attach_predictor(pred, mode=2)
+    X, E = _pairs(net, dict(W, spec=s0), range(20000, 20053), T)
+    net.close()
+    assert X.shape[0] >= 1_000_000, X.shape
+    pred.set_input_scale((1.0 / np.maximum(X.std(axis=0), 1e-3)).astype(np.float32))
+    rng = np.random.default_rng(1)
+    first = last = None
+    for epoch in range(3):
+        order = rng.permutation(len(X))
+        for lo in range(0, len(X) - 4095, 4096):
+            idx = order[lo:lo + 4096]
+            last = pred.train_step(X[idx], E[idx], 1e-3)
+            first = last if first is None else first
+    # batch-256 inference per step (device pointers, CUDA events)
+    xd = torch.from_numpy(X[:256]).cuda()
+    yd = torch.empty((256, K), dtype=torch.float32, device="cuda")
+    lib = ep.load_library()
+    for _ in range(10):
+        lib.eprop_predictor_forward(pred.h, xd.data_ptr(), 256, yd.data_ptr(), 1)
+    lib.eprop_predictor_sync(pred.h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(200):
+        lib.eprop_predictor_forward(pred.h, xd.data_ptr(), 256, yd.data_ptr(), 1)
+    e1.record()
+    torch.cuda.synchronize()
+    lib.eprop_predictor_sync(pred.h)
+    us = 1000.0 * e0.elapsed_time(e1) / 200
+    train = list(range(30000, 30020))
+    held = [C.event_classification(batch=64, sample_seed=40000 + k) for k in range(2)]
+    loss_plain, curve_plain = _train_eprop(W, None, train, held)
+    loss_pred, curve_pred = _train_eprop(W, pred, train, held)
+    pred.close()
+    report = dict(pairs=int(X.shape[0]), predictor_train_loss=[first, last],
+                  inference_us_per_step_batch256=us, heldout_loss_plain=loss_plain,
+                  heldout_loss_with_predictor=loss_pred,
+                  train_loss_plain=curve_plain[::5], train_loss_with_predictor=curve_pred[::5])
+    PT.report(dict(predictor_scale=report))
+    print("predictor at scale:", report)
+    assert last < first
+    assert math.isfinite(loss_plain) and math.isfinite(loss_pred)
+    assert loss_pred <= 1.02 * loss_plain
