@@ -615,9 +615,12 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     // the delivery and trace kernels hold two 256-thread blocks per SM (launch
     // bounds); their work queues are drained by whichever blocks are resident
     const int grid_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 2) * net->sm_count;
-    // delivery without carried state holds four blocks per SM
-    const int deliver_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : (n.has_state && !n.dense ? 2 : 4)) *
-                             net->sm_count;
+    // delivery without carried state holds four blocks per SM; with several
+    // samples the grid's x dimension is shared among them (each sample's
+    // step has a few spiking rows, not enough for a full grid of its own)
+    int deliver_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : (n.has_state && !n.dense ? 2 : 4)) *
+                       net->sm_count;
+    if (B > 1) deliver_rows = std::max(1, (int)((deliver_rows + B - 1) / B));
     // window pass: two blocks per SM by default (a third fits, but the
     // smaller L1 that leaves for the table lookups measured slower)
     const int pass_rows = (c.blocks_per_sm > 0 ? c.blocks_per_sm : 2) * net->sm_count;
@@ -644,7 +647,8 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     // Otherwise a readout trails the neuron updates by fewer than U steps
     // (the joins at window ends), and the ring's RS > U slots keep its
     // step's list until it has run.
-    const bool fork = n.pred_mode == 0 && n.RS > n.U;
+    // (the persistent step loop does the readout itself: one stream)
+    const bool fork = n.pred_mode == 0 && n.RS > n.U && c.launch_mode != 2;
     cudaStream_t sr = fork ? net->st2 : st;
     auto fork_readout = [&]() {
         if (!fork) return;

@@ -689,12 +689,12 @@ __global__ void __launch_bounds__(kPersThreads) persistent_steps_kernel(Net n, i
         // ---- phase A
         if (i > 1)
             for (int b = blockIdx.x; b < n.B; b += gridDim.x) readout_finish(n, i - 1, b);
-        if (n.n_in > 0)
-            for (int b = 0; b < n.B; ++b) {
+        if (n.n_in > 0)                          // input spikes: one warp per sample
+            for (int b = gwarp; b < n.B; b += nwarps) {
                 if (i > n.lengths[b]) continue;
                 const long long q0 = n.x_ptr[(long long)b * n.T + i - 1];
                 const long long q1 = n.x_ptr[(long long)b * n.T + i];
-                for (long long q = q0 + tid; q < q1; q += nth) mark_spike(n, b, n.x_ids[q], r);
+                for (long long q = q0 + lane; q < q1; q += 32) mark_spike(n, b, n.x_ids[q], r);
             }
         for (long long idx = tid; idx < (long long)n.B * n.n_rec; idx += nth) {
             const int b = (int)(idx / n.n_rec), j = (int)(idx - (long long)b * n.n_rec);

@@ -290,3 +290,20 @@ def test_evidence_accumulation_with_adam_batch32():
     # oracle's time in bounds
     W = C.evidence_accumulation(batch=32, t_delay=300)
     run_adam(W, calls=2, pooled=True)
+
+
+# ------------------------------------------------------- per-spike updates
+
+
+@pytest.mark.parametrize("tk", [pytest.param(1, id="lazy"), pytest.param(3, id="dense")])
+def test_weight_updates_with_every_spike(tk):
+    # e-prop+ weight updates with every spike (Results, "Weight updates with
+    # every spike"; Algorithm "Event-driven weight update"): with gradient
+    # descent the weight a spike carries is w0 - eta * (the gradient of every
+    # step before its emission), i.e. updates applied after every step
+    # (update window of one step, continuous dynamics); the lazy form applies
+    # them exactly at each presynaptic spike
+    W = C.pattern_regression(T=80, update_interval=1, continuous=1)
+    W["spec"].lr = 5e-4
+    rep = run_parity(W, calls=2, gpu_kw=dict(trace_kernel=tk))
+    assert rep["spikes"] > 50

@@ -256,7 +256,7 @@ def test_predictor_at_scale_final_loss_against_plain_eprop():
     net = _net(dict(W, spec=s0))
     pred = ep.Predictor(K + 64, K, seed=11, max_rows=4096)
     net.attach_predictor(pred, mode=2)
-    X, E = _pairs(net, dict(W, spec=s0), range(20000, 20053), T)
+    X, E = _pairs(net, dict(W, spec=s0), range(20000, 20060), T)
     net.close()
     assert X.shape[0] >= 1_000_000, X.shape
     pred.set_input_scale((1.0 / np.maximum(X.std(axis=0), 1e-3)).astype(np.float32))
