@@ -48,6 +48,10 @@ __global__ void inject_kernel(Net n, int i) {
 // surrogate): clears its ring slot, writes v, a, ref, z_prev, psi and the
 // rate regularisation signal, and marks a spike.  Shared by the per-step
 // neuron kernel and the persistent step loop.
+// VAR: the e-prop+ variants (fixed reset, ignore-and-fire, exponential
+// surrogate, rate regularisation) are compiled in; the plain method's
+// instance carries none of their code.
+template <bool VAR>
 __device__ __forceinline__ void neuron_update(const Net &n, int i, int b, int j, long long nb, int r, int a0,
                                               long long t_abs, const uint32_t *thr_s, float *psi_row,
                                               long long *ring_row, long long acc_q, float v_hi_q, float v_lo_q,
@@ -79,7 +83,7 @@ __device__ __forceinline__ void neuron_update(const Net &n, int i, int b, int j,
         vth = fmaf(n.beta_a, a_hi_q, n.v_th);
         vth_lo = fmaf(n.beta_a, a_hi_q, n.v_th - vth) + n.beta_a * a_lo_q;
     }
-    if (n.reset_mode == 1 && zp != 0.0f) {
+    if (VAR && n.reset_mode == 1 && zp != 0.0f) {
         // fixed reset: v' = v_reset + I (the decayed membrane is replaced)
         float s, e;
         two_sum(n.v_reset, u_hi, s, e);
@@ -89,7 +93,7 @@ __device__ __forceinline__ void neuron_update(const Net &n, int i, int b, int j,
         v_hi_q = hi;
     } else {
         // v' = alpha v + I - z_prev v_th (Eq. lif_update), input term as a pair
-        if (n.reset_mode == 0) {
+        if (!VAR || n.reset_mode == 0) {
             float e;
             two_sum(u_hi, -zp * vth, u_hi, e);
             u_lo += e - zp * vth_lo;
@@ -103,7 +107,7 @@ __device__ __forceinline__ void neuron_update(const Net &n, int i, int b, int j,
     int z;
     if (n.forced) {
         z = n.forced[((long long)b * n.T + (i - 1)) * n.n_rec + j] ? 1 : 0;
-    } else if (n.if_period > 0) {
+    } else if (VAR && n.if_period > 0) {
         // ignore-and-fire: a fixed schedule with the neuron's own phase
         const uint32_t ph = (uint32_t)(mix64(n.if_seed ^ (uint64_t)j) >> 32) % (uint32_t)n.if_period;
         z = ((t_abs + (long long)ph) % n.if_period) == 0 ? 1 : 0;
@@ -111,14 +115,14 @@ __device__ __forceinline__ void neuron_update(const Net &n, int i, int b, int j,
         z = (!refractory && m > 0.0f) ? 1 : 0;
     }
     float psi;
-    if (n.surrogate == 1) {      // Eq. exponential-surrogate-gradient
+    if (VAR && n.surrogate == 1) {      // Eq. exponential-surrogate-gradient
         psi = refractory ? 0.0f : n.gamma * expf(-n.beta_sg * fabsf(m));
     } else {                     // Eq. piecewise-linear-surrogate-gradient
         const float hh = 1.0f - n.beta_sg * fabsf(m);
         psi = refractory ? 0.0f : n.gamma * fmaxf(hh, 0.0f);
     }
     psi_row[j] = psi;
-    if (n.R_win) {
+    if (VAR && n.R_win) {
         // moving-average rate (Eq. ema-rate) and the regularisation
         // signal of Eq. ema-gradient, with G_beta's factor (1 - beta)
         const float f = n.beta_reg * n.rate[nb] + (1.0f - n.beta_reg) * (float)z;
@@ -154,6 +158,7 @@ __device__ __forceinline__ void neuron_update(const Net &n, int i, int b, int j,
 constexpr int kNPT = 2;
 constexpr int kNeuronThreads = 256;
 
+template <bool VAR>
 __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
     __shared__ uint32_t thr_s[EPROP_MAX_DRIVE_THR];
     __shared__ Clock ck_s;
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(kNeuronThreads) neuron_kernel(Net n, int i) {
         const int j = jb + q * kNeuronThreads;
         if (j >= n.n_rec) break;
         const long long nb = nb0 + j;
-        neuron_update(n, i, b, j, nb, r, a0, t_abs, thr_s, psi_row, ring_row, acc[q], v_hi[q], v_lo[q],
+        neuron_update<VAR>(n, i, b, j, nb, r, a0, t_abs, thr_s, psi_row, ring_row, acc[q], v_hi[q], v_lo[q],
                       a_hi[q], a_lo[q], ref[q], zp8[q]);
     }
     }
@@ -706,7 +711,7 @@ __global__ void __launch_bounds__(kPersThreads) persistent_steps_kernel(Net n, i
                 if (n.record_psi) n.rec_psi[((long long)b * n.T + (i - 1)) * n.n_rec + j] = 0.0f;
                 continue;
             }
-            neuron_update(n, i, b, j, idx, r, a0, t_abs, thr_s, psi_row, ring_row, ring_row[j], n.v[idx],
+            neuron_update<true>(n, i, b, j, idx, r, a0, t_abs, thr_s, psi_row, ring_row, ring_row[j], n.v[idx],
                           n.v_lo[idx], n.alif ? n.a[idx] : 0.f, n.alif ? n.a_lo[idx] : 0.f, n.ref[idx],
                           n.z_prev[idx]);
         }
@@ -765,7 +770,10 @@ void launch_neuron(const Net &n, int i, int sm_count, cudaStream_t st) {
     // the resident blocks, walking several groups per block, measured slower)
     (void)sm_count;
     const int blocks = (n.n_rec + per_block - 1) / per_block;
-    neuron_kernel<<<dim3(blocks, n.B), kNeuronThreads, 0, st>>>(n, i);
+    if (n.surrogate || n.reset_mode || n.if_period || n.R_win)
+        neuron_kernel<true><<<dim3(blocks, n.B), kNeuronThreads, 0, st>>>(n, i);
+    else
+        neuron_kernel<false><<<dim3(blocks, n.B), kNeuronThreads, 0, st>>>(n, i);
 }
 
 void launch_readout(const Net &n, int i, int sm_count, cudaStream_t st) {
