@@ -388,32 +388,31 @@ __device__ __forceinline__ RowInfo row_info(const Net &n, const uint32_t *words,
 struct Coef {
     float4 c0, c1;
 };
-// L2 policy for the window coefficients (16 bytes per neuron, gathered by
-// every synapse of a window): kept last, so the synapse streams passing
-// through L2 do not evict them
-__device__ __forceinline__ uint64_t l2_evict_last() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ float4 ldg_f4_hint(const float4 *p, uint64_t pol) {
-    float4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-}
 template <bool ALIF>
 __device__ __forceinline__ Coef load_coef(const Net &n, long long j, int k) {
     Coef c;
     const int slot = k & (n.RC - 1);
-    const uint64_t pol = l2_evict_last();
     if (ALIF) {
         const float4 *p = reinterpret_cast<const float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
-        c.c0 = ldg_f4_hint(p, pol);
-        c.c1 = ldg_f4_hint(p + 1, pol);
+        c.c0 = __ldg(p);
+        c.c1 = __ldg(p + 1);
     } else {
-        c.c0 = ldg_f4_hint(reinterpret_cast<const float4 *>(n.coef) + (long long)j * n.RC + slot, pol);
+        c.c0 = __ldg(reinterpret_cast<const float4 *>(n.coef) + (long long)j * n.RC + slot);
+        c.c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return c;
+}
+// The dense window pass keeps one window of coefficients (RC = 1): target
+// j's entry is entry j.
+template <bool ALIF>
+__device__ __forceinline__ Coef load_coef_dense(const Net &n, uint32_t j) {
+    Coef c;
+    if (ALIF) {
+        const float4 *p = reinterpret_cast<const float4 *>(n.coef) + 2u * j;
+        c.c0 = __ldg(p);
+        c.c1 = __ldg(p + 1);
+    } else {
+        c.c0 = __ldg(reinterpret_cast<const float4 *>(n.coef) + j);
         c.c1 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     return c;

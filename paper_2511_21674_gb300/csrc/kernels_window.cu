@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
                 zr[u] = zrow[dl];
                 ep[u] = (ALIF && in) ? load_trace(n.epsa, d.q0 + idx, TB) : 0.f;
                 live[u] = in && (LISTS || zr[u] != 0.f || eb[u] != 0.f || ep[u] != 0.f);
-                if (live[u]) cf[u] = load_coef<ALIF>(n, td[u] & 0xFFFFFFu, 0);
+                if (live[u]) cf[u] = load_coef_dense<ALIF>(n, td[u] & 0xFFFFFFu);
                 if (c0[u] >= 0) t0[u] = load_table<ALIF>(n, qa + (long long)(sp[cc] + dl) * N + (td[u] & 0xFFFFFFu));
             }
 #pragma unroll
