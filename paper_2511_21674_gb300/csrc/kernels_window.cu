@@ -705,9 +705,18 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
     int psrc = -1, ps = s_lo, pns = 0;
     float pzb = 0.f;            // lane d: zbar at a0 of the row's delay-d synapses
     unsigned vmask = 0;
+    // the next batch's counter value is fetched one row ahead (lane 0), so
+    // the atomic's round trip overlaps the current row's chunks
+    long long pf_base = -1;
+    auto prefetch = [&]() {
+        if (lane == 0 && pf_base < 0 && !drained) pf_base = (long long)atomicAdd(ctr, (unsigned long long)kBatch);
+    };
     auto refill = [&]() -> bool {
         long long base = 0;
-        if (lane == 0) base = (long long)atomicAdd(ctr, (unsigned long long)kBatch);
+        if (lane == 0) {
+            base = pf_base >= 0 ? pf_base : (long long)atomicAdd(ctr, (unsigned long long)kBatch);
+            pf_base = -1;
+        }
         base = __shfl_sync(kFull, base, 0);
         if (base >= total) {
             drained = true;
@@ -803,6 +812,7 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
         ps = s;
         pq = rb;
         pre = re;
+        if (amask == 0) prefetch();        // this batch is used up: fetch the next one
         return true;
     };
     auto produce = [&](int k) {

@@ -209,25 +209,49 @@ def _pairs(net, W, seeds, T):
     return np.concatenate(X).astype(np.float32), np.concatenate(E).astype(np.float32)
 
 
-def _train_eprop(W, pred, train_sets, epochs, eval_sets):
-    """e-prop training over `epochs` passes of the given batches (predictor
-    attached with mode 1 when pred is given), then the mean windowed loss
-    and the accuracy on the held-out batches with frozen weights."""
+def _train_eprop(W, learner, lam, train_sets, epochs, eval_sets):
+    """e-prop training over `epochs` passes of the given batches; with a
+    learner, a copy of it whose output layer is scaled by lam is attached
+    (mode 3: its estimate stands in for E outside the target window), and
+    after every call the learner trains on the call's target-window steps
+    (where the true E is known) and the copy is refreshed.  Returns the mean
+    windowed loss and the accuracy on the held-out batches with frozen
+    weights, and the training-loss curve."""
     import paper_2511_21674_gb300 as ep
     s = W["spec"]
+    K = s.n_out
     net = _net(W, launch_mode=1)
-    if pred is not None:
-        net.attach_predictor(pred, mode=1)
+    actor = None
+    if learner is not None:
+        actor = ep.Predictor(K + 64, K, seed=0, max_rows=4096)
+        actor.set_input_scale(learner.input_scale)
+
+        def refresh():
+            p = learner.unpack(learner.read("params").copy())
+            p["W3"], p["b3"] = p["W3"] * lam, p["b3"] * lam
+            actor.set_params(learner.pack(p))
+        refresh()
+        net.attach_predictor(actor, mode=3)
     curve = []
     for _ in range(epochs):
         for Ws in train_sets:
             net.set_inputs(Ws["x_ptr"], Ws["x_ids"], Ws["targets"], Ws["window"], Ws["lengths"], s.T)
             net.simulate(s.T)
-            curve.append(float(net.readout()[1].mean()))
+            y, loss = net.readout()
+            curve.append(float(loss.mean()))
+            if learner is not None:
+                x = net.predictor_inputs()
+                win = Ws["window"].astype(bool)
+                e = P.softmax_error(y, Ws["targets"])
+                for _ in range(2):
+                    learner.train_step(x[win].astype(np.float32), e[win].astype(np.float32), 1e-3)
+                refresh()
     w_in = net.weights(ep.PROJ_IN)
     w_rec = net.weights(ep.PROJ_REC)
     w_out = net.weights(ep.PROJ_OUT)
     net.close()
+    if actor is not None:
+        actor.close()
     # held-out loss and accuracy with the trained weights (lr 0)
     s2 = C.Spec(**{**s.__dict__, "lr": 0.0})
     W2 = dict(W, spec=s2, w=np.concatenate([w_in, w_rec]), w_out=w_out)
@@ -288,13 +312,24 @@ def test_predictor_at_scale_final_loss_against_plain_eprop():
     lib.eprop_predictor_sync(pred.h)
     us = 1000.0 * e0.elapsed_time(e1) / 200
     # e-prop with and without the predictor: Adam (lr 2e-3) on the same 8
-    # batches for 6 epochs, judged on 2 held-out batches
+    # batches for 6 epochs, judged on 2 held-out batches.  The predictor
+    # keeps learning from each call's target window (the true E is known
+    # there) and its estimate enters with weight 0.1 before the window (a
+    # frozen predictor, or the full weight, made the network diverge: the
+    # estimate of an untrained network's error is biased towards uniform
+    # outputs, and outside the window it acts on 12 times as many steps)
+    # the pre-trained parameters start the online learner (fresh Adam state)
+    scale = (1.0 / np.maximum(X.std(axis=0), 1e-3)).astype(np.float32)
+    learner = ep.Predictor(K + 64, K, seed=11, max_rows=4096, params=pred.read("params").copy())
+    learner.set_input_scale(scale)
+    learner.input_scale = scale
+    pred.close()
     Wt = dict(W, spec=C.Spec(**{**s.__dict__, "optimizer": 1, "lr": 2e-3}))
     train = [C.event_classification(batch=64, sample_seed=30000 + k) for k in range(8)]
     held = [C.event_classification(batch=64, sample_seed=40000 + k) for k in range(2)]
-    loss_plain, acc_plain, curve_plain = _train_eprop(Wt, None, train, 6, held)
-    loss_pred, acc_pred, curve_pred = _train_eprop(Wt, pred, train, 6, held)
-    pred.close()
+    loss_plain, acc_plain, curve_plain = _train_eprop(Wt, None, 0.0, train, 6, held)
+    loss_pred, acc_pred, curve_pred = _train_eprop(Wt, learner, 0.1, train, 6, held)
+    learner.close()
     chance = 25 * math.log(K)
     report = dict(pairs=int(X.shape[0]), predictor_train_loss=[first, last],
                   inference_us_per_step_batch256=us, chance_loss=chance,
@@ -305,5 +340,6 @@ def test_predictor_at_scale_final_loss_against_plain_eprop():
     print("predictor at scale:", report)
     assert last < first
     assert loss_plain < 0.9 * chance, "plain e-prop must learn the task for the comparison to mean anything"
-    assert math.isfinite(loss_pred)
-    assert loss_pred <= 1.05 * loss_plain
+    # the gain: a lower held-out loss in the target window than plain e-prop
+    # after the same number of updates
+    assert loss_pred < loss_plain
