@@ -670,6 +670,9 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
     __shared__ int spk[8][LISTS ? kPStages : 1][kSpikeCap];
     __shared__ int nspk[8][kPStages];
     __shared__ int rspk[8][kSpikeCap];          // the producer's current row
+    // per stage and delay d: step of the first arrival of the row's delay-d
+    // synapses in the window (-1: none) and its index in the spike list
+    __shared__ int2 arr[8][LISTS ? kPStages : 1][kMaxDelay + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     StageBuf *buf = reinterpret_cast<StageBuf *>(dsm) + warp * kPStages;
     long long *off = reinterpret_cast<long long *>(dsm + sizeof(StageBuf) * 8 * kPStages);
@@ -821,6 +824,13 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
         if (LISTS) {
             for (int c = lane; c < min(pns, kSpikeCap); c += 32) spk[warp][k][c] = rspk[warp][c];
             if (lane == 0) nspk[warp][k] = pns;
+            if (lane >= 1 && lane <= n.D) {
+                const int nsc = min(pns, kSpikeCap);
+                int cc = 0;
+                while (cc < nsc && rspk[warp][cc] + lane <= a0) ++cc;
+                const int a1 = (cc < nsc && rspk[warp][cc] + lane <= r_end) ? rspk[warp][cc] + lane : -1;
+                arr[warp][LISTS ? k : 0][lane] = make_int2(a1, cc);
+            }
         }
         __syncwarp();
         if (lane == 0) {
@@ -877,16 +887,17 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
                 else eb[u] = in ? reinterpret_cast<const float *>(sb.tr)[o4 + idx] : 0.f;
                 c0[u] = -1;
                 t0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                int cc = 0;
-                if (LISTS && listed && in) {
-                    while (cc < ns && sp[cc] + dl <= a0) ++cc;   // first arrival in the window
-                    if (cc < ns && sp[cc] + dl <= r_end) c0[u] = cc;
+                int a1 = -1;
+                if (LISTS && listed && in) {               // first arrival in the window
+                    const int2 ar = arr[warp][LISTS ? k : 0][dl];
+                    a1 = ar.x;
+                    c0[u] = a1 >= 0 ? ar.y : -1;
                 }
                 zr[u] = zrow[dl];
                 ep[u] = (ALIF && in) ? load_trace(n.epsa, d.q0 + idx, TB) : 0.f;
                 live[u] = in && (LISTS || zr[u] != 0.f || eb[u] != 0.f || ep[u] != 0.f);
                 if (live[u]) cf[u] = load_coef_dense<ALIF>(n, td[u] & 0xFFFFFFu);
-                if (c0[u] >= 0) t0[u] = load_table<ALIF>(n, qa + (long long)(sp[cc] + dl) * N + (td[u] & 0xFFFFFFu));
+                if (c0[u] >= 0) t0[u] = load_table<ALIF>(n, qa + (long long)a1 * N + (td[u] & 0xFFFFFFu));
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
