@@ -45,10 +45,11 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="million", choices=["million", "scaling", "batched"],
+    p.add_argument("--workload", default="million", choices=["million", "scaling", "batched", "balanced"],
                    help="million: 1e6 LIF, in-degree 1000; scaling: the paper's scaling network "
                         "(128k ignore-and-fire neurons, in-degree 10,000, 20 s); batched: event "
-                        "classification, 64 samples of uneven length per call")
+                        "classification, 64 samples of uneven length per call; balanced: 1e5 LIF "
+                        "E/I network, in-degree 1000, T = 2000, one gradient per sequence")
     p.add_argument("--launch-mode", type=int, default=None,
                    help="0 eager launches, 1 graph of launches, 2 persistent step loop "
                         "(default: 1, and 2 for the batched workload)")
@@ -210,6 +211,15 @@ def workload_config(args, nnz, world=1):
                 "T_per_step": SCALING["T"], "trace_storage": args.trace_dtype,
                 "trace_form": args.trace_kernel, "parallelism": f"replicas{world}",
                 "l2": "inputs larger than L2 (synapse records ~13 GB)"}
+    if args.workload == "balanced":
+        return {"workload": f"sparse balanced: 100000 LIF (80% excitatory), fixed in-degree 1000 ({nnz} "
+                            "synapses), delays 1-5, Poisson drive (~5-10 Hz), 500 readout-coupled "
+                            "neurons, 1 readout (sum of sinusoids), T = 2000, one update at the "
+                            "sequence end",
+                "n_rec": 100_000, "k_in": 1000, "synapses": nnz, "T_per_step": 2000,
+                "trace_storage": args.trace_dtype, "trace_form": args.trace_kernel,
+                "parallelism": f"replicas{world}",
+                "l2": "inputs larger than L2 (synapse records ~1 GB per step)"}
     return {"workload": f"million_sparse: {args.n_rec} LIF, in-degree {args.k_in} ({nnz} synapses), "
                         f"delays 1-5, ~5 Hz, {args.n_out} readouts, update window 100, continuous",
             "n_rec": args.n_rec, "k_in": args.k_in, "synapses": nnz, "T_per_step": args.T,
@@ -262,6 +272,11 @@ def cpu_baseline(args, steps=1):
         sample = ("scaling network sample: 2000 ignore-and-fire neurons, recurrent in-degree 1000, "
                   "100 Poisson inputs (in-degree 10), 10 readouts (in-degree 100), feedback out-degree 20, "
                   f"100 steps x {steps}, FP64 time-driven oracle, {threads} threads")
+    elif args.workload == "balanced":
+        W = C.sparse_balanced(n_rec=args.cpu_sample_n, T=args.cpu_sample_T, n_coupled=500)
+        sample = (f"sparse balanced sample: {args.cpu_sample_n} LIF, in-degree 1000, delays 1-5, "
+                  f"500 readout-coupled, {args.cpu_sample_T} steps x {steps}, FP64 time-driven oracle, "
+                  f"{threads} threads")
     else:
         W = C.million_sparse(n_rec=args.cpu_sample_n, k_in=args.k_in, T=args.cpu_sample_T,
                              n_out=args.n_out)
@@ -369,6 +384,8 @@ def _run_ours(args, rank, world, local):
         W = C.event_classification(batch=64, seed=1235 + rank)
     elif args.workload == "scaling":
         W = G.scaling_torch(seed=replica_seed(rank) + 4, **SCALING)
+    elif args.workload == "balanced":
+        W = C.sparse_balanced(seed=replica_seed(rank) + 2)
     else:
         W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
                                    seed=replica_seed(rank))
@@ -428,8 +445,10 @@ def _run_ours(args, rank, world, local):
     # ---- end to end through the public API with host buffers
     h2d = (x_ptr.numel() * 8 + x_ids.numel() * 4 + targets.numel() * 4 + window.numel() +
            lengths.numel() * 4)
-    loss_host = np.zeros(spec.batch, np.float32)
-    y_host = np.zeros((spec.batch, T, spec.n_out), np.float32)
+    # results land in pinned host buffers
+    loss_t = torch.zeros(spec.batch, dtype=torch.float32).pin_memory()
+    y_t = torch.zeros((spec.batch, T, spec.n_out), dtype=torch.float32).pin_memory()
+    loss_host, y_host = loss_t.numpy(), y_t.numpy()
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -437,12 +456,14 @@ def _run_ours(args, rank, world, local):
     for _ in range(K):
         net.set_inputs(x_ptr, x_ids, targets, window, lengths, T)
         net.simulate(T)
-        net.lib.eprop_readout(net.h, None, loss_host.ctypes.data, None, 0)
+        # the step's results back on the host: readout trace y and loss
+        st_r = net.lib.eprop_readout(net.h, y_host.ctypes.data, loss_host.ctypes.data, None, 0)
+        if st_r != 0:
+            raise RuntimeError(f"eprop_readout failed: {st_r}")
         e2e_events += net.stats()["events"]
     torch.cuda.synchronize()
     e2e_s = barrier_max(time.perf_counter() - t0, world)
     e2e_value = (e2e_events * world) / e2e_s
-    del y_host
 
     # ---- roofline of the synapse-trace kernel
     bytes_per_event = 16.0 if trace_dtype else 20.0          # j|d 4 r, w 4 r/w, trace 2|4 r/w
@@ -479,7 +500,7 @@ def _run_ours(args, rank, world, local):
                      "trace_ms_per_step": trace_ms / K, "trace_launches_per_step": trace_launches / K},
         "samples_per_s": spec.batch * K / (ms_max / 1000.0),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(loss_host.nbytes)},
+                "d2h_bytes_per_step": int(loss_host.nbytes + y_host.nbytes)},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -97,7 +97,7 @@ struct Net {
     float *y;
     long long *y_acc;
     float *E_win, *Ebar_win, *Cwin;
-    float *L_win;             // [B][U][N] learning signals L = B E of the window (SGEMM)
+    float *L_win;             // [B][U][N] learning signals L = B E of the window (tensor cores)
     float *zk, *zk_next;
     float *y_rec, *loss_acc;
     // window tables

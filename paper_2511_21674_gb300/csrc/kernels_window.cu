@@ -92,7 +92,7 @@ __global__ void filter_error_kernel(Net n) {
 // learning-signal tables: one thread per (sample, neuron), 128 neurons per
 // block.  The window is swept backwards in chunks of steps: the chunk's
 // learning signals L^t = sum_k B_jk E_k^t (Eq. final-gradient; formed for
-// the whole window beforehand by one strided-batched SGEMM, L_win) are
+// the whole window beforehand on the tensor cores, L_win) are
 // loaded into registers, then the adjoint recursion writes the per-step
 // tables and, at the window start, the window coefficients.
 template <bool ALIF, bool REG, bool F64>
