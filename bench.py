@@ -49,7 +49,7 @@ def parse():
                    help="million: 1e6 LIF, in-degree 1000; scaling: the paper's scaling network "
                         "(128k ignore-and-fire neurons, in-degree 10,000, 20 s); batched: event "
                         "classification, 64 samples of uneven length per call; balanced: 1e5 LIF "
-                        "E/I network, in-degree 1000, T = 2000, one gradient per sequence")
+                        "E/I network, in-degree 1000, T = 2000, update window 100 (stored traces)")
     p.add_argument("--launch-mode", type=int, default=None,
                    help="0 eager launches, 1 graph of launches, 2 persistent step loop "
                         "(default: 1, and 2 for the batched workload)")
@@ -214,8 +214,8 @@ def workload_config(args, nnz, world=1):
     if args.workload == "balanced":
         return {"workload": f"sparse balanced: 100000 LIF (80% excitatory), fixed in-degree 1000 ({nnz} "
                             "synapses), delays 1-5, Poisson drive (~5-10 Hz), 500 readout-coupled "
-                            "neurons, 1 readout (sum of sinusoids), T = 2000, one update at the "
-                            "sequence end",
+                            "neurons, 1 readout (sum of sinusoids), T = 2000, update window 100, "
+                            "continuous (traces stored between windows), lr 1e-8",
                 "n_rec": 100_000, "k_in": 1000, "synapses": nnz, "T_per_step": 2000,
                 "trace_storage": args.trace_dtype, "trace_form": args.trace_kernel,
                 "parallelism": f"replicas{world}",
@@ -273,7 +273,8 @@ def cpu_baseline(args, steps=1):
                   "100 Poisson inputs (in-degree 10), 10 readouts (in-degree 100), feedback out-degree 20, "
                   f"100 steps x {steps}, FP64 time-driven oracle, {threads} threads")
     elif args.workload == "balanced":
-        W = C.sparse_balanced(n_rec=args.cpu_sample_n, T=args.cpu_sample_T, n_coupled=500)
+        W = C.sparse_balanced(n_rec=args.cpu_sample_n, T=args.cpu_sample_T, n_coupled=500,
+                              update_interval=100, continuous=1, lr=1e-8)
         sample = (f"sparse balanced sample: {args.cpu_sample_n} LIF, in-degree 1000, delays 1-5, "
                   f"500 readout-coupled, {args.cpu_sample_T} steps x {steps}, FP64 time-driven oracle, "
                   f"{threads} threads")
@@ -385,7 +386,10 @@ def _run_ours(args, rank, world, local):
     elif args.workload == "scaling":
         W = G.scaling_torch(seed=replica_seed(rank) + 4, **SCALING)
     elif args.workload == "balanced":
-        W = C.sparse_balanced(seed=replica_seed(rank) + 2)
+        # lr 1e-8 keeps the rate in the 5-10 Hz band over the timed calls
+        # (the regression signal through unit-variance feedback to every
+        # neuron raises it after ~50 updates at 1e-7)
+        W = C.sparse_balanced(seed=replica_seed(rank) + 2, update_interval=100, continuous=1, lr=1e-8)
     else:
         W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
                                    seed=replica_seed(rank))

@@ -156,8 +156,10 @@ typedef struct eprop_config {
                                  skipped window is caught up at the next
                                  arrival; 2 batched single window (no state
                                  carried between windows); 3 dense window
-                                 pass (batch 1): every synapse is advanced
-                                 at every window end                         */
+                                 pass (batch 1, carried state: continuous or
+                                 update_interval > 0, else EPROP_EINVAL):
+                                 every synapse is advanced at every window
+                                 end                                         */
     int32_t blocks_per_sm;    /* CTAs per SM of the row kernels; 0 = 2        */
     int32_t profile;          /* 1: time the synapse-trace kernels of every
                                  window with CUDA events (see eprop_stats)    */

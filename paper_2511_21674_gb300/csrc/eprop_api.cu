@@ -232,6 +232,9 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
                     "launch_mode 2 (persistent step loop) needs one update window per call and n_out <= 256");
     if (c.trace_kernel < 0 || c.trace_kernel > 3 || c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
         return fail(nullptr, EPROP_EINVAL, "trace_kernel must be 0..3 and blocks_per_sm 0..64");
+    if (c.trace_kernel == 3 && !(c.continuous || c.update_interval > 0))
+        return fail(nullptr, EPROP_EINVAL,
+                    "trace_kernel 3 (dense window pass) advances carried state: it needs continuous or update_interval > 0");
     if ((c.trace_kernel == 1 || c.trace_kernel == 3) && c.batch > 1)
         return fail(nullptr, EPROP_EINVAL, "the window trace kernels need batch = 1");
     if (c.trace_kernel == 2 && (c.continuous || c.update_interval > 0))

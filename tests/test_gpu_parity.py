@@ -319,6 +319,15 @@ def test_sparse_replica_single_window_window_kernel():
 STATE_KERNELS = [pytest.param(1, id="lazy"), pytest.param(3, id="dense")]
 
 
+def test_dense_form_needs_carried_state():
+    # the dense window pass advances state carried across windows; a network
+    # that carries none is rejected at creation
+    import paper_2511_21674_gb300 as ep
+    W = _replica(False, 100)
+    with pytest.raises(ep.EpropError, match="trace_kernel 3"):
+        _gpu_net(W, trace_kernel=3)
+
+
 @pytest.mark.parametrize("tk", STATE_KERNELS)
 def test_million_replica_continuous_windows(tk):
     # continuous dynamics, update window of 100 steps, three calls of 200
