@@ -149,17 +149,19 @@ typedef struct eprop_config {
                                  update window per call (continuous = 0,
                                  update_interval = 0), n_out <= 256 and no
                                  predictor; results are bit-identical to 0/1 */
-    int32_t trace_kernel;     /* synapse-trace kernel: 0 auto (2 for batch >
-                                 1, else 3 when state is carried, else 1);
+    int32_t trace_kernel;     /* synapse-trace kernel: 0 auto (3 when state is
+                                 carried, else 2 for batch > 1, else 1);
                                  1 lazy window work queue (batch 1): only
                                  synapses with an arrival are touched, a
                                  skipped window is caught up at the next
                                  arrival; 2 batched single window (no state
                                  carried between windows); 3 dense window
-                                 pass (batch 1, carried state: continuous or
+                                 pass (carried state: continuous or
                                  update_interval > 0, else EPROP_EINVAL):
                                  every synapse is advanced at every window
-                                 end                                         */
+                                 end; with batch > 1 every synapse carries
+                                 one trace per sample and the weight steps
+                                 with the batch mean                         */
     int32_t blocks_per_sm;    /* CTAs per SM of the row kernels; 0 = 2        */
     int32_t profile;          /* 1: time the synapse-trace kernels of every
                                  window with CUDA events (see eprop_stats)    */
@@ -210,9 +212,11 @@ typedef struct eprop_synapses {
  *             (readout work, see above), freed by eprop_destroy
  * Errors: EPROP_EINVAL (inconsistent sizes, delays out of range, unsupported
  * combination), EPROP_ENOMEM, EPROP_ECUDA.  On error *out is NULL.
- * Unsupported: batch > 1 together with continuous = 1 or update_interval > 0
- * (a shared weight updated inside a call would need every sample's pending
- * trace at each transmission).
+ * Batches: batch > 1 needs continuous = 0 (every sample starts each call
+ * from zero state); update windows inside a call (update_interval > 0) run
+ * with batch <= 64 in the dense form (one trace per sample and synapse, the
+ * shared weight steps with the batch mean at every window end, Eq.
+ * accumulated-gradients); the lazy form (trace_kernel 1) needs batch 1.
  */
 eprop_status eprop_create_network(const eprop_config *cfg, const eprop_synapses *syn,
                                   const float *w_out, const uint8_t *out_mask,

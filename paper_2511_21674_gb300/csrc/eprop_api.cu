@@ -164,7 +164,7 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     if (c.trace_kernel == 1) net->trace_mode = 0;
     else if (c.trace_kernel == 2) net->trace_mode = 1;
     else if (c.trace_kernel == 3) net->trace_mode = 2;
-    else net->trace_mode = B > 1 ? 1 : (n.has_state ? 2 : 0);
+    else net->trace_mode = n.has_state ? 2 : (B > 1 ? 1 : 0);
     (void)qp_bytes;
     n.dense = net->trace_mode == 2 ? 1 : 0;
     n.RS = net->trace_mode != 1 ? U + D + 1 : 2;
@@ -200,7 +200,7 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     WA(Ebar_win, float, B * U * K);
     WA(qp, float, B * (long long)U * N * net->qp_stride);
     WA(win_off, long long, U + D + 2 + eprop::kWorkCounters);
-    if (n.has_state) WA(coef, float, (long long)n.RC * N * (c.neuron_model == 1 ? 8 : 4));
+    if (n.has_state) WA(coef, float, B * n.RC * N * (c.neuron_model == 1 ? 8 : 4));   // [B][N][RC]
 #undef WA
     net->U_alloc = U;
     net->T_alloc = T;
@@ -223,8 +223,10 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     if (c.neuron_model < 0 || c.neuron_model > 1 || c.loss < 0 || c.loss > 2 || c.feedback < 0 ||
         c.feedback > 1 || c.trace_dtype < 0 || c.trace_dtype > 2 || c.t_ref < 0 || c.update_interval < 0)
         return fail(nullptr, EPROP_EINVAL, "invalid enum or negative parameter");
-    if (c.batch > 1 && (c.continuous || c.update_interval > 0))
-        return fail(nullptr, EPROP_EINVAL, "batch > 1 needs continuous = 0 and update_interval = 0");
+    if (c.batch > 1 && c.continuous)
+        return fail(nullptr, EPROP_EINVAL, "batch > 1 needs continuous = 0 (every sample starts from zero state)");
+    if (c.batch > eprop::kBatchWindowMax && c.update_interval > 0)
+        return fail(nullptr, EPROP_EINVAL, "update windows inside a call need batch <= 64");
     if (c.launch_mode < 0 || c.launch_mode > 2)
         return fail(nullptr, EPROP_EINVAL, "launch_mode must be 0, 1 or 2");
     if (c.launch_mode == 2 && (c.continuous || c.update_interval > 0 || c.n_out > 256))
@@ -235,8 +237,8 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     if (c.trace_kernel == 3 && !(c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL,
                     "trace_kernel 3 (dense window pass) advances carried state: it needs continuous or update_interval > 0");
-    if ((c.trace_kernel == 1 || c.trace_kernel == 3) && c.batch > 1)
-        return fail(nullptr, EPROP_EINVAL, "the window trace kernels need batch = 1");
+    if (c.trace_kernel == 1 && c.batch > 1)
+        return fail(nullptr, EPROP_EINVAL, "the lazy trace form (trace_kernel 1) needs batch = 1");
     if (c.trace_kernel == 2 && (c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL, "the batched trace kernel cannot carry state between windows");
     if (c.surrogate < 0 || c.surrogate > 1 || c.reset_mode < 0 || c.reset_mode > 1 || c.sign_mask < 0 ||
@@ -381,9 +383,9 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             if (hflag & 1u) { s = fail(nullptr, EPROP_EINVAL, "synapse target out of [0, n_rec)"); goto fail_out; }
             if (hflag & 2u) { s = fail(nullptr, EPROP_EINVAL, "synapse delay out of [1, max_delay]"); goto fail_out; }
         }
-        if (n.has_state) {
-            FA(ebar, uint16_t, (nnz + 16) * (n.trace_bf16 ? 1 : 2));
-            if (n.alif) FA(epsa, uint16_t, (nnz + 16) * (n.trace_bf16 ? 1 : 2));
+        if (n.has_state) {              // one trace per sample and synapse ([B][nnz])
+            FA(ebar, uint16_t, (B * nnz + 16) * (n.trace_bf16 ? 1 : 2));
+            if (n.alif) FA(epsa, uint16_t, (B * nnz + 16) * (n.trace_bf16 ? 1 : 2));
         }
         if (n.record_grad) FA(grad, float, nnz);
         // neurons
@@ -602,8 +604,8 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         eprop::launch_fill_int(n.anchor_t, B * S, eprop::kNoSpike, st);
         if (n.has_state) {
             const size_t tb = n.trace_bf16 ? 2 : 4;
-            cudaMemsetAsync(n.ebar, 0, n.nnz * tb, st);
-            if (n.alif) cudaMemsetAsync(n.epsa, 0, n.nnz * tb, st);
+            cudaMemsetAsync(n.ebar, 0, B * n.nnz * tb, st);
+            if (n.alif) cudaMemsetAsync(n.epsa, 0, B * n.nnz * tb, st);
         }
     }
     if (n.record_raster) cudaMemsetAsync(n.rec_raster, 0, B * ((T + 31) / 32) * N * 4, st);
@@ -704,6 +706,9 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             if (c.profile) cudaEventRecordWithFlags(net->ev[2 * nwin], st, cudaEventRecordExternal);
             if (net->trace_mode == 1) {
                 eprop::launch_trace_batched(n, net->sm_count, st);
+                LT += 1;
+            } else if (net->trace_mode == 2 && B > 1) {
+                eprop::launch_window_batched(n, i, net->sm_count, st);
                 LT += 1;
             } else if (net->trace_mode == 2) {
                 eprop::launch_window_pass(n, i, pass_rows, idle_rows, st);

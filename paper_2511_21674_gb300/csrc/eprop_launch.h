@@ -19,6 +19,10 @@ void launch_end_call(const Net &n, int T, cudaStream_t st);
 void launch_filter_error(const Net &n, int i_end, cudaStream_t st);
 int launch_tables(const Net &n, int i_end, cudaStream_t st);
 void launch_trace_window(const Net &n, int i_end, int grid_x, cudaStream_t st);
+// dense window update of a batch (batch > 1 with update windows), one
+// state per sample and synapse
+constexpr int kBatchWindowMax = 64;
+void launch_window_batched(const Net &n, int i_end, int sm_count, cudaStream_t st);
 void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st);
 void launch_window_pass(const Net &n, int i_end, int grid_x, int grid_idle, cudaStream_t st);
 void launch_pred_input(const Net &n, int i, cudaStream_t st);

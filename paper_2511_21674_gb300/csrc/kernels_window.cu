@@ -228,16 +228,17 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
         }
     }
     if (!act) return;
-    // window coefficients: c = (mz, ma, me), Phi rows (ez, ea, .) and (az, aa, .)
+    // window coefficients: c = (mz, ma, me), Phi rows (ez, ea, .) and (az, aa, .);
+    // one set per sample ([B][N][RC])
     if (n.has_state) {
         const int slot = (a0 / U) & (n.RC - 1);
+        const long long cj = ((long long)b * N + j) * n.RC + slot;
         if (ALIF) {
-            float4 *c = reinterpret_cast<float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
+            float4 *c = reinterpret_cast<float4 *>(n.coef) + cj * 2;
             c[0] = make_float4((float)mz, (float)ma, (float)me, (float)az);
             c[1] = make_float4((float)aa, (float)ez, (float)ea, 0.f);
         } else {
-            reinterpret_cast<float4 *>(n.coef)[(long long)j * n.RC + slot] =
-                make_float4((float)mz, (float)me, (float)ez, 0.f);
+            reinterpret_cast<float4 *>(n.coef)[cj] = make_float4((float)mz, (float)me, (float)ez, 0.f);
         }
     }
     n.psi_hist[(long long)b * (U + 1) * N + j] = psi_b;     // slot 0 of the next window
@@ -1019,6 +1020,134 @@ __global__ void __launch_bounds__(256) trace_batched_kernel(Net n) {
     }
 }
 
+// Dense window update of a mini-batch (batch > 1 with update windows inside
+// a call; Eq. accumulated-gradients, Eq. gradient-descent).  Every synapse
+// carries one state per sample (ebar, eps_a of sample b at b * nnz + q).
+// At a window end each sample's state passes through that sample's window
+// coefficients and arrival tables -- the arithmetic of the single-sample
+// window pass -- and the weight takes one step with the sum over samples
+// (the batch mean).  One warp per source row: the lanes first form each
+// (sample, delay)'s presynaptic trace at the window start and gather the
+// row's spikes of the window per sample (grouped by sample, ascending),
+// then walk the row's synapses.
+template <bool ALIF, int TB, bool GEN>
+__global__ void __launch_bounds__(256) window_batched_kernel(Net n, int i_end) {
+    constexpr int kCap = 256;                    // spikes of one row (all samples) cached per warp
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ float zb[8][kBatchWindowMax][kMaxDelay + 1];
+    __shared__ int sp[8][kCap];
+    __shared__ int soff[8][kBatchWindowMax + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp, nw = gridDim.x * (blockDim.x >> 5);
+    const int U = n.U, N = n.n_rec, B = n.B, D = n.D;
+    const int r_end = run_step_w(n, i_end);
+    const int a0 = r_end - U;
+    const int s_lo = max(a0 + 1 - D, 1), s_hi = r_end - 1;
+    const float step = n.lr * n.inv_B;
+    const long long nnz = n.nnz;
+    const long long cstride = (long long)N * n.RC;
+    for (int src = gw; src < n.n_src; src += nw) {
+        const long long q0 = n.row_ptr[src], q1 = n.row_ptr[src + 1];
+        if (q1 == q0) continue;
+        for (int e = lane; e < B * D; e += 32) {
+            const int b = e / D, d = e % D + 1;
+            const long long sb = (long long)b * n.n_src + src;
+            zb[warp][b][d] = row_info(n, src_words_c(n, b, src), n.anchor_t[sb], n.anchor_z[sb], a0, d, false).zbar_a0;
+        }
+        // lane l owns samples l and l + 32: counts, then offsets in sample order
+        int cnt[2] = {0, 0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int b = lane + 32 * h;
+            if (b < B && s_lo <= s_hi) for_each_spike(src_words_c(n, b, src), n.RW, s_lo, s_hi, [&](int) { ++cnt[h]; });
+        }
+        int base = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int v = cnt[h];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, v, o);
+                if (lane >= o) v += t;
+            }
+            const int b = lane + 32 * h;
+            if (b < B) soff[warp][b] = base + v - cnt[h];
+            base += __shfl_sync(kFull, v, 31);
+        }
+        if (lane == 0) soff[warp][B] = base;
+        __syncwarp();
+        const int total = base;
+        if (total <= kCap) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int b = lane + 32 * h;
+                if (b < B && s_lo <= s_hi) {
+                    int pos = soff[warp][b];
+                    for_each_spike(src_words_c(n, b, src), n.RW, s_lo, s_hi, [&](int st) { sp[warp][pos++] = st; });
+                }
+            }
+        }
+        __syncwarp();
+        for (long long q = q0 + lane; q < q1; q += 32) {
+            const uint32_t td = n.tgt_d[q];
+            const int j = (int)(td & 0xFFFFFFu);
+            const int dl = (int)(td >> 24);
+            // the sum over samples is reduced in FP64
+            double Gt = 0.0;
+            for (int b = 0; b < B; ++b) {
+                const long long qb = (long long)b * nnz + q;
+                float ebar = load_trace(n.ebar, qb, TB);
+                float epsa = ALIF ? load_trace(n.epsa, qb, TB) : 0.f;
+                float zbar = zb[warp][b][dl];
+                Coef cf;
+                if (ALIF) {
+                    const float4 *p = reinterpret_cast<const float4 *>(n.coef) + ((long long)b * cstride + j) * 2;
+                    cf.c0 = __ldg(p);
+                    cf.c1 = __ldg(p + 1);
+                } else {
+                    cf.c0 = __ldg(reinterpret_cast<const float4 *>(n.coef) + (long long)b * cstride + j);
+                    cf.c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                float G = 0.f;
+                apply_coef<ALIF>(n, cf, zbar, epsa, ebar, G);
+                const long long qa = ((long long)b * U - a0 - 1) * N;   // table index qa + a * N + j
+                if (total <= kCap) {
+                    for (int c = soff[warp][b]; c < soff[warp][b + 1]; ++c) {
+                        const int a = sp[warp][c] + dl;
+                        if (a <= a0) continue;
+                        if (a > r_end) break;
+                        if (ALIF) {
+                            const float4 t = __ldg(reinterpret_cast<const float4 *>(n.qp) + qa + (long long)a * N + j);
+                            G += t.x; ebar += t.y; epsa += t.z;
+                        } else {
+                            const float2 t = __ldg(reinterpret_cast<const float2 *>(n.qp) + qa + (long long)a * N + j);
+                            G += t.x; ebar += t.y;
+                        }
+                    }
+                } else {            // rows with more spikes than the cache holds
+                    G += scan_arrivals<ALIF>(n, src_words_c(n, b, src), max(a0 + 1 - dl, 1), r_end - dl, dl,
+                                             qa + j, ebar, epsa);
+                }
+                store_trace(n.ebar, qb, ebar, TB);
+                if (ALIF) store_trace(n.epsa, qb, epsa, TB);
+                Gt += (double)G;
+            }
+            const float Gf = (float)Gt;
+            if (Gf != 0.f) {
+                const float w = n.w[q];
+                if (GEN) {
+                    const float wn = window_update(n, q, w, Gf);
+                    if (!n.adam) n.w[q] = wn;
+                } else {
+                    n.w[q] = w - step * Gf;
+                }
+            }
+            if (n.record_grad) n.grad[q] += n.inv_B * Gf;
+        }
+        __syncwarp();
+    }
+}
+
 // readout weights: g_kj = sum_b [zk_j^{a0} C_k + sum_{spikes s in window} Ebar_k(s)]
 // (Eq. eprop-output-new-subs-rewritten), one thread per (j, k).
 __global__ void readout_weights_kernel(Net n, int i_end) {
@@ -1385,6 +1514,26 @@ void launch_window_pass(const Net &n, int i_end, int grid_x, int grid_idle, cuda
     }
 #undef EPROP_PASS_T
 #undef EPROP_PASS
+}
+
+void launch_window_batched(const Net &n, int i_end, int sm_count, cudaStream_t st) {
+    int blocks = (n.n_src + 7) / 8;
+    if (blocks > 8 * sm_count) blocks = 8 * sm_count;
+#define EPROP_WB(A, T)                                                                                   \
+    do {                                                                                                 \
+        if (n.adam || n.sign_mask) window_batched_kernel<A, T, true><<<blocks, 256, 0, st>>>(n, i_end);  \
+        else window_batched_kernel<A, T, false><<<blocks, 256, 0, st>>>(n, i_end);                       \
+    } while (0)
+#define EPROP_WB_T(A)                                  \
+    do {                                               \
+        if (n.trace_type == 1) EPROP_WB(A, 1);         \
+        else if (n.trace_type == 2) EPROP_WB(A, 2);    \
+        else EPROP_WB(A, 0);                           \
+    } while (0)
+    if (n.alif) EPROP_WB_T(true);
+    else EPROP_WB_T(false);
+#undef EPROP_WB_T
+#undef EPROP_WB
 }
 
 void launch_trace_batched(const Net &n, int sm_count, cudaStream_t st) {
