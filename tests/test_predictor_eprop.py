@@ -334,14 +334,28 @@ def test_predictor_at_scale_final_loss_against_plain_eprop():
     train = [C.event_classification(batch=64, sample_seed=30000 + k) for k in range(8)]
     held = [C.event_classification(batch=64, sample_seed=40000 + k) for k in range(2)]
     loss_plain, acc_plain, curve_plain = _train_eprop(Wt, None, 0.0, train, 6, held)
+    params0 = learner.read("params").copy()
     loss_pred, acc_pred, curve_pred = _train_eprop(Wt, learner, 0.1, train, 6, held)
+    # the same comparison with update windows of 50 steps inside each call
+    # (seven weight steps per call; plain e-prop steps only in windows that
+    # hold a target window, with the predictor in every window): reported
+    Ww = dict(Wt, spec=C.Spec(**{**Wt["spec"].__dict__, "update_interval": 50}))
+    loss_plain_w, acc_plain_w, _ = _train_eprop(Ww, None, 0.0, train, 6, held)
+    learner.close()
+    learner = ep.Predictor(K + 64, K, seed=11, max_rows=4096, params=params0)
+    learner.set_input_scale(scale)
+    learner.input_scale = scale
+    loss_pred_w, acc_pred_w, _ = _train_eprop(Ww, learner, 0.1, train, 6, held)
     learner.close()
     chance = 25 * math.log(K)
     report = dict(pairs=int(X.shape[0]), predictor_train_loss=[first, last],
                   inference_us_per_step_batch256=us, chance_loss=chance,
                   heldout_loss_plain=loss_plain, heldout_loss_with_predictor=loss_pred,
                   heldout_accuracy_plain=acc_plain, heldout_accuracy_with_predictor=acc_pred,
-                  train_loss_plain=curve_plain[::8], train_loss_with_predictor=curve_pred[::8])
+                  train_loss_plain=curve_plain[::8], train_loss_with_predictor=curve_pred[::8],
+                  windows50_heldout_loss_plain=loss_plain_w, windows50_heldout_loss_with_predictor=loss_pred_w,
+                  windows50_heldout_accuracy_plain=acc_plain_w,
+                  windows50_heldout_accuracy_with_predictor=acc_pred_w)
     PT.report(dict(predictor_scale=report))
     print("predictor at scale:", report)
     assert last < first
