@@ -79,7 +79,7 @@ class _Cfg(ctypes.Structure):
                 ("sign_mask", ctypes.c_int32), ("optimizer", ctypes.c_int32),
                 ("adam_b1", ctypes.c_double), ("adam_b2", ctypes.c_double),
                 ("adam_eps", ctypes.c_double), ("if_period", ctypes.c_int32),
-                ("if_seed", ctypes.c_uint64)]
+                ("if_seed", ctypes.c_uint64), ("d_out", ctypes.c_int32), ("d_ls", ctypes.c_int32)]
 
 
 class _State(ctypes.Structure):
@@ -90,7 +90,8 @@ class _State(ctypes.Structure):
             "ebar", "g", "y", "zk", "g_out", "grad_acc", "grad_out_acc",
             "counters", "g_abs", "g_out_abs", "grad_abs_acc", "grad_out_abs_acc",
             "y_abs", "g_lsens", "g_out_lsens", "grad_lsens_acc", "grad_out_lsens_acc",
-            "rate", "ebar_reg", "w_neg", "w_out_neg", "adam_m", "adam_v", "adam_m_out", "adam_v_out")]
+            "rate", "ebar_reg", "w_neg", "w_out_neg", "adam_m", "adam_v", "adam_m_out", "adam_v_out",
+            "z_hist", "ebar_hist", "L_hist", "Ls_hist")]
 
 
 def _load():
@@ -342,6 +343,12 @@ class Oracle:
                                               dtype=np.uint8)
         self.adam_m, self.adam_v = z(self.nnz), z(self.nnz)
         self.adam_m_out, self.adam_v_out = z((N, K)), z((N, K))
+        # generalized delays: rings of the last d_out + 1 spike vectors, the
+        # last d_out + d_ls + 1 traces of every synapse and d_ls + 1 signals
+        d_out, d_ls = int(getattr(spec, "d_out", 0)), int(getattr(spec, "d_ls", 0))
+        self.z_hist = z((B, d_out + 1, N), np.uint8)
+        self.ebar_hist = z((B, self.nnz, d_out + d_ls + 1))
+        self.L_hist, self.Ls_hist = z((B, d_ls + 1, N)), z((B, d_ls + 1, N))
 
     def _cfg(self, T):
         s = self.spec
@@ -359,7 +366,7 @@ class Oracle:
                     c_reg=p["c_reg"], f_target=p["f_target"], beta_reg=p["beta_reg"],
                     sign_mask=s.sign_mask, optimizer=s.optimizer, adam_b1=p["adam_b1"],
                     adam_b2=p["adam_b2"], adam_eps=p["adam_eps"], if_period=s.if_period,
-                    if_seed=s.if_seed)
+                    if_seed=s.if_seed, d_out=int(getattr(s, "d_out", 0)), d_ls=int(getattr(s, "d_ls", 0)))
 
     def _state(self):
         st = _State(n_src=self.n_src, nnz=self.nnz)
@@ -369,7 +376,7 @@ class Oracle:
                      "grad_out_acc", "counters", "g_abs", "g_out_abs", "grad_abs_acc",
                      "grad_out_abs_acc", "y_abs", "g_lsens", "g_out_lsens", "grad_lsens_acc",
                      "grad_out_lsens_acc", "rate", "ebar_reg", "w_neg", "w_out_neg", "adam_m",
-                     "adam_v", "adam_m_out", "adam_v_out"):
+                     "adam_v", "adam_m_out", "adam_v_out", "z_hist", "ebar_hist", "L_hist", "Ls_hist"):
             setattr(st, name, _p(getattr(self, name)))
         st.fb = _p(self.fb)
         return st

@@ -76,6 +76,14 @@
  *     (t_abs + phase_j) mod period == 0, whatever the membrane does; v and psi
  *     are still integrated; phase_j = (upper 32 bits of mix(if_seed ^ j))
  *     mod period.
+ *   - generalized delays (Supplement, "Generalized delays"): the readout
+ *     receives the recurrent spikes d_out steps late (Eq. leaky_integrator_
+ *     with_delay), so the output gradient filters z^{t-d_out}; the learning
+ *     signal of step tau reaches the recurrent layer at tau + d_ls and is
+ *     paired there with the filtered eligibility trace of step tau - d_out
+ *     (Eq. eprop-learning-signal-delay); signals that would arrive after a
+ *     sample's end are dropped.  Rings of the recent spikes, traces and
+ *     signals (indexed by the absolute step) hold what the pairing needs.
  *
  * E_override (optional, [B][T][K]): where window = 0, E^t is taken from it
  * instead of from the loss (the learned predictor's error estimate).
@@ -128,6 +136,7 @@ typedef struct {
     double adam_b1, adam_b2, adam_eps;
     int32_t if_period;            /* ignore-and-fire period in steps, 0: off */
     uint64_t if_seed;
+    int32_t d_out, d_ls;          /* generalized delays (see the header comment) */
 } oracle_cfg;
 
 typedef struct {
@@ -163,6 +172,10 @@ typedef struct {
     const uint8_t *w_neg, *w_out_neg; /* [nnz], [N][K] 1 where the initial weight is negative */
     double *adam_m, *adam_v;      /* [nnz] */
     double *adam_m_out, *adam_v_out; /* [N][K] */
+    /* generalized delays: rings indexed by the absolute step */
+    uint8_t *z_hist;              /* [B][d_out+1][N] recurrent spikes */
+    double *ebar_hist;            /* [B][nnz][d_out+d_ls+1] filtered eligibility traces */
+    double *L_hist, *Ls_hist;     /* [B][d_ls+1][N] learning signals and their sensitivities */
 } oracle_state;
 
 /* SplitMix64 output function (Steele, Lea & Flood 2014). */
@@ -302,6 +315,10 @@ static void reset_state(const oracle_cfg *c, oracle_state *s) {
     memset(s->zk, 0, sizeof(double) * B * N);
     memset(s->rate, 0, sizeof(double) * B * N);
     memset(s->ebar_reg, 0, sizeof(double) * B * s->nnz);
+    memset(s->z_hist, 0, (size_t)B * (c->d_out + 1) * N);
+    memset(s->ebar_hist, 0, sizeof(double) * B * s->nnz * (c->d_out + c->d_ls + 1));
+    memset(s->L_hist, 0, sizeof(double) * B * (c->d_ls + 1) * N);
+    memset(s->Ls_hist, 0, sizeof(double) * B * (c->d_ls + 1) * N);
     s->counters[1] = 0;
 }
 
@@ -386,13 +403,17 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 rate[j] = c->beta_reg * rate[j] + (1.0 - c->beta_reg) * z[j];
             }
 
-            /* readout, error signal, loss */
+            /* readout, error signal, loss; the readout sees the recurrent
+               spikes d_out steps late (Eq. leaky_integrator_with_delay) */
+            uint8_t *zh = s->z_hist + b * (c->d_out + 1) * N;
+            memcpy(zh + (t_abs % (c->d_out + 1)) * N, z, N);
+            const uint8_t *zd = (t_abs - c->d_out >= 1) ? zh + ((t_abs - c->d_out) % (c->d_out + 1)) * N : NULL;
             const double win = window ? (double)window[bt] : 1.0;
             const double *tgt = targets + bt * K;
             for (int64_t k = 0; k < K; ++k) {
                 double acc = 0.0, acc_abs = 0.0;
                 for (int64_t j = 0; j < N; ++j)
-                    if (z[j]) {
+                    if (zd && zd[j]) {
                         acc += s->w_out[j * K + k];
                         acc_abs += fabs(s->w_out[j * K + k]);
                     }
@@ -461,6 +482,20 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                 Ls[j] = accs;
                 if (L_rec) L_rec[bt * N + j] = acc;
             }
+            /* generalized delays (Eq. eprop-learning-signal-delay): the
+               learning signal of step tau reaches the synapses at tau + d_ls
+               and is paired with their filtered eligibility of tau - d_out */
+            const int64_t RH = c->d_out + c->d_ls + 1;
+            const int delayed = c->d_out != 0 || c->d_ls != 0;
+            double *Lh = s->L_hist + b * (c->d_ls + 1) * N, *Lsh = s->Ls_hist + b * (c->d_ls + 1) * N;
+            if (delayed) {
+                memcpy(Lh + (t_abs % (c->d_ls + 1)) * N, L, sizeof(double) * N);
+                memcpy(Lsh + (t_abs % (c->d_ls + 1)) * N, Ls, sizeof(double) * N);
+            }
+            const int64_t t_sig = t_abs - c->d_ls;            /* step of the arriving learning signal */
+            const int64_t t_eli = t_sig - c->d_out;           /* step of the paired eligibility */
+            const double *Ld = t_sig >= 1 ? Lh + (t_sig % (c->d_ls + 1)) * N : NULL;
+            const double *Lsd = t_sig >= 1 ? Lsh + (t_sig % (c->d_ls + 1)) * N : NULL;
 
             /* eligibility traces and gradients, every synapse, every step;
                each synapse's state and sums are its own, so the sources may
@@ -475,8 +510,18 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     const double e = eligibility_e(c->alpha, c->rho, c->beta_a, c->kappa_e, psi_prev[j],
                                                    psi[j], arrive, s->zbar + b * NNZ + q,
                                                    s->epsa + b * NNZ + q, s->ebar + b * NNZ + q);
-                    double gt = L[j] * s->ebar[b * NNZ + q];
-                    double gabs = fabs(gt);
+                    double gt, gabs, lsens;
+                    if (!delayed) {
+                        gt = L[j] * s->ebar[b * NNZ + q];
+                        lsens = Ls[j] * fabs(s->ebar[b * NNZ + q]);
+                    } else {
+                        double *eh = s->ebar_hist + (b * NNZ + q) * RH;
+                        eh[t_abs % RH] = s->ebar[b * NNZ + q];
+                        const double ed = (Ld && t_eli >= 1) ? eh[t_eli % RH] : 0.0;
+                        gt = Ld ? Ld[j] * ed : 0.0;
+                        lsens = Lsd ? Lsd[j] * fabs(ed) : 0.0;
+                    }
+                    gabs = fabs(gt);
                     if (c->c_reg != 0.0) {        /* Eq. ema-gradient */
                         double *er = s->ebar_reg + b * NNZ + q;
                         *er = c->beta_reg * (*er) + e;
@@ -486,11 +531,11 @@ int oracle_simulate(const oracle_cfg *c, oracle_state *s, int32_t T,
                     }
                     s->g[q] += gt;
                     s->g_abs[q] += gabs;
-                    s->g_lsens[q] += Ls[j] * fabs(s->ebar[b * NNZ + q]);
+                    s->g_lsens[q] += lsens;
                 }
             }
             for (int64_t j = 0; j < N; ++j) {
-                zk[j] = c->kappa * zk[j] + z[j];
+                zk[j] = c->kappa * zk[j] + (zd ? zd[j] : 0);   /* F_kappa(z^{t-d_out}) */
                 for (int64_t k = 0; k < K; ++k)
                     if (s->out_mask[j * K + k]) {
                         s->g_out[j * K + k] += E[k] * zk[j];

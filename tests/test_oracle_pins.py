@@ -208,7 +208,12 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
     dly = torch.tensor(net["delay"].astype(np.int64))
     w = torch.tensor(net["w"].astype(np.float64), requires_grad=True)
     wo = torch.tensor(net["w_out"].astype(np.float64), requires_grad=True)
+    # generalized delays: the readout sees z^{t - d_out}; the recurrent and
+    # input weights learn from the loss terms whose learning signal arrives
+    # within the sample (t <= length - d_ls), the readout from all of them
+    d_out, d_ls = int(getattr(s, "d_out", 0)), int(getattr(s, "d_ls", 0))
     total = 0.0
+    total_rec = 0.0
     for b in range(B):
         v = torch.zeros(N, dtype=torch.float64)
         a = torch.zeros(N, dtype=torch.float64)
@@ -217,6 +222,7 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
         ref = np.zeros(N, dtype=np.int64)
         y = torch.zeros(K, dtype=torch.float64)
         hist = {}
+        zs = {}
         for t in range(1, int(lengths[b]) + 1):
             arrive = torch.zeros(len(src), dtype=torch.float64)
             for q in range(len(src)):
@@ -237,21 +243,33 @@ def _bptt(net, T, x_raster, targets, window, lengths, z_raster):
             ref[z_raster[b, t - 1] > 0] = s.t_ref
             hist[t] = torch.cat([torch.tensor(x_raster[b, t - 1].astype(np.float64)),
                                  z.detach()])
-            y = kappa * y + z @ wo
+            zs[t] = z
+            zd = zs[t - d_out] if t - d_out >= 1 else torch.zeros(N, dtype=torch.float64)
+            y = kappa * y + zd @ wo
             win = float(window[b, t - 1])
             tg = torch.tensor(targets[b, t - 1].astype(np.float64))
             if s.loss == 0:
-                total = total + 0.5 * win * ((y - tg) ** 2).sum()
+                term = 0.5 * win * ((y - tg) ** 2).sum()
             elif s.loss == 2:
-                total = total + win * ((y - tg) ** 2).sum() / K
+                term = win * ((y - tg) ** 2).sum() / K
             else:
-                total = total - win * (tg * torch.log_softmax(y, 0)).sum()
+                term = -win * (tg * torch.log_softmax(y, 0)).sum()
+            total = total + term
+            if t <= int(lengths[b]) - d_ls:
+                total_rec = total_rec + term
             if c_reg != 0.0:
                 f = beta_reg * f + (1.0 - beta_reg) * z
-                total = total + 0.5 * c_reg * ((f - f_target) ** 2).sum()
+                reg = 0.5 * c_reg * ((f - f_target) ** 2).sum()
+                total = total + reg
+                total_rec = total_rec + reg
             zprev = z
-    (total / B).backward()
-    return w.grad.numpy(), wo.grad.numpy()
+    if d_out == 0 and d_ls == 0:
+        (total / B).backward()
+        return w.grad.numpy(), wo.grad.numpy()
+    gw = torch.autograd.grad(total_rec / B, w, retain_graph=True, allow_unused=True)[0]
+    gwo = torch.autograd.grad(total / B, wo)[0]
+    gw = torch.zeros_like(w) if gw is None else gw
+    return gw.numpy(), gwo.numpy()
 
 
 def _random_small(model, loss, seed, B=2, T=40, n_in=3, N=6, K=2, max_delay=3):
@@ -311,6 +329,33 @@ def test_eprop_equals_bptt_with_stop_gradients(model, loss, variant):
     scale = np.abs(gw).max()
     np.testing.assert_allclose(g, gw, rtol=1e-9, atol=1e-12 * scale)
     np.testing.assert_allclose(go, gwo, rtol=1e-9, atol=1e-12 * np.abs(gwo).max())
+
+
+@pytest.mark.parametrize("d_out,d_ls", [(1, 0), (0, 2), (2, 3)])
+@pytest.mark.parametrize("model,loss", [(0, 0), (1, 1)])
+def test_generalized_delays_equal_bptt(model, loss, d_out, d_ls):
+    # Supplement "Generalized delays": the readout sees the recurrent spikes
+    # d_out steps late and the learning signal reaches the recurrent layer
+    # d_ls steps late; e-prop pairs L^tau with the eligibility of tau - d_out
+    # and drops the signals that arrive after the sample's end
+    net, x, tg, window, lengths = _random_small(model, loss, seed=30 + 2 * model + loss + d_out)
+    s = net["spec"]
+    s.d_out, s.d_ls = d_out, d_ls
+    o = oracle.Oracle(s, net["ptr"], net["col"], net["w"], net["delay"], net["w_out"],
+                      net["out_mask"])
+    x_ptr, x_ids = raster_to_lists(x)
+    r = o.simulate(s.T, x_ptr, x_ids, tg, window, lengths)
+    assert r["raster"].sum() > 5, "test network must spike"
+    g, go = o.take_grads()
+    gw, gwo = _bptt(net, s.T, x, tg, window, lengths, r["raster"])
+    scale = np.abs(gw).max()
+    assert scale > 0
+    np.testing.assert_allclose(g, gw, rtol=1e-9, atol=1e-12 * scale)
+    np.testing.assert_allclose(go, gwo, rtol=1e-9, atol=1e-12 * np.abs(gwo).max())
+    # the delays change the gradient (the pin is not the undelayed one)
+    s.d_out, s.d_ls = 0, 0
+    g0, _ = _bptt(net, s.T, x, tg, window, lengths, r["raster"])
+    assert np.abs(g0 - gw).max() > 1e-6 * scale
 
 
 # ---------------------------------------------------------------------------

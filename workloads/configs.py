@@ -99,6 +99,10 @@ class Spec:
     adam_eps: float = 1e-7         # TensorFlow's constant eps_hat
     if_period: int = 0             # ignore-and-fire period in steps (0: off)
     if_seed: int = 0
+    # generalized delays (Supplement "Generalized delays"): recurrent to
+    # readout (d_out) and learning signal back to the recurrent layer (d_ls)
+    d_out: int = 0
+    d_ls: int = 0
 
     @property
     def alpha(self) -> float:
