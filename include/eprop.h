@@ -182,6 +182,15 @@ typedef struct eprop_config {
     float adam_b1, adam_b2, adam_eps;
     int32_t if_period;        /* ignore-and-fire period in steps, 0 = off      */
     uint64_t if_seed;
+    /* generalized delays (Supplement "Generalized delays"), in steps 0..64:
+       the readout receives the recurrent spikes d_out steps late (Eq.
+       leaky_integrator_with_delay), and the learning signal of step tau
+       reaches the recurrent layer at tau + d_ls, paired with the filtered
+       eligibility trace of tau - d_out (Eq. eprop-learning-signal-delay);
+       signals arriving after a sample's end are dropped.  Nonzero values
+       need one update window per call (update_interval = 0, continuous =
+       0) and launch_mode 0 or 1.                                          */
+    int32_t d_out, d_ls;
 } eprop_config;
 
 /*

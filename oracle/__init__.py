@@ -264,9 +264,17 @@ def arrival_magnitude(spec, ptr, col, delay, x_ptr, x_ids, lengths, raster, psi,
     ptr = np.asarray(ptr, dtype=np.int64)
     col = np.asarray(col, dtype=np.int64)
     delay = np.asarray(delay, dtype=np.int64)
+    d_out, d_ls = int(getattr(spec, "d_out", 0)), int(getattr(spec, "d_ls", 0))
     for b in range(B):
-        Qa = np.abs(arrival_contrib(spec, psi[b], L[b]))
         ln = int(lengths[b])
+        Lb = L[b]
+        if d_out or d_ls:
+            # generalized delays: step t pairs with the learning signal of
+            # t + d_out, delivered only when formed by the sample's end - d_ls
+            Lb = np.zeros_like(L[b])
+            m = max(0, min(T - d_out, ln - d_ls - d_out))
+            Lb[:m] = L[b][d_out:d_out + m]
+        Qa = np.abs(arrival_contrib(spec, psi[b], Lb))
         src = np.zeros((ln, n_in + N), dtype=bool)
         for t in range(ln):
             src[t, x_ids[x_ptr[b * T + t]:x_ptr[b * T + t + 1]]] = True

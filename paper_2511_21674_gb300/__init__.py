@@ -52,7 +52,8 @@ class Config(ctypes.Structure):
         ("c_reg", ctypes.c_float), ("f_target", ctypes.c_float), ("beta_reg", ctypes.c_float),
         ("sign_mask", ctypes.c_int32), ("optimizer", ctypes.c_int32),
         ("adam_b1", ctypes.c_float), ("adam_b2", ctypes.c_float), ("adam_eps", ctypes.c_float),
-        ("if_period", ctypes.c_int32), ("if_seed", ctypes.c_uint64)]
+        ("if_period", ctypes.c_int32), ("if_seed", ctypes.c_uint64),
+        ("d_out", ctypes.c_int32), ("d_ls", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -190,6 +191,7 @@ def make_config(spec, launch_mode: int = 1, trace_dtype: int = 0, record_grad: i
     c.sign_mask, c.optimizer = spec.sign_mask, spec.optimizer
     c.adam_b1, c.adam_b2, c.adam_eps = spec.adam_b1, spec.adam_b2, spec.adam_eps
     c.if_period, c.if_seed = spec.if_period, spec.if_seed
+    c.d_out, c.d_ls = int(getattr(spec, "d_out", 0)), int(getattr(spec, "d_ls", 0))
     return c
 
 

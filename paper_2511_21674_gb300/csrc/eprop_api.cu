@@ -167,7 +167,8 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     else net->trace_mode = n.has_state ? 2 : (B > 1 ? 1 : 0);
     (void)qp_bytes;
     n.dense = net->trace_mode == 2 ? 1 : 0;
-    n.RS = net->trace_mode != 1 ? U + D + 1 : 2;
+    // the readout reads the spike list of the step d_out back
+    n.RS = std::max(net->trace_mode != 1 ? U + D + 1 : 2, c.d_out + 2);
     n.RC = 0;
     if (n.has_state && n.dense) {
         n.RC = 1;                       // only the current window's coefficients
@@ -227,6 +228,12 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
         return fail(nullptr, EPROP_EINVAL, "batch > 1 needs continuous = 0 (every sample starts from zero state)");
     if (c.batch > eprop::kBatchWindowMax && c.update_interval > 0)
         return fail(nullptr, EPROP_EINVAL, "update windows inside a call need batch <= 64");
+    if (c.d_out < 0 || c.d_out > 64 || c.d_ls < 0 || c.d_ls > 64)
+        return fail(nullptr, EPROP_EINVAL, "d_out and d_ls must be 0..64");
+    if ((c.d_out || c.d_ls) && (c.update_interval > 0 || c.continuous || c.launch_mode == 2))
+        return fail(nullptr, EPROP_EINVAL,
+                    "generalized delays need one update window per call (update_interval = 0, continuous = 0) "
+                    "and launch_mode 0 or 1");
     if (c.launch_mode < 0 || c.launch_mode > 2)
         return fail(nullptr, EPROP_EINVAL, "launch_mode must be 0, 1 or 2");
     if (c.launch_mode == 2 && (c.continuous || c.update_interval > 0 || c.n_out > 256))
@@ -295,6 +302,8 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     n.D = c.max_delay; n.nnz = nnz;
     n.alif = c.neuron_model == 1; n.t_ref = c.t_ref; n.loss = c.loss; n.feedback = c.feedback;
     n.has_state = (c.continuous || c.update_interval > 0) ? 1 : 0;
+    n.d_out = c.d_out;
+    n.d_ls = c.d_ls;
     n.trace_bf16 = c.trace_dtype != 0; n.trace_type = c.trace_dtype; n.record_grad = c.record_grad != 0;
     n.record_raster = c.record_raster != 0; n.record_psi = c.record_psi != 0; n.n_thr = c.drive_weight != 0.f ? c.n_drive_thr : 0;
     const double alpha = std::exp(-(double)c.dt / c.tau_m);
@@ -651,7 +660,8 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
     // ring is not longer than the update window (batched form, RS = 2).
     // Otherwise a readout trails the neuron updates by fewer than U steps
     // (the joins at window ends), and the ring's RS > U slots keep its
-    // step's list until it has run.
+    // step's list until it has run (with a readout delay d_out it reads the
+    // list of the step d_out back, and RS >= d_out + 2 keeps that one too).
     // (the persistent step loop does the readout itself: one stream)
     const bool fork = n.pred_mode == 0 && n.RS > n.U && c.launch_mode != 2;
     cudaStream_t sr = fork ? net->st2 : st;

@@ -143,6 +143,7 @@ struct Net {
     float *adam_m, *adam_v, *adam_m_out, *adam_v_out;
     int if_period;            // ignore-and-fire period (0: off)
     unsigned long long if_seed;
+    int d_out, d_ls;          // generalized delays: readout input, learning signal
 };
 
 // ----------------------------------------------------------------- helpers

@@ -310,8 +310,10 @@ __global__ void readout_accum_kernel(Net n, int i, int chunk) {
         if (blockIdx.x == 0) readout_finish(n, i, b);
         return;
     }
-    const int r = run_step(n, i);
-    const long long li = list_index(n, b, r % n.RS);
+    // the readout receives the recurrent spikes d_out steps late (Eq.
+    // leaky_integrator_with_delay): the spike list of run step r - d_out
+    const int rs = run_step(n, i) - n.d_out;
+    const long long li = list_index(n, b, (rs >= 1 ? rs : 1) % n.RS);
     const int *cnt = n.list_cnt + li;
     const int *ids = n.list_ids + li * n.list_cap;
     if (threadIdx.x < 32) {
@@ -319,7 +321,7 @@ __global__ void readout_accum_kernel(Net n, int i, int chunk) {
         incl[threadIdx.x] = bs.incl;
     }
     __syncthreads();
-    const int total = incl[kBkt - 1];
+    const int total = rs >= 1 ? incl[kBkt - 1] : 0;
     for (int c0 = blockIdx.x * chunk; c0 < total; c0 += gridDim.x * chunk) {
         const int c1 = min(c0 + chunk, total);
         // every entry of the chunk resolved in parallel: bucket = first

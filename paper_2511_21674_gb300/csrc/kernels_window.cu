@@ -134,6 +134,10 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
     R mb = 0;                                  // adjoint of F_beta(e) (regularisation)
     const R breg = (R)n.beta_reg;
     const float psi_b = act ? psi_g[(long long)U * N] : 0.f;
+    // generalized delays (one window per call): step u pairs with the
+    // learning signal of u + d_out, which reaches the neuron only if it was
+    // formed d_ls or more steps before the sample's end
+    const int l_lim = (n.d_out | n.d_ls) ? min(U, n.lengths[b] - n.d_ls - a0) : U;
     const long long qbase = ((long long)b * U) * N + j;
     // Steps are taken backwards in chunks of kTC: the chunk's psi and
     // learning signals are loaded in one batch, then the recursion runs over
@@ -145,7 +149,8 @@ __global__ void __launch_bounds__(128, 4) tables_kernel(Net n, int i_end) {
         for (int c = 0; c < kTC; ++c) {
             const int u = u1 - c;
             const bool in = act && u >= u0;
-            Lc[c] = in ? L_g[(long long)(u - 1) * N] : 0.f;
+            const int ul = u + n.d_out;
+            Lc[c] = (in && ul <= l_lim) ? L_g[(long long)(ul - 1) * N] : 0.f;
             Pc[c] = in ? psi_g[(long long)u * N] : 0.f;
         }
         float Rc[REG ? kTC : 1];
@@ -1210,8 +1215,11 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
                         while (m) {
                             const int st = sb + __ffs(m) - 1;
                             m &= m - 1;
-                            if (has_k) {
-                                const float4 e = *reinterpret_cast<const float4 *>(Eb + (long long)(st - a0 - 1) * K);
+                            // the spike reaches the readout d_out steps later
+                            // (Eq. eprop-output-new-subs-rewritten with delay)
+                            if (has_k && st + n.d_out <= r_end) {
+                                const float4 e =
+                                    *reinterpret_cast<const float4 *>(Eb + (long long)(st + n.d_out - a0 - 1) * K);
                                 gb.x += e.x; gb.y += e.y; gb.z += e.z; gb.w += e.w;
                             }
                             zn += exp2f(n.log2_kappa * (float)(r_end - st));
@@ -1261,7 +1269,7 @@ __global__ void readout_weights_kernel(Net n, int i_end) {
             float gb = has_k ? z0 * n.Cwin[b * K + k] : 0.f;
             float zn = kU * z0;
             for_each_spike(src_words_c(n, b, n.n_in + (int)j), n.RW, a0 + 1, r_end, [&](int st) {
-                if (has_k) gb += Eb[(long long)(st - a0 - 1) * K];
+                if (has_k && st + n.d_out <= r_end) gb += Eb[(long long)(st + n.d_out - a0 - 1) * K];
                 zn += exp2f(n.log2_kappa * (float)(r_end - st));
             });
             g += gb;

@@ -20,7 +20,9 @@ the surrogate values (every gradient and weight element).  Cases:
   gradients against oracle B started from the GPU's weights, and each Adam
   step against torch.optim.Adam (FP64) driven by the GPU's own gradients;
   the evidence-accumulation task (batch 32, recall-window cross-entropy)
-  with a per-sample oracle pool.
+  with a per-sample oracle pool;
+* generalized delays (Supplement "Generalized delays"): the readout delay
+  d_out and the learning-signal delay d_ls, in the single-window forms.
 """
 from __future__ import annotations
 
@@ -310,3 +312,30 @@ def test_weight_updates_with_every_spike(tk):
     W["spec"].lr = 5e-4
     rep = run_parity(W, calls=1, gpu_kw=dict(trace_kernel=tk))
     assert rep["spikes"] > 50
+
+
+# generalized delays (Supplement "Generalized delays"): the readout sees the
+# recurrent spikes d_out steps late, the learning signal reaches the
+# recurrent layer d_ls steps late (one update window per call)
+@pytest.mark.parametrize("d_out,d_ls", [(2, 0), (1, 3)])
+def test_generalized_delays_pattern_regression(d_out, d_ls):
+    W = C.pattern_regression(T=300)
+    W["spec"].d_out, W["spec"].d_ls = d_out, d_ls
+    rep = run_parity(W, calls=2)
+    assert rep["spikes"] > 300
+
+
+def test_generalized_delays_batched_event_classification():
+    W = C.event_classification(batch=4, T=150, len_lo=100, len_hi=150, n_rec=60, side=8,
+                               events_per_300=3000.0)
+    W["spec"].d_out, W["spec"].d_ls = 2, 2
+    rep = run_parity(W)
+    assert rep["spikes"] > 100
+
+
+def test_generalized_delays_need_one_window_per_call():
+    import paper_2511_21674_gb300 as ep
+    W = _replica(True, 200)
+    W["spec"].d_out = 1
+    with pytest.raises(ep.EpropError, match="generalized delays"):
+        _gpu_net(W)
