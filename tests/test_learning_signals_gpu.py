@@ -10,7 +10,7 @@ magnitudes).  The worst ratio is also reported against 1e-6 (the level of
 an FP32 FMA loop).  Shapes cover ragged tiles: neurons not a multiple of
 the 128-row tile, window lengths not a multiple of 16 and above the 256
 columns of one pass, K not a multiple of the 8-element K-step nor of the
-32-element chunk, K = 1, several samples.
+32-element chunk, K = 1, K of seven chunks, several samples.
 """
 from __future__ import annotations
 
@@ -29,6 +29,8 @@ SHAPES = [
     (129, 16, 33, 1),          # two K chunks, last one with one element
     (5000, 257, 64, 1),        # 257 steps: a pass of 256 and one of 1
     (257, 512, 8, 1),          # exactly two full passes
+    (300, 50, 200, 1),         # K = 200: seven K-chunks
+    (4000, 100, 100, 3),       # several samples over many tiles
 ]
 
 
