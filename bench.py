@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--launch-mode", type=int, default=None,
                    help="0 eager launches, 1 graph of launches, 2 persistent step loop "
                         "(default: 1, and 2 for the batched workload)")
+    p.add_argument("--scale", type=int, default=1,
+                   help="scaling workload: input, recurrent and readout layers times this factor "
+                        "(in-degrees and feedback out-degree fixed), as the paper's weak scaling grows it")
     p.add_argument("--n-rec", type=int, default=1_000_000)
     p.add_argument("--k-in", type=int, default=1000)
     p.add_argument("--T", type=int, default=1000)
@@ -201,14 +204,15 @@ def workload_config(args, nnz, world=1):
                 "trace_storage": "fp32", "parallelism": f"replicas{world}",
                 "l2": "small working set (L2-resident): a latency-bound workload"}
     if args.workload == "scaling":
-        return {"workload": f"scaling: {SCALING['n_rec']} ignore-and-fire neurons at 5 Hz, recurrent "
-                            f"in-degree {SCALING['k_rec']}, {SCALING['n_in']} Poisson inputs at 5 Hz "
-                            f"(in-degree {SCALING['k_in']}), {SCALING['n_out']} readouts (in-degree "
-                            f"{SCALING['k_out']}), feedback out-degree {SCALING['fb_outdeg']}, delays 1-5, "
-                            f"update window {SCALING['update_interval']}, continuous, "
-                            f"{SCALING['T']} steps per bench step ({nnz} synapses)",
-                "n_rec": SCALING["n_rec"], "k_rec": SCALING["k_rec"], "synapses": nnz,
-                "T_per_step": SCALING["T"], "trace_storage": args.trace_dtype,
+        sc = scaling_sizes(args)
+        return {"workload": f"scaling: {sc['n_rec']} ignore-and-fire neurons at 5 Hz, recurrent "
+                            f"in-degree {sc['k_rec']}, {sc['n_in']} Poisson inputs at 5 Hz "
+                            f"(in-degree {sc['k_in']}), {sc['n_out']} readouts (in-degree "
+                            f"{sc['k_out']}), feedback out-degree {sc['fb_outdeg']}, delays 1-5, "
+                            f"update window {sc['update_interval']}, continuous, "
+                            f"{sc['T']} steps per bench step ({nnz} synapses)",
+                "n_rec": sc["n_rec"], "k_rec": sc["k_rec"], "synapses": nnz, "scale": args.scale,
+                "T_per_step": sc["T"], "trace_storage": args.trace_dtype,
                 "trace_form": args.trace_kernel, "parallelism": f"replicas{world}",
                 "l2": "inputs larger than L2 (synapse records ~13 GB)"}
     if args.workload == "balanced":
@@ -231,6 +235,15 @@ def workload_config(args, nnz, world=1):
 # the scaling experiment's network (Methods, "Scaling"): base size, 20 s
 SCALING = dict(n_rec=128_000, k_rec=10_000, n_in=1000, k_in=100, n_out=10, k_out=1000, fb_outdeg=100,
                T=20_000, update_interval=1000)
+
+
+def scaling_sizes(args):
+    """The scaling network grown by --scale: the paper's weak scaling enlarges
+    the input, recurrent and readout layers together at fixed in-degrees."""
+    f = max(1, int(getattr(args, "scale", 1)))
+    return dict(SCALING, n_rec=SCALING["n_rec"] * f, n_in=SCALING["n_in"] * f, n_out=SCALING["n_out"] * f)
+
+
 # the bounded sample of it the CPU oracle runs
 SCALING_SAMPLE = dict(n_rec=2000, k_rec=1000, n_in=100, k_in=10, n_out=10, k_out=100, fb_outdeg=20,
                       T=100, update_interval=100)
@@ -384,7 +397,7 @@ def _run_ours(args, rank, world, local):
     if args.workload == "batched":
         W = C.event_classification(batch=64, seed=1235 + rank)
     elif args.workload == "scaling":
-        W = G.scaling_torch(seed=replica_seed(rank) + 4, **SCALING)
+        W = G.scaling_torch(seed=replica_seed(rank) + 4, **scaling_sizes(args))
     elif args.workload == "balanced":
         # lr 1e-8 keeps the rate in the 5-10 Hz band over the timed calls
         # (the regression signal through unit-variance feedback to every

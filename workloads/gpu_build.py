@@ -27,10 +27,10 @@ def ei_network_torch(n: int, k_in: int, max_delay: int, J: float, g: float, seed
     s = span // k_in
     if k_in > span:
         raise ValueError("in-degree larger than the number of sources")
-    keys, dels = [], []
     m = torch.arange(k_in, device=device, dtype=torch.int64)
-    for j0 in range(0, n, chunk_targets):
-        j1 = min(n, j0 + chunk_targets)
+
+    def chunk(j0, j1):
+        """(pre, target, delay) of the synapses onto targets j0..j1-1, by target."""
         j = torch.arange(j0, j1, device=device, dtype=torch.int64).repeat_interleave(k_in)
         mm = m.repeat(j1 - j0)
         h = _u64_t(seed, C._TAG_PRE, j, mm)
@@ -38,15 +38,48 @@ def ei_network_torch(n: int, k_in: int, max_delay: int, J: float, g: float, seed
         hi = (h >> 32) & 0xFFFFFFFF
         lo = h & 0xFFFFFFFF
         r = ((hi % s) * ((1 << 32) % s) + lo % s) % s
-        off = 1 + mm * s + r
-        pre = (j + off) % n
-        keys.append(pre * n + j)
+        pre = (j + 1 + mm * s + r) % n
         hd = _u64_t(seed, C._TAG_DELAY, j, mm)
         hi = (hd >> 32) & 0xFFFFFFFF
         lo = hd & 0xFFFFFFFF
-        dels.append((1 + ((hi % max_delay) * ((1 << 32) % max_delay) + lo % max_delay) % max_delay)
-                    .to(torch.uint8))
-        del j, mm, h, hi, lo, r, off, pre, hd
+        d = (1 + ((hi % max_delay) * ((1 << 32) % max_delay) + lo % max_delay) % max_delay).to(torch.uint8)
+        return pre, j, d
+
+    if n * k_in >= (1 << 31) - 1:
+        # too many synapses for one sort: counting placement by source, chunk
+        # by chunk in ascending target order, gives the same CSR (targets of
+        # a row ascending, as the sorted build)
+        counts = torch.zeros(n, dtype=torch.int64, device=device)
+        for j0 in range(0, n, chunk_targets):
+            pre, _, _ = chunk(j0, min(n, j0 + chunk_targets))
+            counts += torch.bincount(pre, minlength=n)
+        ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+        ptr[1:] = torch.cumsum(counts, 0)
+        nnz = int(ptr[-1])
+        col = torch.empty(nnz, dtype=torch.int32, device=device)
+        dly = torch.empty(nnz, dtype=torch.uint8, device=device)
+        w = torch.empty(nnz, dtype=torch.float32, device=device)
+        fill = ptr[:-1].clone()
+        for j0 in range(0, n, chunk_targets):
+            pre, j, d = chunk(j0, min(n, j0 + chunk_targets))
+            pre_s, order = torch.sort(pre, stable=True)     # targets stay ascending within a source
+            grp, cnt = torch.unique_consecutive(pre_s, return_counts=True)
+            first = torch.cumsum(cnt, 0) - cnt
+            rank = torch.arange(pre_s.numel(), device=device) - torch.repeat_interleave(first, cnt)
+            pos = fill[pre_s] + rank
+            col[pos] = j[order].to(torch.int32)
+            dly[pos] = d[order]
+            w[pos] = torch.where(pre_s < int(0.8 * n), torch.tensor(J, device=device),
+                                 torch.tensor(-g * J, device=device)).to(torch.float32)
+            fill[grp] += cnt
+            del pre, j, d, pre_s, order, grp, cnt, first, rank, pos
+        return ptr, col, w, dly
+    keys, dels = [], []
+    for j0 in range(0, n, chunk_targets):
+        pre, j, d = chunk(j0, min(n, j0 + chunk_targets))
+        keys.append(pre * n + j)
+        dels.append(d)
+        del pre, j, d
     key = torch.cat(keys)
     del keys
     dly = torch.cat(dels)
