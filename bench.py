@@ -407,6 +407,7 @@ def _run_ours(args, rank, world, local):
         W = G.million_sparse_torch(n_rec=args.n_rec, k_in=args.k_in, T=args.T, n_out=args.n_out,
                                    seed=replica_seed(rank))
     spec = W["spec"]
+    torch.cuda.empty_cache()        # the build's freed temporaries back to the device
     trace_dtype = {"fp32": 0, "bf16": 1, "fp16": 2}[args.trace_dtype]
     if args.workload == "batched":
         trace_dtype = 0                  # single-window form: no traces are stored
