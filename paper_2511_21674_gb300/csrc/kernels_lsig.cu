@@ -252,13 +252,225 @@ __global__ void __launch_bounds__(kLsThreads) learning_signal_kernel(const float
     }
 }
 
+// Warp-specialised form for one error window (batch 1, U <= 128, K <= 128:
+// the million-neuron workload's window).  One CTA per SM walks tiles of 128
+// neurons; the window's E is split into TF32 hi + lo once and stays in
+// shared memory.  Roles run concurrently, joined by mbarriers:
+//   warps 4-7  producers: each feedback chunk (128 rows x 32) is loaded
+//              (registers one chunk ahead), split and stored into one of two
+//              operand stages; arrive on full[stage];
+//   warp 8     one thread issues the chunk's products into one of two
+//              accumulator pairs in TMEM and commits to empty[stage], and at
+//              a tile's end to acc_full[pair];
+//   warps 0-3  epilogue: read a finished accumulator pair (TMEM lanes 32 w ..
+//              32 w + 31 = the tile's neurons), add hi*hi and the corrections
+//              and store L; arrive on acc_empty[pair].
+// So the loads, the products and the stores of different tiles overlap.
+// The products and their order within a tile are those of
+// learning_signal_kernel.  Every wait is bounded; a wait that gives up
+// raises a CTA-wide abort flag that every role checks.
+constexpr int kLsPKC = 4;                          // K-chunks kept resident (K <= 128)
+constexpr int kLsWThreads = 288;                   // 9 warps
+constexpr int kLsWStages = 2;
+constexpr size_t kLsWSmem = 1024 + (size_t)kLsPKC * 2 * kLsEreg + (size_t)kLsWStages * 2 * kLsAreg;
+static_assert(kLsWSmem <= 200 * 1024, "warp-specialised learning-signal buffers exceed the request");
+
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kLsWThreads, 1)
+    learning_signal_ws_kernel(const float *__restrict__ fb, const float *__restrict__ E, float *__restrict__ L,
+                              int N, int U, int K, unsigned *err) {
+    extern __shared__ unsigned char ls_raw[];
+    __shared__ uint64_t full[kLsWStages], empty[kLsWStages], acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(ls_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *e_base = base;
+    unsigned char *a_base = base + (size_t)kLsPKC * 2 * kLsEreg;
+    const int nkc = (K + kLsKC - 1) / kLsKC;
+    const int tiles = (N + kLsM - 1) / kLsM;
+    const int npad = (U + 15) & ~15;
+    uint32_t half = 32;
+    while ((int)half < npad) half <<= 1;
+    const uint32_t ncols = 4 * half;                 // two accumulator pairs
+    if (warp == 0) tmem_alloc(&tmem_slot, ncols);
+    if (tid == 0) {
+        for (int q2 = 0; q2 < kLsWStages; ++q2) {
+            mbar_init(&full[q2], 4);                  // one arrival per producer warp
+            mbar_init(&empty[q2], 1);                 // the products' commit
+        }
+        for (int q2 = 0; q2 < 2; ++q2) {
+            mbar_init(&acc_full[q2], 1);
+            mbar_init(&acc_empty[q2], 4);             // one arrival per epilogue warp
+        }
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    // the error window, split once (every thread)
+    for (int kc = 0; kc < nkc; ++kc) {
+        const int k = kc * kLsKC + lane;
+        const bool kin = k < K;
+        for (int r = warp; r < npad; r += kLsWThreads / 32) {
+            const float x = (kin && r < U) ? __ldg(E + (long long)r * K + k) : 0.f;
+            put_split(e_base + (size_t)(2 * kc) * kLsEreg, e_base + (size_t)(2 * kc + 1) * kLsEreg,
+                      sw128_off(r, lane), x);
+        }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        for (unsigned it2 = 0; it2 < kWaitLimit; ++it2) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if (s_abort) return false;
+        }
+        atomicOr(err, 2u);
+        s_abort = 1;
+        return false;
+    };
+    long long n_my = 0;                               // tiles of this CTA
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) ++n_my;
+    long long last_commit = -1;                       // products: chunks committed
+    if (warp >= 4 && warp < 8) {
+        // ---- producers: 128 threads, thread (pw, lane) owns rows pw + 4 i
+        const int pw = warp - 4;
+        float pre[kLsM / 4];
+        auto load_chunk = [&](long long c) {
+            const long long tl = c / nkc;
+            const int kc = (int)(c % nkc);
+            const int j0 = (int)(blockIdx.x + tl * gridDim.x) * kLsM;
+            const int k = kc * kLsKC + lane;
+            const bool use = tl < n_my && k < K;
+#pragma unroll
+            for (int i = 0; i < kLsM / 4; ++i) {
+                const int j = j0 + pw + 4 * i;
+                pre[i] = (use && j < N) ? __ldg(fb + (long long)j * K + k) : 0.f;
+            }
+        };
+        const long long nch = n_my * nkc;
+        if (nch > 0) load_chunk(0);
+        for (long long c = 0; c < nch; ++c) {
+            const int st = (int)(c % kLsWStages);
+            if (c >= kLsWStages && !wait(&empty[st], (uint32_t)(((c / kLsWStages) - 1) & 1))) break;
+            unsigned char *ah = a_base + (size_t)(2 * st) * kLsAreg, *al = a_base + (size_t)(2 * st + 1) * kLsAreg;
+#pragma unroll
+            for (int i = 0; i < kLsM / 4; ++i) put_split(ah, al, sw128_off(pw + 4 * i, lane), pre[i]);
+            if (c + 1 < nch) load_chunk(c + 1);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cta(&full[st]);
+        }
+    } else if (warp == 8) {
+        // ---- products: the whole warp follows the barriers (it stays
+        // converged), lane 0 issues
+        const uint32_t idesc = idesc_tf32(kLsM, npad);
+        long long c = 0;
+        for (long long tl = 0; tl < n_my; ++tl) {
+            const int pair = (int)(tl & 1);
+            if (tl >= 2 && !wait(&acc_empty[pair], (uint32_t)(((tl / 2) - 1) & 1))) break;
+            tc_fence_after();
+            const uint32_t acc_hi = tmem + (uint32_t)pair * 2 * half, acc_lo = acc_hi + half;
+            bool okc = true;
+            for (int kc = 0; kc < nkc; ++kc, ++c) {
+                const int st = (int)(c % kLsWStages);
+                if (!wait(&full[st], (uint32_t)((c / kLsWStages) & 1))) { okc = false; break; }
+                tc_fence_after();
+                if (lane == 0) {
+                    const int nks = (min(kLsKC, K - kc * kLsKC) + 7) >> 3;
+                    const uint32_t ah = smem_u32(a_base + (size_t)(2 * st) * kLsAreg);
+                    const uint32_t al = smem_u32(a_base + (size_t)(2 * st + 1) * kLsAreg);
+                    const uint32_t eh = smem_u32(e_base + (size_t)(2 * kc) * kLsEreg);
+                    const uint32_t el = smem_u32(e_base + (size_t)(2 * kc + 1) * kLsEreg);
+                    uint32_t acc = kc > 0 ? 1u : 0u;
+                    for (int s2 = 0; s2 < nks; ++s2) {
+                        const uint32_t o = 32u * s2;
+                        umma_tf32(acc_hi, sdesc_sw128(ah + o), sdesc_sw128(eh + o), idesc, acc);
+                        umma_tf32(acc_lo, sdesc_sw128(ah + o), sdesc_sw128(el + o), idesc, acc);
+                        umma_tf32(acc_lo, sdesc_sw128(al + o), sdesc_sw128(eh + o), idesc, 1);
+                        acc = 1;
+                    }
+                    umma_commit(&empty[st]);
+                }
+                __syncwarp();
+                last_commit = c;
+            }
+            if (!okc) break;
+            if (lane == 0) umma_commit(&acc_full[pair]);
+            __syncwarp();
+        }
+    } else if (warp < 4) {
+        // ---- epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31
+        const int ngrp = npad >> 4;
+        for (long long tl = 0; tl < n_my; ++tl) {
+            const int pair = (int)(tl & 1);
+            if (!wait(&acc_full[pair], (uint32_t)((tl / 2) & 1))) break;
+            tc_fence_after();
+            const int j = (int)(blockIdx.x + tl * gridDim.x) * kLsM + 32 * warp + lane;
+            const uint32_t ta0 = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)pair * 2 * half;
+            for (int g = 0; g < ngrp; ++g) {
+                uint32_t v[16], w[16];
+                tmem_ld16_nowait(ta0 + (uint32_t)(16 * g), v);
+                tmem_ld16_nowait(ta0 + half + (uint32_t)(16 * g), w);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (j < N) {
+#pragma unroll
+                    for (int c2 = 0; c2 < 16; ++c2) {
+                        const int u = 16 * g + c2;
+                        if (u < U) L[(long long)u * N + j] = __uint_as_float(v[c2]) + __uint_as_float(w[c2]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cta(&acc_empty[pair]);
+        }
+    }
+    // products in flight when a wait gave up: one more bounded wait on the
+    // last commit before the accumulators are released
+    if (warp == 8 && lane == 0 && s_abort && last_commit >= 0) {
+        const int st = (int)(last_commit % kLsWStages);
+        for (unsigned it2 = 0; it2 < kWaitLimit; ++it2)
+            if (mbar_try_wait(&empty[st], (uint32_t)((last_commit / kLsWStages) & 1))) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
 void prepare_learning_signal_attributes() {
     cudaFuncSetAttribute(learning_signal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLsSmem);
+    cudaFuncSetAttribute(learning_signal_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLsWSmem);
 }
 
 void launch_learning_signals(const float *fb, const float *E, float *L, int N, int U, int K, int B,
                              unsigned *err, cudaStream_t st) {
     if (N <= 0 || U <= 0 || K <= 0 || B <= 0) return;
+    if (B == 1 && U <= kLsNmax && K <= kLsPKC * kLsKC) {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int tiles = (N + kLsM - 1) / kLsM;
+        learning_signal_ws_kernel<<<tiles < sms ? tiles : sms, kLsWThreads, kLsWSmem, st>>>(fb, E, L, N, U, K, err);
+        return;
+    }
     const dim3 grid((unsigned)((N + kLsM - 1) / kLsM), (unsigned)B);
     learning_signal_kernel<<<grid, kLsThreads, kLsSmem, st>>>(fb, E, L, N, U, K, err);
 }

@@ -10,7 +10,8 @@ magnitudes).  The worst ratio is also reported against 1e-6 (the level of
 an FP32 FMA loop).  Shapes cover ragged tiles: neurons not a multiple of
 the 128-row tile, window lengths not a multiple of 16 and above the 256
 columns of one pass, K not a multiple of the 8-element K-step nor of the
-32-element chunk, K = 1, K of seven chunks, several samples.
+32-element chunk, K = 1, K of seven chunks, several samples, and one window
+of one sample over many tiles (the warp-specialised form of U, K <= 128).
 """
 from __future__ import annotations
 
@@ -31,6 +32,11 @@ SHAPES = [
     (257, 512, 8, 1),          # exactly two full passes
     (300, 50, 200, 1),         # K = 200: seven K-chunks
     (4000, 100, 100, 3),       # several samples over many tiles
+    # one window of one sample (the warp-specialised form): several tiles
+    # per CTA (stage and accumulator reuse), full U and K, tiny shapes
+    (100_000, 100, 100, 1),
+    (2000, 128, 128, 1),
+    (300, 5, 7, 1),
 ]
 
 
