@@ -62,8 +62,10 @@ def parse():
     p.add_argument("--n-out", type=int, default=100)
     p.add_argument("--trace-dtype", default="bf16", choices=["bf16", "fp16", "fp32"])
     p.add_argument("--blocks-per-sm", type=int, default=0)
-    p.add_argument("--trace-kernel", default="dense", choices=["dense", "lazy"],
-                   help="synapse-trace form: dense window pass or lazy catch-up at arrivals")
+    p.add_argument("--trace-kernel", default="dense", choices=["dense", "band", "lazy"],
+                   help="synapse-trace form: dense window pass (source-major records), the same "
+                        "with band-major records (coefficients in shared memory), or lazy catch-up "
+                        "at arrivals")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the batched-form timing (event classification, batch 64)")
@@ -415,7 +417,7 @@ def _run_ours(args, rank, world, local):
                      launch_mode=launch_mode(args), trace_dtype=trace_dtype, record_grad=0, record_raster=0,
                      profile=1, blocks_per_sm=args.blocks_per_sm,
                      trace_kernel=(0 if args.workload == "batched" else
-                                   3 if args.trace_kernel == "dense" else 1))
+                                   {"dense": 3, "band": 4, "lazy": 1}[args.trace_kernel]))
     nnz = int(W["col"].shape[0])
     del W["ptr"], W["col"], W["w"], W["delay"], W["w_out"], W["feedback"], W["out_mask"]
     torch.cuda.empty_cache()
@@ -507,9 +509,11 @@ def _run_ours(args, rank, world, local):
                       "BF16 traces: ~5e-4 relative L2 vs the oracle (gated at 1e-2)",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": ("window_pass_kernel (spiking-row and idle-row launches per update window)"
-                                if args.trace_kernel == "dense" else
-                                "trace_window_kernel (lazy: rows with an arrival in the window)"),
+                     "kernel": {"dense": "window_pass_kernel (spiking-row and idle-row launches per update window)",
+                                "band": "window_band_kernel (band-major records, the band's coefficients in "
+                                        "shared memory) after band_rows_kernel (row records of the window)",
+                                "lazy": "trace_window_kernel (lazy: rows with an arrival in the window)"
+                                }[args.trace_kernel],
                      "bytes_per_event": bytes_per_event,
                      "stream_bytes_per_window": nnz * bytes_per_event,
                      "algorithmic_bytes_per_window": (events * bytes_per_event / windows) if windows else None,

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libeprop.so")
-SOURCES = ["eprop_api.cu", "kernels_step.cu", "kernels_window.cu", "kernels_lsig.cu", "predictor.cu"]
+SOURCES = ["eprop_api.cu", "kernels_step.cu", "kernels_window.cu", "kernels_lsig.cu", "kernels_band.cu",
+           "predictor.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

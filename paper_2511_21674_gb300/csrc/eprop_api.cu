@@ -33,7 +33,8 @@ struct eprop_net {
     std::vector<DevAlloc> in_allocs;      // per-T input buffers
     long long nnz_in = 0;
     int U_alloc = 0, T_alloc = 0, T_in = 0, U_fixed = 0;
-    int trace_mode = 0;                 // 0 window work queue, 1 batched, 2 dense window pass
+    int trace_mode = 0;                 // 0 window work queue, 1 batched, 2 dense window pass,
+                                        // 3 band-major dense window pass
     int qp_stride = 2;
     long long x_cap = 0;
     long long max_in_per_step = 0;
@@ -164,9 +165,13 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     if (c.trace_kernel == 1) net->trace_mode = 0;
     else if (c.trace_kernel == 2) net->trace_mode = 1;
     else if (c.trace_kernel == 3) net->trace_mode = 2;
+    else if (c.trace_kernel == 4) net->trace_mode = 3;
     else net->trace_mode = n.has_state ? 2 : (B > 1 ? 1 : 0);
     (void)qp_bytes;
-    n.dense = net->trace_mode == 2 ? 1 : 0;
+    // row records keep spike steps as 16-bit offsets inside the window
+    if (net->trace_mode == 3 && U + D > 65536)
+        return fail(net, EPROP_EINVAL, "trace_kernel 4 needs update windows of at most 65536 - max_delay steps");
+    n.dense = (net->trace_mode == 2 || net->trace_mode == 3) ? 1 : 0;
     // the readout reads the spike list of the step d_out back
     n.RS = std::max(net->trace_mode != 1 ? U + D + 1 : 2, c.d_out + 2);
     n.RC = 0;
@@ -208,6 +213,105 @@ static eprop_status alloc_window(eprop_net *net, int U, int T) {
     return EPROP_OK;
 }
 
+// Band-major records (trace_kernel 4, kernels_band.cu), built from the
+// source-major packing (n.tgt_d, n.w): per row and band the count and first
+// position (seg), bands padded to whole tiles, per tile its first row and
+// band, then every record placed.  The source-major weights are freed; n.w
+// becomes the band-major array.
+static eprop_status build_band(eprop_net *net) {
+    Net &n = net->n;
+    std::vector<DevAlloc> &o = net->fixed_allocs;
+    eprop::prepare_band_attributes();
+    const int S = n.n_src, N = n.n_rec;
+    const int Wmax = eprop::band_width(n.alif != 0);
+    const int nb = (N + Wmax - 1) / Wmax;
+    const int W = (N + nb - 1) / nb;
+    n.band = 1;
+    n.band_w = W;
+    n.nb = nb;
+    n.rr_stride = (4 * n.D + 2 + 16 + 15) & ~15;
+    n.rr_cap = (n.rr_stride - 4 * n.D - 2) / 2;
+    std::vector<DevAlloc> tmp;
+    auto nomem = [&]() {
+        free_all(tmp);
+        return fail(nullptr, EPROP_ENOMEM, "band layout allocation");
+    };
+    void *p;
+    if (dalloc(o, &p, (size_t)(S + 1) * nb * 4) != cudaSuccess) return nomem();
+    int *seg = static_cast<int *>(p);
+    n.seg = seg;
+    if (S > 0) eprop::launch_band_count(n.row_ptr, n.tgt_d, S, W, nb, seg);
+    const int chunk = 1024;
+    const int nch = std::max(1, (S + chunk - 1) / chunk);
+    if (dalloc(tmp, &p, (size_t)nch * nb * 8) != cudaSuccess) return nomem();
+    long long *part = static_cast<long long *>(p);
+    if (S > 0) eprop::launch_band_chunk_sum(seg, S, nb, chunk, part);
+    std::vector<long long> hp((size_t)nch * nb), tot(nb, 0);
+    cudaError_t e = cudaMemcpy(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        free_all(tmp);
+        return cuda_fail(nullptr, e, "band layout counts");
+    }
+    for (int c = 0; c < nch; ++c)
+        for (int b = 0; b < nb; ++b) {
+            const long long v = hp[(size_t)c * nb + b];
+            hp[(size_t)c * nb + b] = tot[b];
+            tot[b] += v;
+        }
+    for (int b = 0; b < nb; ++b)
+        if (tot[b] > (long long)INT32_MAX - eprop::kBandTile) {
+            free_all(tmp);
+            return fail(nullptr, EPROP_EINVAL, "trace_kernel 4: a band holds 2^31 synapses or more");
+        }
+    cudaMemcpy(part, hp.data(), hp.size() * 8, cudaMemcpyHostToDevice);
+    if (S > 0) eprop::launch_band_chunk_scan(seg, S, nb, chunk, part);
+    std::vector<int> last(nb);
+    for (int b = 0; b < nb; ++b) last[b] = (int)tot[b];
+    cudaMemcpy(seg + (size_t)S * nb, last.data(), (size_t)nb * 4, cudaMemcpyHostToDevice);
+    std::vector<long long> t0(nb + 1, 0), base(nb + 1);
+    for (int b = 0; b < nb; ++b) t0[b + 1] = t0[b] + (tot[b] + eprop::kBandTile - 1) / eprop::kBandTile;
+    for (int b = 0; b <= nb; ++b) base[b] = t0[b] * eprop::kBandTile;
+    n.n_tiles = t0[nb];
+    n.nnz_b = n.n_tiles * eprop::kBandTile;
+    if (dalloc(o, &p, (size_t)(nb + 1) * 8) != cudaSuccess) return nomem();
+    cudaMemcpy(p, base.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice);
+    n.band_base = static_cast<const long long *>(p);
+    if (dalloc(tmp, &p, (size_t)(nb + 1) * 8) != cudaSuccess) return nomem();
+    long long *tile0 = static_cast<long long *>(p);
+    cudaMemcpy(tile0, t0.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice);
+    if (dalloc(o, &p, (size_t)std::max(1LL, n.n_tiles) * sizeof(int4)) != cudaSuccess) return nomem();
+    int4 *tiles = static_cast<int4 *>(p);
+    n.tiles = tiles;
+    if (dalloc(tmp, &p, 4) != cudaSuccess) return nomem();
+    unsigned *flag = static_cast<unsigned *>(p);
+    if (n.n_tiles > 0) eprop::launch_band_tiles(seg, tile0, S, nb, n.n_tiles, tiles, flag);
+    if (dalloc(o, &p, (size_t)(n.nnz_b + 16) * 4) != cudaSuccess) return nomem();
+    uint32_t *bd_td = static_cast<uint32_t *>(p);
+    cudaMemset(bd_td, 0xFF, (size_t)(n.nnz_b + 16) * 4);
+    n.bd_td = bd_td;
+    if (dalloc(o, &p, (size_t)(n.nnz_b + 16) * 4) != cudaSuccess) return nomem();
+    float *w_b = static_cast<float *>(p);
+    if (S > 0 && n.nnz > 0) eprop::launch_band_scatter(n, n.w, bd_td, w_b);
+    unsigned hflag = 0;
+    e = cudaMemcpy(&hflag, flag, 4, cudaMemcpyDeviceToHost);
+    free_all(tmp);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "band layout build");
+    if (hflag)
+        return fail(nullptr, EPROP_EINVAL,
+                    "trace_kernel 4: a tile of a band spans 2^15 source rows or more (rows too sparse per band)");
+    for (size_t q = 0; q < o.size(); ++q)
+        if (o[q].p == n.w) {
+            cudaFree(o[q].p);
+            o.erase(o.begin() + (long long)q);
+            break;
+        }
+    n.w = w_b;
+    if (dalloc(o, &p, (size_t)std::max(1, S) * n.rr_stride) != cudaSuccess)
+        return fail(nullptr, EPROP_ENOMEM, "band layout allocation");
+    n.rrec = static_cast<unsigned char *>(p);
+    return EPROP_OK;
+}
+
 extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const eprop_synapses *syn,
                                              const float *w_out, const uint8_t *out_mask,
                                              const float *feedback, int32_t is_device,
@@ -239,11 +343,16 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
     if (c.launch_mode == 2 && (c.continuous || c.update_interval > 0 || c.n_out > 256))
         return fail(nullptr, EPROP_EINVAL,
                     "launch_mode 2 (persistent step loop) needs one update window per call and n_out <= 256");
-    if (c.trace_kernel < 0 || c.trace_kernel > 3 || c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
-        return fail(nullptr, EPROP_EINVAL, "trace_kernel must be 0..3 and blocks_per_sm 0..64");
+    if (c.trace_kernel < 0 || c.trace_kernel > 4 || c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
+        return fail(nullptr, EPROP_EINVAL, "trace_kernel must be 0..4 and blocks_per_sm 0..64");
     if (c.trace_kernel == 3 && !(c.continuous || c.update_interval > 0))
         return fail(nullptr, EPROP_EINVAL,
                     "trace_kernel 3 (dense window pass) advances carried state: it needs continuous or update_interval > 0");
+    if (c.trace_kernel == 4 && (!(c.continuous || c.update_interval > 0) || c.batch != 1 || c.optimizer != 0 ||
+                                (c.sign_mask & 3)))
+        return fail(nullptr, EPROP_EINVAL,
+                    "trace_kernel 4 (band-major dense window pass) needs carried state (continuous or "
+                    "update_interval > 0), batch 1, optimizer 0 and free synapse signs");
     if (c.trace_kernel == 1 && c.batch > 1)
         return fail(nullptr, EPROP_EINVAL, "the lazy trace form (trace_kernel 1) needs batch = 1");
     if (c.trace_kernel == 2 && (c.continuous || c.update_interval > 0))
@@ -392,11 +501,19 @@ extern "C" eprop_status eprop_create_network(const eprop_config *cfg, const epro
             if (hflag & 1u) { s = fail(nullptr, EPROP_EINVAL, "synapse target out of [0, n_rec)"); goto fail_out; }
             if (hflag & 2u) { s = fail(nullptr, EPROP_EINVAL, "synapse delay out of [1, max_delay]"); goto fail_out; }
         }
-        if (n.has_state) {              // one trace per sample and synapse ([B][nnz])
-            FA(ebar, uint16_t, (B * nnz + 16) * (n.trace_bf16 ? 1 : 2));
-            if (n.alif) FA(epsa, uint16_t, (B * nnz + 16) * (n.trace_bf16 ? 1 : 2));
+        if (c.trace_kernel == 4) {
+            s = build_band(net);
+            if (s != EPROP_OK) goto fail_out;
         }
-        if (n.record_grad) FA(grad, float, nnz);
+        {
+            // band-major records include the padding of whole tiles
+            const long long nnz_t = n.band ? n.nnz_b : nnz;
+            if (n.has_state) {              // one trace per sample and synapse ([B][nnz])
+                FA(ebar, uint16_t, (B * nnz_t + 16) * (n.trace_bf16 ? 1 : 2));
+                if (n.alif) FA(epsa, uint16_t, (B * nnz_t + 16) * (n.trace_bf16 ? 1 : 2));
+            }
+            if (n.record_grad) FA(grad, float, nnz_t + 16);
+        }
         // neurons
         FA(v, float, B * N);
         FA(a, float, B * N);
@@ -613,8 +730,9 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
         eprop::launch_fill_int(n.anchor_t, B * S, eprop::kNoSpike, st);
         if (n.has_state) {
             const size_t tb = n.trace_bf16 ? 2 : 4;
-            cudaMemsetAsync(n.ebar, 0, B * n.nnz * tb, st);
-            if (n.alif) cudaMemsetAsync(n.epsa, 0, B * n.nnz * tb, st);
+            const long long nt = n.band ? n.nnz_b : n.nnz;
+            cudaMemsetAsync(n.ebar, 0, B * nt * tb, st);
+            if (n.alif) cudaMemsetAsync(n.epsa, 0, B * nt * tb, st);
         }
     }
     if (n.record_raster) cudaMemsetAsync(n.rec_raster, 0, B * ((T + 31) / 32) * N * 4, st);
@@ -699,7 +817,8 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
                 L += 5;
             }
         }
-        eprop::launch_deliver(n, i, deliver_rows, st);
+        if (n.band) eprop::launch_deliver_band(n, i, deliver_rows, st);
+        else eprop::launch_deliver(n, i, deliver_rows, st);
         L += 3;
         }
         if (i % U == 0) {
@@ -723,6 +842,9 @@ static void issue_call(eprop_net *net, int T, const uint8_t *forced) {
             } else if (net->trace_mode == 2) {
                 eprop::launch_window_pass(n, i, pass_rows, idle_rows, st);
                 LT += 3;
+            } else if (net->trace_mode == 3) {
+                eprop::launch_window_band(n, i, net->sm_count, st);
+                LT += 2;
             } else {
                 eprop::launch_trace_window(n, i, grid_rows, st);
                 LT += 2;
@@ -828,7 +950,15 @@ extern "C" eprop_status eprop_read_weights_grads(eprop_net *net, int32_t proj, f
     const long long q1 = proj == 0 ? net->nnz_in : n.nnz;
     const long long cnt = q1 - q0;
     if (cnt == 0) return EPROP_OK;
-    if (n.has_state && !n.dense && c.continuous && net->r_base > 0 && net->U_alloc > 0) {
+    if (n.band) {
+        eprop_status s = ensure_tmp(net, n.nnz);
+        if (s != EPROP_OK) return s;
+        const int r0 = proj == 0 ? 0 : c.n_in, r1 = proj == 0 ? c.n_in : c.n_in + c.n_rec;
+        eprop::launch_band_gather(n, r0, r1, q0, w ? net->tmp_w : nullptr, grad ? net->tmp_g : nullptr, st);
+        CK(net, cudaGetLastError());
+        if (w) CK(net, cudaMemcpyAsync(w, net->tmp_w, cnt * 4, kind, st));
+        if (grad) CK(net, cudaMemcpyAsync(grad, net->tmp_g, cnt * 4, kind, st));
+    } else if (n.has_state && !n.dense && c.continuous && net->r_base > 0 && net->U_alloc > 0) {
         eprop_status s = ensure_tmp(net, n.nnz);
         if (s != EPROP_OK) return s;
         eprop::launch_flush(n, 0, net->tmp_w, net->tmp_g, q0, q1, 0, net->sm_count, st);
@@ -919,7 +1049,8 @@ extern "C" eprop_status eprop_autotune(eprop_net *net, eprop_tune_result *out) {
     // candidates: the trace form (only before the first call, while the
     // carried state is still zero) and the CTAs per SM of the row kernels
     std::vector<int> tks;
-    if (pristine && c.batch == 1 && net->n.has_state && !net->n.adam && !(c.sign_mask & 3)) tks = {3, 1};
+    if (pristine && c.batch == 1 && net->n.has_state && !net->n.adam && !(c.sign_mask & 3) && !net->n.band)
+        tks = {3, 1};
     else tks = {tk0};
     const int bps_list[4] = {1, 2, 3, 4};
     std::memset(out, 0, sizeof(*out));

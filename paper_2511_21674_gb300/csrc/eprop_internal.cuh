@@ -144,7 +144,25 @@ struct Net {
     int if_period;            // ignore-and-fire period (0: off)
     unsigned long long if_seed;
     int d_out, d_ls;          // generalized delays: readout input, learning signal
+    // band-major learning state (trace_kernel 4, kernels_band.cu): w, ebar,
+    // epsa and grad above are then in band-major order, tgt_d stays the
+    // source-major packing of the creation arrays (read-back order)
+    int band;                 // 1: band-major synapse records
+    int band_w, nb;           // targets per band, number of bands
+    int rr_stride, rr_cap;    // bytes per row record, spikes kept per record
+    long long nnz_b;          // band-major records incl. padding (multiple of kBandTile)
+    long long n_tiles;        // nnz_b / kBandTile
+    const uint32_t *bd_td;    // [nnz_b] (target - band start) | (delay - 1) << 14 | (row - tile row0) << 17
+    const int *seg;           // [n_src + 1][nb] first position of each row inside each band
+    const long long *band_base;   // [nb + 1] first record of each band (padded)
+    const int4 *tiles;        // [n_tiles] (first row, rows spanned, band, 0)
+    unsigned char *rrec;      // [n_src][rr_stride] row records of the current window
 };
+
+// Band-major form: records of one band (a range of band_w targets) are
+// contiguous, by source row, padded to whole tiles of kBandTile records.
+constexpr int kBandTile = 1024;
+constexpr uint32_t kBandPad = 0xFFFFFFFFu;     // bd_td of a padding record
 
 // ----------------------------------------------------------------- helpers
 
@@ -363,7 +381,7 @@ __device__ __forceinline__ RowInfo row_info(const Net &n, const uint32_t *words,
     float z_p = anchor_z;
     for (int s = (lo > 1 ? lo : 1); s <= lim; ++s) {
         if (bit_at(words, n.RW, s)) {
-            z_p = (s_p == kNoSpike ? 0.0f : z_p * pow_alpha(n, s - s_p)) + 1.0f;
+            z_p = s_p == kNoSpike ? 1.0f : __fmaf_rn(z_p, pow_alpha(n, s - s_p), 1.0f);
             s_p = s;
         }
     }
@@ -377,8 +395,8 @@ __device__ __forceinline__ RowInfo row_info(const Net &n, const uint32_t *words,
         const int b_p = ((a_p + n.U - 1) / n.U) * n.U;
         ri.b_prev = b_p;
         ri.k_prev = b_p / n.U;
-        ri.zbar_bp = z_p * pow_alpha(n, b_p - a_p);
-        ri.zbar_a0 = z_p * pow_alpha(n, a0 - a_p);
+        ri.zbar_bp = __fmul_rn(z_p, pow_alpha(n, b_p - a_p));
+        ri.zbar_a0 = __fmul_rn(z_p, pow_alpha(n, a0 - a_p));
     }
     (void)want_first;
     return ri;
@@ -418,20 +436,34 @@ __device__ __forceinline__ Coef load_coef_dense(const Net &n, uint32_t j) {
     }
     return c;
 }
+// The window transfer's products and sums are spelled out with explicit
+// rounding (fmaf / fmul intrinsics, never contracted or reordered by the
+// compiler), so every kernel that applies it (source-major and band-major
+// window passes, lazy catch-up) rounds the same way.
+__device__ __forceinline__ float dot2_rn(float a, float x, float b, float y) {
+    return __fmaf_rn(a, x, __fmul_rn(b, y));
+}
+__device__ __forceinline__ float dot3_rn(float a, float x, float b, float y, float c, float z) {
+    return __fmaf_rn(a, x, __fmaf_rn(b, y, __fmul_rn(c, z)));
+}
+// plain window-end step w - step G and the gradient record g + G / B, one
+// rounding each (see dot2_rn)
+__device__ __forceinline__ float sgd_step(float w, float step, float G) { return __fmaf_rn(-step, G, w); }
+__device__ __forceinline__ float grad_add(float g, float inv_B, float G) { return __fmaf_rn(inv_B, G, g); }
 template <bool ALIF>
 __device__ __forceinline__ void apply_coef(const Net &n, const Coef &c, float &zbar, float &epsa,
                                            float &ebar, float &G) {
     if (ALIF) {
-        G += c.c0.x * zbar + c.c0.y * epsa + c.c0.z * ebar;
-        const float ea = c.c0.w * zbar + c.c1.x * epsa;
-        const float ee = c.c1.y * zbar + c.c1.z * epsa + n.kappaeU * ebar;
+        G = __fadd_rn(G, dot3_rn(c.c0.x, zbar, c.c0.y, epsa, c.c0.z, ebar));
+        const float ea = dot2_rn(c.c0.w, zbar, c.c1.x, epsa);
+        const float ee = dot3_rn(c.c1.y, zbar, c.c1.z, epsa, n.kappaeU, ebar);
         epsa = ea;
         ebar = ee;
     } else {
-        G += c.c0.x * zbar + c.c0.y * ebar;
-        ebar = c.c0.z * zbar + n.kappaeU * ebar;
+        G = __fadd_rn(G, dot2_rn(c.c0.x, zbar, c.c0.y, ebar));
+        ebar = dot2_rn(c.c0.z, zbar, n.kappaeU, ebar);
     }
-    zbar *= n.alphaU;
+    zbar = __fmul_rn(zbar, n.alphaU);
 }
 
 // Window transfer of one synapse state x = (zbar, eps_a, ebar) over window
@@ -440,20 +472,16 @@ template <bool ALIF>
 __device__ __forceinline__ void apply_window(const Net &n, long long j, int k, float &zbar,
                                              float &epsa, float &ebar, float &G) {
     const int slot = k & (n.RC - 1);
+    Coef cf;
     if (ALIF) {
         const float4 *c = reinterpret_cast<const float4 *>(n.coef) + ((long long)j * n.RC + slot) * 2;
-        const float4 c0 = c[0], c1 = c[1];   // (cz, ca, ce, maz), (maa, mez, mea, -)
-        G += c0.x * zbar + c0.y * epsa + c0.z * ebar;
-        const float ea = c0.w * zbar + c1.x * epsa;
-        const float ee = c1.y * zbar + c1.z * epsa + n.kappaeU * ebar;
-        epsa = ea;
-        ebar = ee;
+        cf.c0 = c[0];                        // (cz, ca, ce, maz), (maa, mez, mea, -)
+        cf.c1 = c[1];
     } else {
-        const float4 c = __ldg(reinterpret_cast<const float4 *>(n.coef) + (long long)j * n.RC + slot);
-        G += c.x * zbar + c.y * ebar;        // (cz, ce, mez, -)
-        ebar = c.z * zbar + n.kappaeU * ebar;
+        cf.c0 = __ldg(reinterpret_cast<const float4 *>(n.coef) + (long long)j * n.RC + slot);   // (cz, ce, mez, -)
+        cf.c1 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    zbar *= n.alphaU;
+    apply_coef<ALIF>(n, cf, zbar, epsa, ebar, G);
 }
 
 }  // namespace eprop

@@ -1,6 +1,8 @@
 // Host-side launch wrappers of the libeprop kernels (internal).
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
 
 namespace eprop {
 
@@ -37,6 +39,20 @@ void launch_adam(const Net &n, int sm_count, cudaStream_t st);
 int persistent_blocks(int sm_count);
 cudaError_t launch_persistent_steps(const Net &n, int T, GridBar *gb, int blocks, cudaStream_t st);
 void prepare_learning_signal_attributes();
+// band-major learning state (trace_kernel 4)
+int band_width(bool alif);
+size_t band_window_smem(const Net &n);
+void launch_band_count(const long long *row_ptr, const uint32_t *tgt_d, int S, int W, int nb, int *seg);
+void launch_band_chunk_sum(const int *seg, int S, int nb, int chunk, long long *part);
+void launch_band_chunk_scan(int *seg, int S, int nb, int chunk, const long long *off);
+void launch_band_tiles(const int *seg, const long long *band_tile0, int S, int nb, long long n_tiles, int4 *tiles,
+                       unsigned *flag);
+void launch_band_scatter(const Net &n, const float *w_src, uint32_t *bd_td, float *w_b);
+void launch_band_gather(const Net &n, int r0, int r1, long long q_begin, float *w_dst, float *g_dst,
+                        cudaStream_t st);
+void launch_window_band(const Net &n, int i_end, int sm_count, cudaStream_t st);
+void launch_deliver_band(const Net &n, int i, int grid_x, cudaStream_t st);
+void prepare_band_attributes();
 void launch_learning_signals(const float *fb, const float *E, float *L, int N, int U, int K, int B,
                              unsigned *err, cudaStream_t st);
 

@@ -301,11 +301,10 @@ __device__ __noinline__ float catch_up(const Net n, int j, int k0, int kW, float
 }
 
 template <bool ALIF>
-__device__ __noinline__ float scan_arrivals(const Net n, const uint32_t *words, int lo, int hi, int d,
-                                            long long qrow, float &ebar, float &epsa) {
+__device__ __noinline__ void scan_arrivals(const Net n, const uint32_t *words, int lo, int hi, int d,
+                                           long long qrow, float &G, float &ebar, float &epsa) {
     const int N = n.n_rec;
     const int mask = n.RW * 32 - 1;
-    float G = 0.f;
     int r = lo;
     while (r <= hi) {
         const int p = r & mask;
@@ -326,7 +325,6 @@ __device__ __noinline__ float scan_arrivals(const Net n, const uint32_t *words, 
         }
         r += span + 1;
     }
-    return G;
 }
 
 // Event-driven synapse trace + gradient of one update window (the metric
@@ -593,7 +591,7 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
                         }
                     }
                 } else {            // rows with more spikes than the cache holds
-                    G += scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - dl), r_end - dl, dl, qa + j, ebar, epsa);
+                    scan_arrivals<ALIF>(n, words, max(s, a0 + 1 - dl), r_end - dl, dl, qa + j, G, ebar, epsa);
                 }
                 {
                     const float wn = window_update(n, q, wv[u], G);
@@ -603,7 +601,7 @@ __global__ void __launch_bounds__(256, 2) trace_window_kernel(Net n, int i_end) 
                     store_trace(n.ebar, q, ebar, n.trace_type);
                     if (ALIF) store_trace(n.epsa, q, epsa, n.trace_type);
                 }
-                if (n.record_grad) n.grad[q] += n.inv_B * G;
+                if (n.record_grad) n.grad[q] = grad_add(n.grad[q], n.inv_B, G);
             }
         }
         __syncwarp();
@@ -931,8 +929,8 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
                         }
                     } else {
                         // rows with more spikes than the cache holds
-                        G += scan_arrivals<ALIF>(n, src_words_c(n, 0, d.src), max(d.row, a0 + 1 - dl),
-                                                 r_end - dl, dl, qa + j, ebar, epsa);
+                        scan_arrivals<ALIF>(n, src_words_c(n, 0, d.src), max(d.row, a0 + 1 - dl), r_end - dl, dl,
+                                            qa + j, G, ebar, epsa);
                     }
                 }
                 if (G != 0.f) {
@@ -940,13 +938,13 @@ __global__ void __launch_bounds__(256, MODE == kPassIdle ? 3 : 2) window_pass_ke
                         const float wn = window_update(n, d.q0 + idx, wv[u], G);
                         if (!n.adam) __stcs(wq + idx, wn);
                     } else {
-                        __stcs(wq + idx, wv[u] - step * G);
+                        __stcs(wq + idx, sgd_step(wv[u], step, G));
                     }
                 }
                 if (TB) __stcs(reinterpret_cast<uint16_t *>(n.ebar) + d.q0 + idx, float_to_trace16(ebar, TB));
                 else __stcs(reinterpret_cast<float *>(n.ebar) + d.q0 + idx, ebar);
                 if (ALIF) store_trace(n.epsa, d.q0 + idx, epsa, TB);
-                if (n.record_grad) gq[idx] += n.inv_B * G;
+                if (n.record_grad) gq[idx] = grad_add(gq[idx], n.inv_B, G);
             }
         }
         __syncwarp();
@@ -1130,8 +1128,8 @@ __global__ void __launch_bounds__(256) window_batched_kernel(Net n, int i_end) {
                         }
                     }
                 } else {            // rows with more spikes than the cache holds
-                    G += scan_arrivals<ALIF>(n, src_words_c(n, b, src), max(a0 + 1 - dl, 1), r_end - dl, dl,
-                                             qa + j, ebar, epsa);
+                    scan_arrivals<ALIF>(n, src_words_c(n, b, src), max(a0 + 1 - dl, 1), r_end - dl, dl, qa + j, G,
+                                        ebar, epsa);
                 }
                 store_trace(n.ebar, qb, ebar, TB);
                 if (ALIF) store_trace(n.epsa, qb, epsa, TB);
@@ -1144,10 +1142,10 @@ __global__ void __launch_bounds__(256) window_batched_kernel(Net n, int i_end) {
                     const float wn = window_update(n, q, w, Gf);
                     if (!n.adam) n.w[q] = wn;
                 } else {
-                    n.w[q] = w - step * Gf;
+                    n.w[q] = sgd_step(w, step, Gf);
                 }
             }
-            if (n.record_grad) n.grad[q] += n.inv_B * Gf;
+            if (n.record_grad) n.grad[q] = grad_add(n.grad[q], n.inv_B, Gf);
         }
         __syncwarp();
     }

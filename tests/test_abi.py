@@ -90,6 +90,9 @@ def _create(lib, cfg, n_src=5, nnz=0):
     (dict(batch=2, continuous=1), "batch > 1"),
     (dict(feedback=1), "feedback"),
     (dict(trace_kernel=2, update_interval=10), "batched trace kernel"),
+    (dict(trace_kernel=5), "trace_kernel must be 0..4"),
+    (dict(trace_kernel=4), "trace_kernel 4"),
+    (dict(trace_kernel=4, update_interval=10, optimizer=1), "trace_kernel 4"),
     (dict(tau_m=0.0), "time constants"),
 ])
 def test_invalid_config_is_rejected_before_any_cuda_call(lib, kw, msg):

@@ -316,7 +316,7 @@ def test_sparse_replica_single_window_window_kernel():
 
 # state-carrying window forms: 1 = lazy (catch-up at the next arrival),
 # 3 = dense (every synapse advanced at every window end)
-STATE_KERNELS = [pytest.param(1, id="lazy"), pytest.param(3, id="dense")]
+STATE_KERNELS = [pytest.param(1, id="lazy"), pytest.param(3, id="dense"), pytest.param(4, id="band")]
 
 
 def test_dense_form_needs_carried_state():
