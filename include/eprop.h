@@ -161,7 +161,15 @@ typedef struct eprop_config {
                                  every synapse is advanced at every window
                                  end; with batch > 1 every synapse carries
                                  one trace per sample and the weight steps
-                                 with the batch mean                         */
+                                 with the batch mean; 4 the dense window pass
+                                 with the synapse records kept by target band
+                                 (12288 LIF / 4608 ALIF targets, a band's
+                                 window coefficients in shared memory): same
+                                 results bit for bit as 3; needs carried
+                                 state, batch 1, optimizer 0 and free synapse
+                                 signs (sign_mask & 3 == 0), else
+                                 EPROP_EINVAL; eprop_read_weights_grads
+                                 returns the creation order                  */
     int32_t blocks_per_sm;    /* CTAs per SM of the row kernels; 0 = 2        */
     int32_t profile;          /* 1: time the synapse-trace kernels of every
                                  window with CUDA events (see eprop_stats)    */

@@ -224,13 +224,17 @@ static eprop_status build_band(eprop_net *net) {
     eprop::prepare_band_attributes();
     const int S = n.n_src, N = n.n_rec;
     const int Wmax = eprop::band_width(n.alif != 0);
+    // the kernels use the band width as a compile-time constant
     const int nb = (N + Wmax - 1) / Wmax;
-    const int W = (N + nb - 1) / nb;
+    const int W = Wmax;
     n.band = 1;
     n.band_w = W;
     n.nb = nb;
-    n.rr_stride = (4 * n.D + 2 + 16 + 15) & ~15;
-    n.rr_cap = (n.rr_stride - 4 * n.D - 2) / 2;
+    // row record: zbar per delay, arrival range per delay, >= 8 spike steps
+    n.rr_stride = (6 * n.D + 16 + 15) & ~15;
+    n.rr_cap = (n.rr_stride - 6 * n.D) / 2;
+    n.band_stages = eprop::band_stages_fit(n.alif != 0, n.rr_stride);
+    n.band_stage_b = eprop::band_stage_size(n.alif != 0, n.rr_stride);
     std::vector<DevAlloc> tmp;
     auto nomem = [&]() {
         free_all(tmp);

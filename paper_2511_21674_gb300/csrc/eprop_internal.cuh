@@ -150,6 +150,8 @@ struct Net {
     int band;                 // 1: band-major synapse records
     int band_w, nb;           // targets per band, number of bands
     int rr_stride, rr_cap;    // bytes per row record, spikes kept per record
+    int band_stages;          // shared-memory stages of the band window kernel
+    unsigned band_stage_b;    // bytes per stage
     long long nnz_b;          // band-major records incl. padding (multiple of kBandTile)
     long long n_tiles;        // nnz_b / kBandTile
     const uint32_t *bd_td;    // [nnz_b] (target - band start) | (delay - 1) << 14 | (row - tile row0) << 17
@@ -161,6 +163,8 @@ struct Net {
 
 // Band-major form: records of one band (a range of band_w targets) are
 // contiguous, by source row, padded to whole tiles of kBandTile records.
+// two records per consumer thread of the band window kernel (16 consumer
+// warps); a tile's 4-byte and 2-byte streams start on 16-byte boundaries
 constexpr int kBandTile = 1024;
 constexpr uint32_t kBandPad = 0xFFFFFFFFu;     // bd_td of a padding record
 

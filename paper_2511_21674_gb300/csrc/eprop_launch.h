@@ -42,6 +42,8 @@ void prepare_learning_signal_attributes();
 // band-major learning state (trace_kernel 4)
 int band_width(bool alif);
 size_t band_window_smem(const Net &n);
+int band_stages_fit(bool alif, int rr_stride);
+uint32_t band_stage_size(bool alif, int rr_stride);
 void launch_band_count(const long long *row_ptr, const uint32_t *tgt_d, int S, int W, int nb, int *seg);
 void launch_band_chunk_sum(const int *seg, int S, int nb, int chunk, long long *part);
 void launch_band_chunk_scan(int *seg, int S, int nb, int chunk, const long long *off);

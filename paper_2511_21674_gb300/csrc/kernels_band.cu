@@ -36,7 +36,8 @@ namespace eprop {
 
 namespace {
 
-constexpr int kBandStages = 4;
+constexpr int kBandStagesMax = 8;      // stages of the window kernel (as many as fit)
+constexpr size_t kBandSmem = 227 * 1024 - 1024;   // dynamic shared memory of the window kernel, at most
 constexpr int kRowCap = 128;             // row records staged per tile
 constexpr int kBandRowBits = 15;         // row - tile row0 < 2^15
 
@@ -57,8 +58,9 @@ __device__ __forceinline__ void bulk_g2s_keep(void *dst, const void *src, uint32
 }
 
 __host__ __device__ constexpr int band_coef_floats(bool alif) { return alif ? 7 : 3; }
-__host__ __device__ constexpr size_t band_stage_bytes(bool alif) {
-    return (size_t)4096 * (alif ? 4 : 3) + (size_t)kRowCap * 64;
+// one stage: records, weights, trace(s) of a tile, then its staged row records
+__host__ __device__ inline uint32_t band_stage_bytes(bool alif, int rr_stride) {
+    return (uint32_t)((4096 * (alif ? 4 : 3) + kRowCap * rr_stride + 127) & ~127);
 }
 
 // ------------------------------------------------------------- layout build
@@ -205,12 +207,16 @@ __global__ void band_gather_kernel(Net n, int r0, int r1, long long q_begin, flo
 
 // Row record of every source for the window (a0, r_end]: zbar at a0 of the
 // row's delay-d synapses for d = 1..D (RowInfo.zbar_a0, the value the
-// source-major pass uses), then the number of the row's spikes in
-// [a0 + 1 - D, r_end - 1] and, if at most rr_cap, their steps - s_lo.
+// source-major pass uses); per delay d the range [c0, ce) of the row's
+// spike list whose delay-d arrivals fall in the window (packed c0 | ce << 8,
+// 0xFFFF when the row has more spikes than the record keeps); the steps -
+// s_lo of the row's spikes in [a0 + 1 - D, r_end - 1] (at most rr_cap).
+// Layout: float zb[D] | u16 range[D] | u16 steps[rr_cap].
 __global__ void band_rows_kernel(Net n, int i_end) {
     const int r_end = run_step_b(n, i_end);
     const int a0 = r_end - n.U;
-    const int s_lo = a0 + 1 - n.D, s_hi = r_end - 1;
+    const int D = n.D;
+    const int s_lo = a0 + 1 - D, s_hi = r_end - 1;
     const int src = blockIdx.x * blockDim.x + threadIdx.x;
     if (src >= n.n_src) return;
     const uint32_t *words = words_b(n, src);
@@ -218,9 +224,9 @@ __global__ void band_rows_kernel(Net n, int i_end) {
     float *zb = reinterpret_cast<float *>(rec);
     const int at = n.anchor_t[src];
     const float az = n.anchor_z[src];
-    for (int d = 1; d <= n.D; ++d) zb[d - 1] = row_info(n, words, at, az, a0, d, false).zbar_a0;
-    unsigned short *ns = reinterpret_cast<unsigned short *>(rec + 4 * n.D);
-    unsigned short *sp = ns + 1;
+    for (int d = 1; d <= D; ++d) zb[d - 1] = row_info(n, words, at, az, a0, d, false).zbar_a0;
+    unsigned short *rg = reinterpret_cast<unsigned short *>(rec + 4 * D);
+    unsigned short *sp = rg + D;
     const int mask = n.RW * 32 - 1;
     int cnt = 0;
     int r = s_lo < 1 ? 1 : s_lo;
@@ -237,7 +243,20 @@ __global__ void band_rows_kernel(Net n, int i_end) {
         }
         r += span + 1;
     }
-    *ns = (unsigned short)cnt;
+    for (int d = 1; d <= D; ++d) {
+        if (cnt > n.rr_cap) {
+            rg[d - 1] = 0xFFFFu;
+            continue;
+        }
+        // arrival s + d in (a0, r_end]  <=>  D <= step + d <= U + D - 1
+        int c0 = 0, ce = 0;
+        for (int c = 0; c < cnt; ++c) {
+            const int v = (int)sp[c] + d;
+            c0 += v < D;
+            ce += v <= n.U + D - 1;
+        }
+        rg[d - 1] = (unsigned short)(c0 | (ce << 8));
+    }
 }
 
 template <bool ALIF>
@@ -274,8 +293,9 @@ __device__ __noinline__ void band_scan(const Net n, const uint32_t *words, int l
 
 // ------------------------------------------------------------ window pass
 
-constexpr int kBandConsumers = 16;                     // consumer warps (512 threads)
+constexpr int kBandConsumers = 16;                     // consumer warps (512 threads, two records each)
 constexpr int kBandU = kBandTile / (kBandConsumers * 32);   // records per thread and tile
+constexpr int kBandWLif = 12288, kBandWAlif = 4608;  // targets per band (coefficients in shared memory)
 
 __device__ __forceinline__ void band_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -283,105 +303,113 @@ __device__ __forceinline__ void band_arrive(uint64_t *bar) {
 
 // A tile's per-thread state between its two phases: the records read from
 // shared memory and the table entries of the first two arrivals in flight.
-// rro: byte offset of the record's row summary in the stage, or -1 - (row
-// index in the tile) when the tile spans more rows than are staged.
+// rng: the record's arrival range (c0 | ce << 8, 0xFFFF: scan the bits);
+// rro: byte offset of its row record in the stage, or -1 - (row index in the
+// tile) when the tile spans more rows than are staged.
 template <bool ALIF>
 struct BandRegs {
-    uint32_t td[kBandU];
+    uint32_t td[kBandU], rng[kBandU];
     float wv[kBandU], zr[kBandU], eb[kBandU], ep[kBandU];
     float4 t0[kBandU], t1[kBandU];
-    int ns[kBandU], c0[kBandU], rro[kBandU];
+    int rro[kBandU];
     bool live[kBandU];
 };
 
 struct BandCtx {
-    int a0, r_end, s_lo, D, N, W, rs, rcap;
-    long long qa;
+    int a0, r_end, s_lo, D, N, rs;
+    const float *qp;                             // table entries of step a0 + 1
     float step;
 };
 
+// table entry of arrival step a of target j
 template <bool ALIF>
-__device__ __forceinline__ const unsigned char *band_rec(const Net &n, const BandCtx &x, const unsigned char *s_rr,
-                                                         int row0, int rro) {
-    return rro >= 0 ? s_rr + rro : n.rrec + (long long)(row0 - 1 - rro) * x.rs;
+__device__ __forceinline__ float4 band_entry(const BandCtx &x, int a, int j) {
+    const long long e = (long long)(a - x.a0 - 1) * x.N + j;
+    if (ALIF) return __ldg(reinterpret_cast<const float4 *>(x.qp) + e);
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(x.qp) + e);
+    return make_float4(t.x, t.y, 0.f, 0.f);
 }
 
 // phase 1 of a tile: records, weight, traces and row summary into
 // registers; the table loads of the first two arrivals are issued
 template <bool ALIF, int TB>
-__device__ __forceinline__ void band_phase1(const Net &n, const BandCtx &x, const unsigned char *s, int4 dk, int ct,
+__device__ __forceinline__ void band_phase1(const Net &n, const BandCtx &x, uint32_t soff, int4 dk, int ct,
                                             BandRegs<ALIF> &r) {
+    // stage pointers derived from the dynamic shared array itself, so the
+    // compiler emits shared-memory loads
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const unsigned char *s = dsm + soff;
+    constexpr int W = ALIF ? kBandWAlif : kBandWLif;
     const uint32_t *s_td = reinterpret_cast<const uint32_t *>(s);
     const float *s_w = reinterpret_cast<const float *>(s + 4096);
     const unsigned char *s_rr = s + (ALIF ? 16384 : 12288);
     const int rows_st = min(dk.z, kRowCap);
-    const int jb = dk.w * x.W;
+    const int jb = dk.w * W;
 #pragma unroll
     for (int u = 0; u < kBandU; ++u) {
         const int idx = ct + kBandConsumers * 32 * u;
-        r.td[u] = s_td[idx];
+        const uint32_t td = s_td[idx];
+        r.td[u] = td;
         r.live[u] = false;
-        r.c0[u] = -1;
-        r.ns[u] = 0;
-        r.rro[u] = 0;
-        r.t0[u] = r.t1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.zr[u] = r.eb[u] = r.ep[u] = r.wv[u] = 0.f;
-        if (r.td[u] == kBandPad) continue;
-        const int tl = (int)(r.td[u] & 0x3FFFu);
-        const int dl = (int)((r.td[u] >> 14) & 7u) + 1;
-        const int rit = (int)(r.td[u] >> 17);
-        const unsigned short *sp;
+        if (td == kBandPad) continue;
+        const int tl = (int)(td & 0x3FFFu);
+        const int dl = (int)((td >> 14) & 7u) + 1;
+        const int rit = (int)(td >> 17);
+        uint32_t rng;
+        int s1 = 0, s2 = 0;
         if (rit < rows_st) {
             const unsigned char *rec = s_rr + rit * x.rs;
             r.rro[u] = rit * x.rs;
             r.zr[u] = reinterpret_cast<const float *>(rec)[dl - 1];
-            sp = reinterpret_cast<const unsigned short *>(rec + 4 * x.D);
+            const unsigned short *rg = reinterpret_cast<const unsigned short *>(rec + 4 * x.D);
+            rng = rg[dl - 1];
+            const int c0 = (int)(rng & 0xFFu), ce = (int)(rng >> 8);
+            if (rng != 0xFFFFu && ce > c0) s1 = rg[x.D + c0];
+            if (rng != 0xFFFFu && ce > c0 + 1) s2 = rg[x.D + c0 + 1];
         } else {
             const unsigned char *rec = n.rrec + (long long)(dk.y + rit) * x.rs;
             r.rro[u] = -1 - rit;
             r.zr[u] = reinterpret_cast<const float *>(rec)[dl - 1];
-            sp = reinterpret_cast<const unsigned short *>(rec + 4 * x.D);
+            const unsigned short *rg = reinterpret_cast<const unsigned short *>(rec + 4 * x.D);
+            rng = rg[dl - 1];
+            const int c0 = (int)(rng & 0xFFu), ce = (int)(rng >> 8);
+            if (rng != 0xFFFFu && ce > c0) s1 = rg[x.D + c0];
+            if (rng != 0xFFFFu && ce > c0 + 1) s2 = rg[x.D + c0 + 1];
         }
-        r.ns[u] = sp[0];
-        ++sp;
+        r.rng[u] = rng;
         r.wv[u] = s_w[idx];
         if (TB) r.eb[u] = trace16_to_float(reinterpret_cast<const uint16_t *>(s + 8192)[idx], TB);
         else r.eb[u] = reinterpret_cast<const float *>(s + 8192)[idx];
+        r.ep[u] = 0.f;
         if (ALIF) {
             if (TB) r.ep[u] = trace16_to_float(reinterpret_cast<const uint16_t *>(s + 12288)[idx], TB);
             else r.ep[u] = reinterpret_cast<const float *>(s + 12288)[idx];
         }
-        r.live[u] = r.ns[u] > 0 || r.zr[u] != 0.f || r.eb[u] != 0.f || r.ep[u] != 0.f;
-        if (r.ns[u] > 0 && r.ns[u] <= x.rcap) {
-            // first spike whose delay-dl arrival is in the window (a > a0)
-            int cc = 0;
-            while (cc < r.ns[u] && (int)sp[cc] + dl < x.D) ++cc;
-            const int a1 = cc < r.ns[u] ? x.s_lo + (int)sp[cc] + dl : x.r_end + 1;
-            if (a1 <= x.r_end) {
-                r.c0[u] = cc;
-                r.t0[u] = band_table<ALIF>(n, x.qa + (long long)a1 * x.N + jb + tl);
-                const int a2 = cc + 1 < r.ns[u] ? x.s_lo + (int)sp[cc + 1] + dl : x.r_end + 1;
-                if (a2 <= x.r_end) r.t1[u] = band_table<ALIF>(n, x.qa + (long long)a2 * x.N + jb + tl);
-            }
-        }
+        const int na = rng == 0xFFFFu ? 0 : (int)(rng >> 8) - (int)(rng & 0xFFu);
+        r.live[u] = na > 0 || rng == 0xFFFFu || r.zr[u] != 0.f || r.eb[u] != 0.f || r.ep[u] != 0.f;
+        if (na >= 1) r.t0[u] = band_entry<ALIF>(x, x.s_lo + s1 + dl, jb + tl);
+        if (na >= 2) r.t1[u] = band_entry<ALIF>(x, x.s_lo + s2 + dl, jb + tl);
     }
 }
 
 // phase 2 of a tile: the window transfer with the band's coefficients, the
 // arrivals in ascending order (the first two from phase 1), the stores
 template <bool ALIF, int TB>
-__device__ __forceinline__ void band_phase2(const Net &n, const BandCtx &x, const float *cf, const unsigned char *s,
-                                            long long q0, int4 dk, int ct, const BandRegs<ALIF> &r) {
-    const int jb = dk.w * x.W;
-    const int W = x.W;
+__device__ __forceinline__ void band_phase2(const Net &n, const BandCtx &x, uint32_t soff, long long q0, int4 dk, int ct,
+                                            const BandRegs<ALIF> &r) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const float *cf = reinterpret_cast<const float *>(dsm);
+    const unsigned char *s = dsm + soff;
+    constexpr int W = ALIF ? kBandWAlif : kBandWLif;
+    const int jb = dk.w * W;
     const unsigned char *s_rr = s + (ALIF ? 16384 : 12288);
 #pragma unroll
     for (int u = 0; u < kBandU; ++u) {
         if (!r.live[u]) continue;
         const int idx = ct + kBandConsumers * 32 * u;
-        const int tl = (int)(r.td[u] & 0x3FFFu);
-        const int dl = (int)((r.td[u] >> 14) & 7u) + 1;
-        const int j = jb + tl;
+        const uint32_t td = r.td[u];
+        const int tl = (int)(td & 0x3FFFu);
+        const int dl = (int)((td >> 14) & 7u) + 1;
         Coef co;
         if (ALIF) {
             co.c0 = make_float4(cf[tl], cf[W + tl], cf[2 * W + tl], cf[3 * W + tl]);
@@ -392,50 +420,44 @@ __device__ __forceinline__ void band_phase2(const Net &n, const BandCtx &x, cons
         }
         float G = 0.f, zbar = r.zr[u], ebar = r.eb[u], epsa = r.ep[u];
         apply_coef<ALIF>(n, co, zbar, epsa, ebar, G);
-        const int ns = r.ns[u];
-        if (ns > 0) {
-            if (ns <= x.rcap) {
-                const int c0 = r.c0[u];
-                if (c0 >= 0) {
-                    G += r.t0[u].x;
-                    ebar += r.t0[u].y;
-                    if (ALIF) epsa += r.t0[u].z;
-                    if (c0 + 1 < ns) {
-                        const unsigned short *sp =
-                            reinterpret_cast<const unsigned short *>(band_rec<ALIF>(n, x, s_rr, dk.y, r.rro[u]) +
-                                                                     4 * x.D) + 1;
-                        if (x.s_lo + (int)sp[c0 + 1] + dl <= x.r_end) {
-                            G += r.t1[u].x;
-                            ebar += r.t1[u].y;
-                            if (ALIF) epsa += r.t1[u].z;
-                            // further arrivals: four table loads in flight, summed in order
-                            for (int cc = c0 + 2; cc < ns; cc += 4) {
-                                float4 t[4];
-                                bool v[4];
-#pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    const int a = cc + q < ns ? x.s_lo + (int)sp[cc + q] + dl : x.r_end + 1;
-                                    v[q] = a <= x.r_end;
-                                    t[q] = v[q] ? band_table<ALIF>(n, x.qa + (long long)a * x.N + j)
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                                }
-#pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    if (v[q]) {
-                                        G += t[q].x;
-                                        ebar += t[q].y;
-                                        if (ALIF) epsa += t[q].z;
-                                    }
-                                if (!v[3]) break;
-                            }
-                        }
-                    }
-                }
-            } else {
-                // rows with more spikes than the record holds
-                const int row = dk.y + (int)(r.td[u] >> 17);
-                band_scan<ALIF>(n, words_b(n, row), x.a0 + 1 - dl, x.r_end - dl, dl, x.qa + j, G, ebar, epsa);
+        const uint32_t rng = r.rng[u];
+        if (rng != 0xFFFFu) {
+            const int c0 = (int)(rng & 0xFFu), ce = (int)(rng >> 8);
+            if (ce > c0) {
+                G += r.t0[u].x;
+                ebar += r.t0[u].y;
+                if (ALIF) epsa += r.t0[u].z;
             }
+            if (ce > c0 + 1) {
+                G += r.t1[u].x;
+                ebar += r.t1[u].y;
+                if (ALIF) epsa += r.t1[u].z;
+            }
+            if (ce > c0 + 2) {
+                // further arrivals: four table loads in flight, summed in order
+                const int ro = r.rro[u];
+                const unsigned char *rec = ro >= 0 ? s_rr + ro : n.rrec + (long long)(dk.y - 1 - ro) * x.rs;
+                const unsigned short *sp = reinterpret_cast<const unsigned short *>(rec + 4 * x.D) + x.D;
+                for (int cc = c0 + 2; cc < ce; cc += 4) {
+                    float4 t[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        t[q] = cc + q < ce ? band_entry<ALIF>(x, x.s_lo + (int)sp[cc + q] + dl, jb + tl)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (cc + q < ce) {
+                            G += t[q].x;
+                            ebar += t[q].y;
+                            if (ALIF) epsa += t[q].z;
+                        }
+                }
+            }
+        } else {
+            // rows with more spikes than the record holds
+            const int row = dk.y + (int)(td >> 17);
+            band_scan<ALIF>(n, words_b(n, row), x.a0 + 1 - dl, x.r_end - dl, dl, (long long)(-x.a0 - 1) * x.N + jb + tl,
+                            G, ebar, epsa);
         }
         const long long q = q0 + idx;
         if (G != 0.f) __stcs(n.w + q, sgd_step(r.wv[u], x.step, G));
@@ -450,8 +472,7 @@ __device__ __forceinline__ void band_phase2(const Net &n, const BandCtx &x, cons
 struct BandSm {
     uint64_t *full, *empty, *bandbar;
     int4 *desc;
-    unsigned char *stg;
-    float *cf;
+    uint32_t stg;                                // byte offset of stage 0 in the dynamic shared array
 };
 
 // consumers: meet at the band barrier (bounded); false when a wait gave up
@@ -470,8 +491,8 @@ __device__ __forceinline__ bool band_sync(const Net &n, const BandSm &m, int &bp
 template <bool ALIF, int TB>
 __device__ __forceinline__ bool band_wstep(const Net &n, const BandCtx &x, const BandSm &m, int c, int4 &dk,
                                            int &cur_band, int &bphase, BandRegs<ALIF> &cur, BandRegs<ALIF> &nxt) {
-    constexpr int S = kBandStages;
-    constexpr size_t kStage = band_stage_bytes(ALIF);
+    const int S = n.band_stages;
+    const uint32_t kStage = n.band_stage_b;
     const int ct = threadIdx.x;
     const int k = c % S, k1 = (c + 1) % S;
     if (!mbar_wait(&m.full[k1], (uint32_t)(((c + 1) / S) & 1), n.err_flags)) return false;
@@ -480,24 +501,26 @@ __device__ __forceinline__ bool band_wstep(const Net &n, const BandCtx &x, const
     if (dk.w != cur_band) {
         // every consumer warp is past the previous band's tiles
         if (!band_sync(n, m, bphase)) return false;
-        const int j0 = dk.w * x.W;
-        const int jn = min(x.W, x.N - j0);
-        float *cf = m.cf;
+        constexpr int W = ALIF ? kBandWAlif : kBandWLif;
+        const int j0 = dk.w * W;
+        const int jn = min(W, x.N - j0);
+        extern __shared__ __align__(128) unsigned char dsm[];
+        float *cf = reinterpret_cast<float *>(dsm);
         for (int jj = ct; jj < jn; jj += kBandConsumers * 32) {
             if (ALIF) {
                 const float4 *q = reinterpret_cast<const float4 *>(n.coef) + 2LL * (j0 + jj);
                 const float4 c0 = __ldg(q), c1 = __ldg(q + 1);
-                cf[jj] = c0.x; cf[x.W + jj] = c0.y; cf[2 * x.W + jj] = c0.z; cf[3 * x.W + jj] = c0.w;
-                cf[4 * x.W + jj] = c1.x; cf[5 * x.W + jj] = c1.y; cf[6 * x.W + jj] = c1.z;
+                cf[jj] = c0.x; cf[W + jj] = c0.y; cf[2 * W + jj] = c0.z; cf[3 * W + jj] = c0.w;
+                cf[4 * W + jj] = c1.x; cf[5 * W + jj] = c1.y; cf[6 * W + jj] = c1.z;
             } else {
                 const float4 c0 = __ldg(reinterpret_cast<const float4 *>(n.coef) + (j0 + jj));
-                cf[jj] = c0.x; cf[x.W + jj] = c0.y; cf[2 * x.W + jj] = c0.z;
+                cf[jj] = c0.x; cf[W + jj] = c0.y; cf[2 * W + jj] = c0.z;
             }
         }
         if (!band_sync(n, m, bphase)) return false;
         cur_band = dk.w;
     }
-    band_phase2<ALIF, TB>(n, x, m.cf, m.stg + k * kStage, (long long)dk.x * kBandTile, dk, ct, cur);
+    band_phase2<ALIF, TB>(n, x, m.stg + k * kStage, (long long)dk.x * kBandTile, dk, ct, cur);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) band_arrive(&m.empty[k]);
     dk = dn;
@@ -508,7 +531,7 @@ constexpr int kBandThreadsAll = (kBandConsumers + 1) * 32;   // consumers + one 
 
 // Warp-specialised window pass.  One CTA per SM: a producer warp streams
 // the CTA's tiles (round-robin over the grid, so all CTAs move through the
-// bands together) into kBandStages shared-memory stages with bulk copies
+// bands together) into shared-memory stages (as many as fit) with bulk copies
 // (records, weights, traces and the row records of the rows a tile spans),
 // 16 consumer warps process every tile, each its 64 records.  A consumer
 // warp is software-pipelined by one tile (phase 1 of tile c + 1, with the
@@ -520,25 +543,24 @@ constexpr int kBandThreadsAll = (kBandConsumers + 1) * 32;   // consumers + one 
 template <bool ALIF, int TB>
 __global__ void __launch_bounds__(kBandThreadsAll, 1) window_band_kernel(Net n, int i_end) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ uint64_t full[kBandStages], empty[kBandStages], bandbar;
-    __shared__ int4 desc[kBandStages];           // (tile, first row, rows spanned, band); tile -1: none
+    __shared__ uint64_t full[kBandStagesMax], empty[kBandStagesMax], bandbar;
+    __shared__ int4 desc[kBandStagesMax];        // (tile, first row, rows spanned, band); tile -1: none
     constexpr int NF = band_coef_floats(ALIF);
-    constexpr int S = kBandStages;
-    constexpr size_t kStage = band_stage_bytes(ALIF);
-    constexpr uint32_t kTrB = TB ? 2048u : 4096u;
+    const int S = n.band_stages;
+    const uint32_t kStage = n.band_stage_b;
+    constexpr uint32_t kRecB = kBandTile * 4u;             // bytes of a tile's 4-byte stream
+    constexpr uint32_t kTrB = TB ? kBandTile * 2u : kRecB;
+    constexpr int W = ALIF ? kBandWAlif : kBandWLif;
     BandCtx x;
-    x.W = n.band_w;
     x.D = n.D;
     x.N = n.n_rec;
     x.r_end = run_step_b(n, i_end);
     x.a0 = x.r_end - n.U;
     x.s_lo = x.a0 + 1 - x.D;
-    x.qa = (long long)(-x.a0 - 1) * x.N;       // table index = qa + a * N + j
+    x.qp = n.qp;
     x.step = n.lr * n.inv_B;
     x.rs = n.rr_stride;
-    x.rcap = n.rr_cap;
-    float *cf = reinterpret_cast<float *>(dsm);
-    unsigned char *stg = dsm + (((size_t)NF * x.W * 4 + 127) & ~(size_t)127);
+    unsigned char *stg = dsm + (((size_t)NF * W * 4 + 127) & ~(size_t)127);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) {
@@ -572,9 +594,9 @@ __global__ void __launch_bounds__(kBandThreadsAll, 1) window_band_kernel(Net n, 
             unsigned char *s = stg + k * kStage;
             const long long q0 = t * kBandTile;
             desc[k] = make_int4((int)t, cur.x, cur.y, cur.z);
-            mbar_expect_tx(&full[k], 8192u + kTrB * (ALIF ? 2u : 1u) + rrb);
-            bulk_g2s(s, n.bd_td + q0, 4096u, &full[k]);
-            bulk_g2s(s + 4096, n.w + q0, 4096u, &full[k]);
+            mbar_expect_tx(&full[k], 2u * kRecB + kTrB * (ALIF ? 2u : 1u) + rrb);
+            bulk_g2s(s, n.bd_td + q0, kRecB, &full[k]);
+            bulk_g2s(s + 4096, n.w + q0, kRecB, &full[k]);
             bulk_g2s(s + 8192, reinterpret_cast<const unsigned char *>(n.ebar) + q0 * (TB ? 2 : 4), kTrB, &full[k]);
             if (ALIF)
                 bulk_g2s(s + 12288, reinterpret_cast<const unsigned char *>(n.epsa) + q0 * (TB ? 2 : 4), kTrB,
@@ -595,14 +617,13 @@ __global__ void __launch_bounds__(kBandThreadsAll, 1) window_band_kernel(Net n, 
     m.empty = empty;
     m.bandbar = &bandbar;
     m.desc = desc;
-    m.stg = stg;
-    m.cf = cf;
+    m.stg = (uint32_t)(stg - dsm);
     int cur_band = -1, bphase = 0;
     if (!mbar_wait(&full[0], 0u, n.err_flags)) return;
     int4 dk = desc[0];
     if (dk.x < 0) return;
     BandRegs<ALIF> X, Y;
-    band_phase1<ALIF, TB>(n, x, stg, dk, threadIdx.x, X);
+    band_phase1<ALIF, TB>(n, x, m.stg, dk, threadIdx.x, X);
     for (int c = 0;; c += 2) {
         if (!band_wstep<ALIF, TB>(n, x, m, c, dk, cur_band, bphase, X, Y)) break;
         if (!band_wstep<ALIF, TB>(n, x, m, c + 1, dk, cur_band, bphase, Y, X)) break;
@@ -716,12 +737,23 @@ __global__ void __launch_bounds__(256, 4) deliver_band_kernel(Net n, int i) {
 
 // ------------------------------------------------------------- launchers
 
-int band_width(bool alif) { return alif ? 4608 : 12288; }
+int band_width(bool alif) { return alif ? kBandWAlif : kBandWLif; }
 
+// dynamic shared memory of the window kernel for n.band_stages stages
 size_t band_window_smem(const Net &n) {
     const int nf = band_coef_floats(n.alif != 0);
-    return (((size_t)nf * n.band_w * 4 + 127) & ~(size_t)127) + kBandStages * band_stage_bytes(n.alif != 0);
+    return (((size_t)nf * band_width(n.alif != 0) * 4 + 127) & ~(size_t)127) +
+           (size_t)n.band_stages * band_stage_bytes(n.alif != 0, n.rr_stride);
 }
+
+// stages that fit beside the coefficients (kBandSmem bytes in all)
+int band_stages_fit(bool alif, int rr_stride) {
+    const size_t coef = ((size_t)band_coef_floats(alif) * band_width(alif) * 4 + 127) & ~(size_t)127;
+    const int s = (int)((kBandSmem - coef) / band_stage_bytes(alif, rr_stride));
+    return s < kBandStagesMax ? s : kBandStagesMax;
+}
+
+uint32_t band_stage_size(bool alif, int rr_stride) { return band_stage_bytes(alif, rr_stride); }
 
 static int band_walk_blocks(long long rows) {
     long long b = (rows + 3) / 4;
@@ -783,16 +815,13 @@ void prepare_band_attributes() {
     cudaFuncSetAttribute(band_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(band_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(band_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    const int lif = (int)((((size_t)3 * band_width(false) * 4 + 127) & ~(size_t)127) +
-                          kBandStages * band_stage_bytes(false));
-    const int alif = (int)((((size_t)7 * band_width(true) * 4 + 127) & ~(size_t)127) +
-                           kBandStages * band_stage_bytes(true));
-    cudaFuncSetAttribute(window_band_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lif);
-    cudaFuncSetAttribute(window_band_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lif);
-    cudaFuncSetAttribute(window_band_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lif);
-    cudaFuncSetAttribute(window_band_kernel<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, alif);
-    cudaFuncSetAttribute(window_band_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, alif);
-    cudaFuncSetAttribute(window_band_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, alif);
+    const int w = (int)kBandSmem;
+    cudaFuncSetAttribute(window_band_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, w);
+    cudaFuncSetAttribute(window_band_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, w);
+    cudaFuncSetAttribute(window_band_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, w);
+    cudaFuncSetAttribute(window_band_kernel<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, w);
+    cudaFuncSetAttribute(window_band_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, w);
+    cudaFuncSetAttribute(window_band_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, w);
 }
 
 }  // namespace eprop
