@@ -636,16 +636,17 @@ __global__ void __launch_bounds__(kBandThreadsAll, 1) window_band_kernel(Net n, 
 // of 32 bands (lane l: band 32 g + l), with the inclusive prefix of their
 // lengths over the lanes.
 struct BandItem {
-    int src, g, incl, cnt, total;
+    int src, g, part, incl, cnt, total;
     long long base;
 };
 
-__device__ __forceinline__ BandItem band_item(const Net &n, const int *ids, const BucketScan &bs, int ng,
+__device__ __forceinline__ BandItem band_item(const Net &n, const int *ids, const BucketScan &bs, int ng, int np,
                                               long long it) {
     const int lane = threadIdx.x & 31;
     BandItem m;
-    const int row = (int)(it / ng);
-    m.g = (int)(it % ng);
+    const int row = (int)(it / ((long long)ng * np));
+    m.g = (int)((it / np) % ng);
+    m.part = (int)(it % np);
     m.src = bucket_entry(n, ids, bs, row);
     const int b = m.g * 32 + lane;
     m.cnt = 0;
@@ -659,9 +660,11 @@ __device__ __forceinline__ BandItem band_item(const Net &n, const int *ids, cons
 }
 
 // Spikes of call step i (batch 1) into the input ring.  Work items: (spiking
-// row, group of 32 bands), dealt round-robin to the warps; the next item's
-// segment bounds are loaded while the current one is delivered, four
-// records per lane in flight.
+// row, group of 32 bands, part), dealt round-robin to the warps; with few
+// band groups a group's records are split into parts (as the source-major
+// delivery splits rows), so a step's few spiking rows still spread over the
+// grid.  The next item's segment bounds are loaded while the current one
+// is delivered, four records per lane in flight.
 __global__ void __launch_bounds__(256, 4) deliver_band_kernel(Net n, int i) {
     __shared__ unsigned long long ev_block;
     __shared__ long long ring_off[kMaxDelay + 1];
@@ -678,15 +681,16 @@ __global__ void __launch_bounds__(256, 4) deliver_band_kernel(Net n, int i) {
     const int *ids = n.list_ids + li * n.list_cap;
     const BucketScan bs = bucket_scan(n.list_cnt + li);
     const int ng = (n.nb + 31) >> 5;
-    const long long items = (long long)bs.total * ng;
+    const int np = ng == 1 ? 4 : (ng == 2 ? 2 : 1);   // parts per band group
+    const long long items = (long long)bs.total * ng * np;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     unsigned long long ev = 0ULL;
     BandItem nx;
-    if (gw < items) nx = band_item(n, ids, bs, ng, gw);
+    if (gw < items) nx = band_item(n, ids, bs, ng, np, gw);
     for (long long it = gw; it < items; it += nw) {
         BandItem m = nx;
-        if (it + nw < items) nx = band_item(n, ids, bs, ng, it + nw);
+        if (it + nw < items) nx = band_item(n, ids, bs, ng, np, it + nw);
         int incl = m.cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -694,9 +698,11 @@ __global__ void __launch_bounds__(256, 4) deliver_band_kernel(Net n, int i) {
             if (lane >= o) incl += t;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (m.g == 0 && lane == 0) ev += (unsigned long long)(n.row_ptr[m.src + 1] - n.row_ptr[m.src]);
+        if (m.g == 0 && m.part == 0 && lane == 0)
+            ev += (unsigned long long)(n.row_ptr[m.src + 1] - n.row_ptr[m.src]);
         const int excl = incl - m.cnt;
-        for (int k0 = 0; k0 < total; k0 += 128) {
+        const int k_lo = (int)((long long)total * m.part / np), k_hi = (int)((long long)total * (m.part + 1) / np);
+        for (int k0 = k_lo; k0 < k_hi; k0 += 128) {
             uint32_t tdv[4];
             float wv[4];
             int bm[4];
@@ -713,7 +719,7 @@ __global__ void __launch_bounds__(256, 4) deliver_band_kernel(Net n, int i) {
                 const long long bq = __shfl_sync(0xffffffffu, m.base, l);
                 const int eq = __shfl_sync(0xffffffffu, excl, l);
                 bm[u] = m.g * 32 + l;
-                const bool in = k < total;
+                const bool in = k < k_hi;
                 const long long q = bq + (k - eq);
                 tdv[u] = in ? n.bd_td[q] : kBandPad;
                 wv[u] = in ? n.w[q] : 0.f;
